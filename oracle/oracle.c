@@ -1,0 +1,527 @@
+/*
+ * CPU ORACLE for the single-temperature Markov chain Monte Carlo decoder of the
+ * planar surface code (Hutter, Wootton, Loss, "An efficient Markov chain Monte
+ * Carlo algorithm for the surface code", arXiv:1302.2669).
+ *
+ * THIS FILE IS TEST INFRASTRUCTURE.  It is a plain, slow, obviously correct
+ * restatement of what the decoder computes, used only by the tests, by the
+ * smoke check and by the benchmark's CPU-baseline leg.  It shares no code,
+ * header, table or helper with the CUDA library and must never be linked into
+ * the product path.
+ *
+ * Representation: one byte per data qubit for the x part and one for the z
+ * part of a Pauli frame (Y = x and z), plain loops everywhere, integers for
+ * every decision.  Each function cites the passage of the paper it restates.
+ *
+ * Readings taken where the paper is silent (each is listed with its reason in
+ * the design notes of the repository):
+ *   - Geometry of the missing Fig. 1: unrotated planar layout on a
+ *     (2L-1)x(2L-1) grid; data qubits at r+c even, sigma_x ("star",
+ *     s-anyon) generators at (odd r, even c), sigma_z ("plaquette",
+ *     p-anyon) generators at (even r, odd c).  This gives the counts of
+ *     Sec. II: n_stab = 2L(L-1) generators of weight 3 or 4 and
+ *     n_qubits = n_stab + 1.
+ *   - Start state: instead of enhanced MWPM (Sec. III, needs Blossom V) each
+ *     anyon is joined by a straight string to its nearer absorbing boundary
+ *     (s-anyons: top/bottom, p-anyons: left/right, Sec. III), and class k
+ *     multiplies that pure error by a logical operator.
+ *   - Sweep: the four non-overlapping groups of Sec. V become four colours of
+ *     generators; a sweep proposes every generator once, colour by colour.
+ *   - n is sampled after every colour phase (one "group step" of Sec. V).
+ *   - Randomness: Philox4x32-10 (Salmon et al., SC'11), counter indexed; a
+ *     uniform 32-bit u per chain and proposal, assembled from "bit planes"
+ *     (see chain_uniform_less below).  Acceptance of Delta n > 0 iff
+ *     u < T[Delta n], T[d] = floor(r^d 2^32), r = e^{-beta*} (Eq. 2).
+ *   - Decision: argmin over classes of the integer sum of sampled n
+ *     (Sec. IV.A, "performing error correction in accordance with the
+ *     equivalence class E for which this value is smallest"), lowest class
+ *     on ties.
+ *   - Class index k is the absolute class code a + 2b of a frame, where a is
+ *     the parity of x on the column-0 qubits (the support of the logical
+ *     Z-bar) and b the parity of z on the row-0 qubits (support of X-bar);
+ *     Sec. II identifies classes by such parities.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_L 64
+
+/* ------------------------------------------------------------------------ */
+/* Geometry (Sec. II, Fig. 1 as read above)                                  */
+/* ------------------------------------------------------------------------ */
+
+int orc_nq(int L) { return 2 * L * L - 2 * L + 1; }     /* n_stab + 1, Sec. IV.A */
+int orc_nstab(int L) { return 2 * L * (L - 1); }         /* Sec. II */
+
+static int qidx(int L, int r, int c) { return (r * (2 * L - 1) + c) / 2; }
+static int in_grid(int L, int r, int c) { return r >= 0 && c >= 0 && r <= 2 * L - 2 && c <= 2 * L - 2; }
+
+/* Grid position of stabilizer generator number g in the syndrome layout:
+ * first the sigma_x generators row-major over (i, j), i < L-1, j < L, at grid
+ * point (2i+1, 2j); then the sigma_z generators row-major over (i, j), i < L,
+ * j < L-1, at grid point (2i, 2j+1).  Returns 0 for sigma_x, 1 for sigma_z. */
+int orc_stab_pos(int L, int g, int* r, int* c)
+{
+    int nx = (L - 1) * L;
+    if (g < nx) {
+        *r = 2 * (g / L) + 1;
+        *c = 2 * (g % L);
+        return 0;
+    }
+    g -= nx;
+    *r = 2 * (g / (L - 1));
+    *c = 2 * (g % (L - 1)) + 1;
+    return 1;
+}
+
+/* Support of generator g: the data qubits among the four grid neighbours
+ * (3 on a boundary, 4 inside, Sec. II).  Returns the weight. */
+int orc_stab_support(int L, int g, int32_t* q)
+{
+    int r, c, w = 0;
+    orc_stab_pos(L, g, &r, &c);
+    const int dr[4] = {-1, 1, 0, 0};
+    const int dc[4] = {0, 0, -1, 1};
+    for (int k = 0; k < 4; ++k)
+        if (in_grid(L, r + dr[k], c + dc[k])) q[w++] = qidx(L, r + dr[k], c + dc[k]);
+    return w;
+}
+
+/* Colour of generator g (the four groups of Sec. V): sigma_x generators with
+ * (i+j) even -> 0, odd -> 1; sigma_z generators with (i+j) even -> 2, odd -> 3. */
+int orc_stab_colour(int L, int g)
+{
+    int r, c;
+    int type = orc_stab_pos(L, g, &r, &c);
+    int i, j;
+    if (type == 0) { i = (r - 1) / 2; j = c / 2; }
+    else { i = r / 2; j = (c - 1) / 2; }
+    return 2 * type + ((i + j) & 1);
+}
+
+/* Number of generators of a colour, and the m-th generator of a colour in
+ * syndrome-layout order (row-major within each type).  Plain enumeration. */
+int orc_colour_count(int L, int col)
+{
+    int n = 0;
+    for (int g = 0; g < orc_nstab(L); ++g) n += orc_stab_colour(L, g) == col;
+    return n;
+}
+int orc_colour_member(int L, int col, int m)
+{
+    for (int g = 0; g < orc_nstab(L); ++g)
+        if (orc_stab_colour(L, g) == col && m-- == 0) return g;
+    return -1;
+}
+
+/* Syndrome of a frame: a sigma_x generator is violated (s-anyon) when it
+ * anticommutes with the error, i.e. odd overlap with the z part; a sigma_z
+ * generator (p-anyon) when the overlap with the x part is odd (Sec. II). */
+void orc_syndrome(int L, const uint8_t* ex, const uint8_t* ez, uint8_t* syn)
+{
+    int32_t q[4];
+    for (int g = 0; g < orc_nstab(L); ++g) {
+        int r, c;
+        int type = orc_stab_pos(L, g, &r, &c);
+        int w = orc_stab_support(L, g, q);
+        int par = 0;
+        for (int k = 0; k < w; ++k) par ^= type == 0 ? ez[q[k]] : ex[q[k]];
+        syn[g] = (uint8_t)par;
+    }
+}
+
+/* Class code of a frame: a = parity of x on column 0 (support of Z-bar),
+ * b = parity of z on row 0 (support of X-bar); code = a + 2b.  Applying a
+ * stabilizer generator never changes it (Sec. II: the classes are told apart
+ * by the error parity along a line joining two opposite boundaries). */
+int orc_class_code(int L, const uint8_t* ex, const uint8_t* ez)
+{
+    int a = 0, b = 0;
+    for (int i = 0; i < L; ++i) a ^= ex[qidx(L, 2 * i, 0)];
+    for (int j = 0; j < L; ++j) b ^= ez[qidx(L, 0, 2 * j)];
+    return a + 2 * b;
+}
+
+/* Multiply a frame by the logical L_k: bit 0 of k applies X-bar = sigma_x on
+ * row 0, bit 1 applies Z-bar = sigma_z on column 0. */
+void orc_apply_logical(int L, int k, uint8_t* ex, uint8_t* ez)
+{
+    if (k & 1)
+        for (int j = 0; j < L; ++j) ex[qidx(L, 0, 2 * j)] ^= 1;
+    if (k & 2)
+        for (int i = 0; i < L; ++i) ez[qidx(L, 2 * i, 0)] ^= 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two      */
+/* 32x32->64 multiplications with the published multipliers and Weyl key     */
+/* increments.                                                               */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t* ctr_in, const uint32_t* key_in, uint32_t* out)
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Synthetic syndromes: i.i.d. depolarizing noise (Eq. 1 with p_x = p_y =    */
+/* p_z = p/3, Sec. II).                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Error of syndrome number `id`: qubit q draws word (q mod 4) of the Philox
+ * block with counter (id, q div 4, 0, 0) and key (seed_lo, seed_hi ^
+ * 0x53594E44); with tau = floor((p/3) 2^32): u < tau -> X, u < 2 tau -> Y,
+ * u < 3 tau -> Z, otherwise no error. */
+void orc_gen_error(uint64_t seed, uint32_t id, int L, double p, uint8_t* ex, uint8_t* ez)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u};
+    uint64_t tau = (uint64_t)floor((p / 3.0) * 4294967296.0);
+    uint32_t blk[4];
+    for (int q = 0; q < orc_nq(L); ++q) {
+        uint32_t ctr[4] = {id, (uint32_t)(q / 4), 0, 0};
+        orc_philox4x32_10(ctr, key, blk);
+        uint64_t u = blk[q % 4];
+        int x = 0, z = 0;
+        if (u < tau) x = 1;
+        else if (u < 2 * tau) { x = 1; z = 1; }
+        else if (u < 3 * tau) z = 1;
+        ex[q] = (uint8_t)x;
+        ez[q] = (uint8_t)z;
+    }
+}
+
+/* n syndromes with ids id0 .. id0+n-1; true_class gets the class code of the
+ * sampled error (the class a perfect decoder must return). */
+void orc_gen_syndromes(uint64_t seed, uint32_t id0, int64_t n, int L, double p,
+                       uint8_t* syn, int32_t* true_class)
+{
+    int nq = orc_nq(L), ns = orc_nstab(L);
+    uint8_t* ex = malloc(nq);
+    uint8_t* ez = malloc(nq);
+    for (int64_t i = 0; i < n; ++i) {
+        orc_gen_error(seed, id0 + (uint32_t)i, L, p, ex, ez);
+        orc_syndrome(L, ex, ez, syn + i * ns);
+        if (true_class) true_class[i] = orc_class_code(L, ex, ez);
+    }
+    free(ex);
+    free(ez);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Start state (reading of Sec. III / Sec. IV start "from each equivalence  */
+/* class"): every anyon is joined by a straight string to its nearer         */
+/* absorbing boundary; ties go left (p-anyons) or up (s-anyons).             */
+/* ------------------------------------------------------------------------ */
+void orc_pure_error(int L, const uint8_t* syn, uint8_t* ex, uint8_t* ez)
+{
+    int nq = orc_nq(L);
+    memset(ex, 0, nq);
+    memset(ez, 0, nq);
+    for (int g = 0; g < orc_nstab(L); ++g) {
+        if (!syn[g]) continue;
+        int r, c;
+        int type = orc_stab_pos(L, g, &r, &c);
+        if (type == 1) {
+            /* p-anyon at (r, c odd): sigma_x string along row r to the left
+             * or right boundary, which absorb p-anyons. */
+            int left = (c + 1) / 2, right = L - (c + 1) / 2;
+            if (left <= right)
+                for (int cc = c - 1; cc >= 0; cc -= 2) ex[qidx(L, r, cc)] ^= 1;
+            else
+                for (int cc = c + 1; cc <= 2 * L - 2; cc += 2) ex[qidx(L, r, cc)] ^= 1;
+        } else {
+            /* s-anyon at (r odd, c): sigma_z string along column c to the
+             * top or bottom boundary, which absorb s-anyons. */
+            int up = (r + 1) / 2, down = L - (r + 1) / 2;
+            if (up <= down)
+                for (int rr = r - 1; rr >= 0; rr -= 2) ez[qidx(L, rr, c)] ^= 1;
+            else
+                for (int rr = r + 1; rr <= 2 * L - 2; rr += 2) ez[qidx(L, rr, c)] ^= 1;
+        }
+    }
+}
+
+/* Start frame of class k: pure error times the logical that moves its class
+ * code to k.  Returns the class code of the pure error. */
+int orc_start_frame(int L, const uint8_t* syn, int k, uint8_t* ex, uint8_t* ez)
+{
+    orc_pure_error(L, syn, ex, ez);
+    int code0 = orc_class_code(L, ex, ez);
+    orc_apply_logical(L, k ^ code0, ex, ez);
+    return code0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Acceptance table (Eq. 2): r = (p/3)/(1-p) = e^{-beta_bar}; with a        */
+/* scaled temperature beta* = s beta_bar, r* = e^{-beta*}.                   */
+/* T[d] = floor(r*^d 2^32) for d = 1..4, r*^d by repeated multiplication.   */
+/* ------------------------------------------------------------------------ */
+void orc_thresholds(double p, double beta_scale, uint64_t* T, double* beta_bar)
+{
+    double r = (p / 3.0) / (1.0 - p);
+    double rs = beta_scale == 1.0 ? r : exp(-beta_scale * -log(r));
+    double rd = rs;
+    T[0] = 0;
+    for (int d = 1; d <= 4; ++d) {
+        T[d] = (uint64_t)floor(rd * 4294967296.0);
+        rd = rd * rs;
+    }
+    if (beta_bar) *beta_bar = -log(r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The uniform u of one chain for one proposal.                             */
+/*                                                                          */
+/* C = chains per syndrome; G = min(32, smallest power of two >= C) is the  */
+/* plane width; chain c has group w = c div G and lane b = c mod G.  For    */
+/* proposal (syndrome id s, sweep t, colour col, index m within the colour) */
+/* and group w, Philox blocks j = 0, 1, ... with counter                    */
+/*    (s, t, (col << 24) | m, (w << 8) | j)                                 */
+/* and key (seed_lo, seed_hi) are concatenated into one bit stream (block j */
+/* supplies stream bits 128j .. 128j+127; word i of a block supplies bits   */
+/* 32i .. 32i+31, least significant first).  Plane k (k = 0..31) is stream  */
+/* bits kG .. kG+G-1; chain c's bit of plane k is stream bit kG + b, and    */
+/*    u_c = sum_k bit_k(c) 2^(31-k)                                         */
+/* (plane 0 is the most significant bit).                                   */
+/* ------------------------------------------------------------------------ */
+int orc_plane_width(int C)
+{
+    int G = 1;
+    while (G < C && G < 32) G *= 2;
+    return G;
+}
+
+typedef struct {
+    uint32_t key[2];
+    uint32_t s, t, col, m, w;
+    int cached_j;
+    uint32_t blk[4];
+} stream_t;
+
+static int stream_bit(stream_t* st, uint32_t idx)
+{
+    int j = (int)(idx / 128);
+    if (j != st->cached_j) {
+        uint32_t ctr[4] = {st->s, st->t, (st->col << 24) | st->m, (st->w << 8) | (uint32_t)j};
+        orc_philox4x32_10(ctr, st->key, st->blk);
+        st->cached_j = j;
+    }
+    return (st->blk[(idx / 32) % 4] >> (idx % 32)) & 1u;
+}
+
+/* Full 32-bit u of chain c (assembles all 32 planes). */
+uint32_t orc_chain_uniform(uint64_t seed, uint32_t s, uint32_t t, int col, int m, int c, int C)
+{
+    int G = orc_plane_width(C);
+    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, s, t, (uint32_t)col, (uint32_t)m,
+                   (uint32_t)(c / G), -1, {0, 0, 0, 0}};
+    uint32_t u = 0;
+    for (int k = 0; k < 32; ++k) u |= (uint32_t)stream_bit(&st, (uint32_t)(k * G + c % G)) << (31 - k);
+    return u;
+}
+
+/* u_c < T, evaluated by comparing the binary digits most significant first
+ * and stopping at the first digit where they differ (the ordinary
+ * lexicographic comparison of two 32-digit binary numbers; it reads only as
+ * many planes as the comparison needs).  T may equal 2^32. */
+int orc_chain_uniform_less(uint64_t seed, uint32_t s, uint32_t t, int col, int m, int c, int C, uint64_t T)
+{
+    if (T >= 4294967296ull) return 1;
+    int G = orc_plane_width(C);
+    stream_t st = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, s, t, (uint32_t)col, (uint32_t)m,
+                   (uint32_t)(c / G), -1, {0, 0, 0, 0}};
+    for (int k = 0; k < 32; ++k) {
+        int ub = stream_bit(&st, (uint32_t)(k * G + c % G));
+        int tb = (int)((T >> (31 - k)) & 1u);
+        if (ub != tb) return ub < tb;
+    }
+    return 0; /* equal: u == T is not less */
+}
+
+/* ------------------------------------------------------------------------ */
+/* The single-temperature algorithm (Sec. IV.A) for one syndrome.           */
+/* ------------------------------------------------------------------------ */
+
+static int weight(int nq, const uint8_t* ex, const uint8_t* ez)
+{
+    int n = 0;
+    for (int q = 0; q < nq; ++q) n += ex[q] | ez[q];
+    return n;
+}
+
+/* Delta n of applying generator g (Sec. IV: "the number Delta n by which the
+ * total number of errors n in the code would change if that stabilizer were
+ * applied"); a sigma_x generator flips x on its support, a sigma_z generator
+ * flips z.  Plain before/after count over the support. */
+static int delta_n(int type, int w, const int32_t* q, const uint8_t* ex, const uint8_t* ez)
+{
+    int before = 0, after = 0;
+    for (int k = 0; k < w; ++k) {
+        int x = ex[q[k]], z = ez[q[k]];
+        before += x | z;
+        if (type == 0) x ^= 1; else z ^= 1;
+        after += x | z;
+    }
+    return after - before;
+}
+
+typedef struct {
+    int32_t L, K, R;
+    uint32_t t_begin, t_end, burn_in;
+    double p, beta_scale;
+    uint64_t seed;
+    uint32_t id;
+} orc_run_t;
+
+/* Run all K*R chains of one syndrome over sweeps t_begin .. t_end-1.
+ *   frames_x/z [C][nq]: in: state at t_begin (if start_from_syndrome the
+ *     start frames are built here), out: final state.
+ *   chain_sum [C]: in/out running sum of sampled n (after every colour phase
+ *     of a sweep t >= burn_in); chain_n [C]: out final n;
+ *   accepts [C]: in/out number of accepted proposals (may be NULL);
+ *   trace (may be NULL): receives n after every colour phase of chain 0,
+ *     4 (t_end - t_begin) entries. */
+void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndrome,
+                    uint8_t* frames_x, uint8_t* frames_z, uint64_t* chain_sum,
+                    int32_t* chain_n, uint64_t* accepts, int32_t* trace)
+{
+    int L = a->L, nq = orc_nq(L), C = a->K * a->R;
+    uint64_t T[5];
+    orc_thresholds(a->p, a->beta_scale, T, NULL);
+    int ncol[4], members[4][ORC_MAX_L * ORC_MAX_L];
+    for (int col = 0; col < 4; ++col) {
+        ncol[col] = orc_colour_count(L, col);
+        for (int m = 0; m < ncol[col]; ++m) members[col][m] = orc_colour_member(L, col, m);
+    }
+    for (int c = 0; c < C; ++c) {
+        uint8_t* ex = frames_x + (size_t)c * nq;
+        uint8_t* ez = frames_z + (size_t)c * nq;
+        if (start_from_syndrome) orc_start_frame(L, syn, c / a->R, ex, ez);
+        int n = weight(nq, ex, ez);
+        for (uint32_t t = a->t_begin; t < a->t_end; ++t) {
+            for (int col = 0; col < 4; ++col) {
+                int type = col / 2;
+                for (int m = 0; m < ncol[col]; ++m) {
+                    int32_t q[4];
+                    int w = orc_stab_support(L, members[col][m], q);
+                    int dn = delta_n(type, w, q, ex, ez);
+                    /* Metropolis (Sec. IV): apply if Delta n <= 0, otherwise
+                     * with probability e^{-beta* Delta n} = T[Delta n] / 2^32. */
+                    int accept = dn <= 0 ||
+                                 orc_chain_uniform_less(a->seed, a->id, t, col, m, c, C, T[dn]);
+                    if (accept) {
+                        for (int k = 0; k < w; ++k) {
+                            if (type == 0) ex[q[k]] ^= 1; else ez[q[k]] ^= 1;
+                        }
+                        n += dn;
+                        if (accepts) accepts[c] += 1;
+                    }
+                }
+                /* Sec. V: n is added up after every group step. */
+                if (t >= a->burn_in) chain_sum[c] += (uint64_t)n;
+                if (trace && c == 0) trace[4 * (t - a->t_begin) + col] = n;
+            }
+        }
+        if (chain_n) chain_n[c] = n;
+    }
+}
+
+/* Decision (Sec. IV.A): S_k = sum over the R chains of class k; choose the
+ * class with the smallest S_k (the smallest <n>, all classes having the same
+ * number of samples), lowest k on ties.  Also reports the log-ratio proxy
+ * -beta_bar (<n>_k - min_k <n>_k). */
+int orc_decide(int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_bar,
+               const uint64_t* chain_sum, uint64_t* class_sum, double* log_ratio)
+{
+    uint64_t S[64];
+    int best = 0;
+    for (int k = 0; k < K; ++k) {
+        S[k] = 0;
+        for (int r = 0; r < R; ++r) S[k] += chain_sum[k * R + r];
+        if (S[k] < S[best]) best = k;
+        if (class_sum) class_sum[k] = S[k];
+    }
+    if (log_ratio) {
+        uint64_t samples = n_sweeps > burn_in ? (uint64_t)4 * (uint64_t)R * (n_sweeps - burn_in) : 0;
+        for (int k = 0; k < K; ++k) {
+            if (samples == 0) { log_ratio[k] = 0.0; continue; }
+            double mean_k = (double)S[k] / (double)samples;
+            double mean_b = (double)S[best] / (double)samples;
+            log_ratio[k] = -beta_bar * (mean_k - mean_b);
+        }
+    }
+    return best;
+}
+
+/* Full decode of one syndrome from its start frames. */
+int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in,
+                   double beta_scale, uint64_t seed, uint32_t id, const uint8_t* syn,
+                   uint64_t* class_sum, double* log_ratio, uint64_t* chain_sum, int32_t* chain_n,
+                   uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts)
+{
+    int nq = orc_nq(L), C = K * R;
+    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id};
+    uint8_t* fx = frames_x ? frames_x : malloc((size_t)C * nq);
+    uint8_t* fz = frames_z ? frames_z : malloc((size_t)C * nq);
+    uint64_t* cs = chain_sum ? chain_sum : malloc(sizeof(uint64_t) * C);
+    memset(cs, 0, sizeof(uint64_t) * C);
+    if (accepts) memset(accepts, 0, sizeof(uint64_t) * C);
+    orc_run_chains(&a, syn, 1, fx, fz, cs, chain_n, accepts, NULL);
+    double beta_bar;
+    uint64_t T[5];
+    orc_thresholds(p, 1.0, T, &beta_bar);
+    int k = orc_decide(K, R, n_sweeps, burn_in, beta_bar, cs, class_sum, log_ratio);
+    if (!frames_x) free(fx);
+    if (!frames_z) free(fz);
+    if (!chain_sum) free(cs);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact class statistics by enumeration (Eq. 3): the histogram of n over    */
+/* all 2^{n_stab} frames of each class (start frame times every product of  */
+/* generators).  hist[k][n] counts frames of class k with weight n, so that */
+/* Z_k(beta) = sum_n hist[k][n] e^{-beta n} and <n>_{beta,k} follows         */
+/* (Eq. 4).  Gray-code order: one generator is toggled per step.  L <= 4.   */
+/* ------------------------------------------------------------------------ */
+int orc_exact_histogram(int L, const uint8_t* syn, uint64_t* hist /* [4][nq+1] */)
+{
+    int nq = orc_nq(L), ns = orc_nstab(L);
+    if (ns > 30) return -1;
+    int32_t sup[4 * 64];
+    int wt[64], type[64];
+    for (int g = 0; g < ns; ++g) {
+        int r, c;
+        type[g] = orc_stab_pos(L, g, &r, &c);
+        wt[g] = orc_stab_support(L, g, sup + 4 * g);
+    }
+    uint8_t ex[64], ez[64];
+    for (int k = 0; k < 4; ++k) {
+        uint64_t* h = hist + (size_t)k * (nq + 1);
+        memset(h, 0, sizeof(uint64_t) * (nq + 1));
+        orc_start_frame(L, syn, k, ex, ez);
+        h[weight(nq, ex, ez)] += 1;
+        for (uint64_t i = 1; i < ((uint64_t)1 << ns); ++i) {
+            int g = __builtin_ctzll(i); /* generator toggled between Gray codes i-1 and i */
+            for (int e = 0; e < wt[g]; ++e) {
+                if (type[g] == 0) ex[sup[4 * g + e]] ^= 1; else ez[sup[4 * g + e]] ^= 1;
+            }
+            h[weight(nq, ex, ez)] += 1;
+        }
+    }
+    return 0;
+}
