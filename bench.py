@@ -1,0 +1,305 @@
+#!/usr/bin/env python3
+"""Throughput of the single-temperature MCMC decoder (arXiv:1302.2669, Sec. IV.A).
+
+Workload (one step = one decode call over one resident batch): planar code
+L = 13 (313 qubits), depolarizing p cycling through 0.10, 0.13, 0.16, 0.18,
+16,384 seeded synthetic syndromes per batch, 4 classes x 16 chains, 20,000
+sweeps per chain (= 312 proposals each).  Metric: syndromes decoded per second
+(and stabilizer updates per second = proposals, accepted or not), with the
+logical error rate of the decoded batches beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain C, one process per syndrome on
+the host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L = 13
+PS = [0.10, 0.13, 0.16, 0.18]
+SYN_SEEDS = [2010, 2013, 2016, 2018]
+N_PER_STEP = 16384
+K_CLASSES = 4
+R_CHAINS = 16
+SWEEPS = 20000
+NQ = 2 * L * L - 2 * L + 1
+NSTAB = 2 * L * (L - 1)
+UPDATES_PER_SYNDROME = K_CLASSES * R_CHAINS * SWEEPS * NSTAB
+WORKLOAD = (f"planar surface code L={L} ({NQ} qubits), depolarizing p cycling {PS}, {N_PER_STEP} syndromes "
+            f"per step, {K_CLASSES} classes x {R_CHAINS} chains, {SWEEPS} sweeps")
+METRIC = "syndromes decoded/sec & stabilizer updates/sec at matched logical error rate"
+SM_COUNT = 152
+INT_LANES_PER_SM = 128
+
+
+def ops_per_update() -> float:
+    """Algorithmic integer operations per proposal of one chain in the
+    bit-sliced formulation (32 chains per word): 28 bitwise ops to classify
+    Delta n and apply the flip, 6 digit planes to decide the Metropolis test
+    of a 32-chain word (10 ops of Philox4x32-10 per 32-bit plane + 6 compare
+    ops), and the carry-save recount of n after each colour phase (3 ops per
+    qubit, spread over the phase's n_stab/4 proposals)."""
+    per_word = 28 + 6 * (10 + 6) + 3.0 * NQ / (NSTAB / 4)
+    return per_word / 32.0
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def cpu_baseline(n_syn=None, p=0.13, seed=SYN_SEEDS[1]):
+    """The oracle as it stands, one process per syndrome on the host cores,
+    on `n_syn` syndromes of the workload at full length."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    n_syn = n_syn or cores
+    syn, _ = O.gen_syndromes(seed, 0, n_syn, L, p)
+    t0 = time.perf_counter()
+    O.decode_batch(L, p, K_CLASSES, R_CHAINS, SWEEPS, seed + 100, range(n_syn), syn, processes=min(cores, n_syn))
+    dt = time.perf_counter() - t0
+    return {"value": n_syn / dt, "unit": "syndromes/s", "cores": min(cores, n_syn), "kind": "oracle",
+            "sample": f"{n_syn} syndromes of the workload at p={p} (L={L}, {K_CLASSES}x{R_CHAINS} chains, "
+                      f"{SWEEPS} sweeps), one process per syndrome",
+            "updates_per_s": n_syn * UPDATES_PER_SYNDROME / dt, "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    times = []
+    for step in range(args.warmup + args.steps):
+        p = PS[step % 4]
+        r = cpu_baseline(n_syn=cores, p=p, seed=SYN_SEEDS[step % 4])
+        if step >= args.warmup:
+            times.append(r["seconds"])
+    total = sum(times)
+    value = cores * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "updates_per_s": value * UPDATES_PER_SYNDROME,
+            "config": {"workload": WORKLOAD, "sample_per_step": f"{cores} syndromes", "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} syndromes per step, full length"},
+            "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_PER_STEP, help="syndromes per step (default: the workload's)")
+    ap.add_argument("--sweeps", type=int, default=SWEEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1302_2669_gb300 as pkg
+    from paper_1302_2669_gb300 import build as b
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    b.build()
+    ctx = pkg.Context(local)
+    n, sweeps = args.n, args.sweeps
+    opts = pkg.Opts(n_classes=K_CLASSES, chains_per_class=R_CHAINS, n_sweeps=sweeps)
+    id0 = rank * n
+    like = torch.zeros(1, device=dev)
+    syn, tcls = [], []
+    for p, s in zip(PS, SYN_SEEDS):
+        a, t = ctx.gen_syndromes(s, id0, n, L, p, like=like)
+        syn.append(a)
+        tcls.append(t)
+    out_cls = torch.empty(n, dtype=torch.int32, device=dev)
+    out_sum = torch.empty((n, K_CLASSES), dtype=torch.uint64, device=dev)
+    out_lr = torch.empty((n, K_CLASSES), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(j):
+        i = j % 4
+        ctx.decode(syn[i], L, PS[i], opts, seed=SYN_SEEDS[i] + 100, id0=id0, out_class=out_cls,
+                   out_class_sum=out_sum, out_log_ratio=out_lr)
+        return i
+
+    for j in range(args.warmup):
+        step(j)
+    torch.cuda.synchronize()
+
+    fails = {p: [0, 0] for p in PS}
+    ctx.set_timing(True)
+    ctx.sweep_time()
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for j in range(args.warmup, args.warmup + args.steps):
+        flush.fill_(j)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i = step(j)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        fails[PS[i]][0] += int((out_cls != tcls[i]).sum())
+        fails[PS[i]][1] += n
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    sweep_ms, sweep_launches = ctx.sweep_time()
+    ctx.set_timing(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hsyn = [s.cpu().pin_memory() for s in syn]
+        hcls = torch.empty(n, dtype=torch.int32).pin_memory()
+        hsum = torch.empty((n, K_CLASSES), dtype=torch.uint64).pin_memory()
+        hlr = torch.empty((n, K_CLASSES), dtype=torch.float64).pin_memory()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for j in range(args.warmup, args.warmup + args.steps):
+            i = j % 4
+            ctx.decode(hsyn[i], L, PS[i], opts, seed=SYN_SEEDS[i] + 100, id0=id0, out_class=hcls, out_class_sum=hsum,
+                       out_log_ratio=hlr)
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t)
+        e2e = {"value": world * n * args.steps / e2e_s, "unit": "syndromes/s", "h2d_bytes_per_step": n * NSTAB,
+               "d2h_bytes_per_step": n * (4 + 8 * K_CLASSES + 8 * K_CLASSES)}
+
+    if rank != 0:
+        return 0
+    value = world * n * args.steps / (total_ms / 1000.0)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SM_COUNT * INT_LANES_PER_SM * sm_max * 1e6
+    avg_sweep_s = (sweep_ms / max(sweep_launches, 1)) / 1000.0
+    updates_per_launch = n * UPDATES_PER_SYNDROME * sweeps / SWEEPS
+    achieved = updates_per_launch * ops_per_update() / avg_sweep_s
+    line = {
+        "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "updates_per_s": value * UPDATES_PER_SYNDROME * sweeps / SWEEPS,
+        "config": {"workload": WORKLOAD if (n == N_PER_STEP and sweeps == SWEEPS) else
+                   f"reduced: L={L}, {n} syndromes per step, {sweeps} sweeps",
+                   "L": L, "p": PS, "syndromes_per_step": n, "classes": K_CLASSES, "chains_per_class": R_CHAINS,
+                   "sweeps": sweeps, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"shard{world}" if world > 1 else "single GPU"},
+        "ler": {f"{p:.2f}": {"ler": f / max(m, 1), "sigma": math.sqrt(max(f / max(m, 1) * (1 - f / max(m, 1)), 0)
+                                                                     / max(m, 1)), "syndromes": m}
+                for p, (f, m) in fails.items() if m},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "sweep_kernel", "ops_per_update": ops_per_update(),
+                     "kernel_ms_avg": avg_sweep_s * 1000.0, "kernel_launches": sweep_launches,
+                     "peak_basis": f"{SM_COUNT} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_max:.0f} MHz "
+                                   "(max SM clock of measured peaks)"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * surfmcmc — C ABI of a GB300 (sm_103a) implementation of the single-temperature
+ * Markov chain Monte Carlo decoder for the planar surface code of Hutter,
+ * Wootton and Loss, "An efficient Markov chain Monte Carlo algorithm for the
+ * surface code" (arXiv:1302.2669).
+ *
+ * What is computed (Sec. IV and IV.A of the paper): given the anyon
+ * configuration (syndrome) of a size-L planar code under depolarizing noise
+ * of rate p, sample <n>_{beta*,E}, the mean number of single-qubit errors of
+ * the error chains of each equivalence class E, with Metropolis chains over
+ * stabilizer moves at beta* = beta_bar = -log((p/3)/(1-p)) (Eq. 2), and
+ * return the class with the smallest mean.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Geometry (Sec. II; Fig. 1 is not available, so this is the unrotated planar
+ * layout): a (2L-1) x (2L-1) grid, data qubits at r+c even with index
+ * q = (r(2L-1)+c)/2, n_q = 2L^2-2L+1; sigma_x generators (s-anyons) at odd r,
+ * even c; sigma_z generators (p-anyons) at even r, odd c; n_stab = 2L(L-1).
+ *
+ * Syndrome layout: uint8 0/1 per generator, n_stab bytes per syndrome: first
+ * the sigma_x generators row-major over (i=(r-1)/2, j=c/2), then the sigma_z
+ * generators row-major over (i=r/2, j=(c-1)/2).
+ *
+ * Frame layout: a Pauli frame is two bit planes (x then z) of W = ceil(n_q/32)
+ * uint32 words each; qubit q is bit q%32 of word q/32; bits past n_q are zero.
+ *
+ * Class code: a + 2b, a = parity of x on the column-0 qubits, b = parity of z
+ * on the row-0 qubits (Sec. II identifies classes by error parities along a
+ * line joining opposite boundaries).  Class k chains start at the pure error
+ * times the logical that gives them class code k.
+ *
+ * Pointers: every buffer is owned by the caller and may be host or device
+ * memory (detected per pointer).  With device pointers and a non-NULL stream
+ * the call is stream-ordered and returns once the work is queued; with host
+ * buffers, or stream == NULL, the call returns after the results are in the
+ * caller's buffers.  The library keeps no pointer after a call returns.
+ *
+ * Errors: 0 on success, a negative SURFMCMC_E* code otherwise; no exception
+ * crosses the ABI.  surfmcmc_last_error() gives a message for the last
+ * failing call on a context.  Contexts are not thread-safe; use one per host
+ * thread.
+ */
+#ifndef SURFMCMC_H
+#define SURFMCMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SURFMCMC_OK 0
+#define SURFMCMC_EINVAL (-1)    /* bad argument: L, p, sizes, NULL pointer, options */
+#define SURFMCMC_ENOMEM (-2)    /* device allocation failed */
+#define SURFMCMC_ECUDA (-3)     /* a CUDA call failed; see surfmcmc_last_error */
+#define SURFMCMC_ENODEV (-4)    /* no such device, or not an sm_103 device */
+
+#define SURFMCMC_MAX_L 31       /* largest code size accepted */
+
+typedef struct surfmcmc_ctx surfmcmc_ctx;
+
+/* Decoder options.
+ *   n_classes        number of equivalence classes; must be 4 (planar code,
+ *                    Sec. II "there are four such equivalence classes").
+ *   chains_per_class R >= 1 independent replica chains per class;
+ *                    n_classes * R <= 1024.
+ *   n_sweeps         sweeps per chain; one sweep proposes every generator
+ *                    once, colour by colour (the four non-overlapping groups
+ *                    of Sec. V), so n_sample = n_sweeps * n_stab per chain.
+ *   burn_in          sweeps before sampling starts (the paper uses none).
+ *   beta_scale       beta* = beta_scale * beta_bar (Sec. IV.A sets beta* =
+ *                    beta_bar, i.e. 1.0); 0 <= beta_scale <= +infinity.
+ *   lanes_per_bundle GPU tuning knob: threads sharing one 32-chain bundle, a
+ *                    power of two in 1..32, or 0 for automatic.  Results do
+ *                    not depend on it.
+ *   reserved         must be 0. */
+typedef struct {
+    int32_t n_classes;
+    int32_t chains_per_class;
+    uint32_t n_sweeps;
+    uint32_t burn_in;
+    double beta_scale;
+    int32_t lanes_per_bundle;
+    int32_t reserved;
+} surfmcmc_opts;
+
+/* Fills opts with K = 4, R = 4, 2000 sweeps, no burn-in, beta* = beta_bar,
+ * automatic tuning. */
+void surfmcmc_default_opts(surfmcmc_opts* opts);
+
+/* Creates a context bound to CUDA device `device`; *ctx receives it.
+ * Returns ENODEV if the device does not exist or is not compute capability
+ * 10.3, EINVAL if ctx is NULL. */
+int surfmcmc_create(surfmcmc_ctx** ctx, int device);
+
+/* Releases the context and the device scratch it owns.  NULL is ignored. */
+void surfmcmc_destroy(surfmcmc_ctx* ctx);
+
+/* Static description of an error code. */
+const char* surfmcmc_strerror(int code);
+
+/* Message of the last failing call on ctx ("" if none). */
+const char* surfmcmc_last_error(const surfmcmc_ctx* ctx);
+
+/* Synthetic input: n syndromes of i.i.d. depolarizing noise (Eq. 1 with
+ * p_x = p_y = p_z = p/3, Sec. II) with ids id0 .. id0+n-1.
+ *   syndromes  [n][n_stab] uint8 out.
+ *   true_class [n] int32 out (may be NULL): class code of the sampled error,
+ *              the answer of a perfect decoder.
+ * Qubit q of syndrome id takes word q%4 of the Philox4x32-10 block with
+ * counter (id, q/4, 0, 0) and key (seed_lo, seed_hi ^ 0x53594E44); with
+ * tau = floor((p/3) 2^32): u < tau X, u < 2tau Y, u < 3tau Z, else I.
+ * EINVAL: L outside 2..SURFMCMC_MAX_L, p outside [0, 0.75], n < 0,
+ * id0 + n > 2^32, NULL syndromes with n > 0. */
+int surfmcmc_gen_syndromes(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L,
+                           double p, uint8_t* syndromes, int32_t* true_class, void* stream);
+
+/* Start state (Sec. IV: one syndrome-compatible error per class, Sec. III's
+ * boundary rule): the pure error joins every anyon to its nearer absorbing
+ * boundary by a straight string (s-anyons up/down, p-anyons left/right,
+ * ties up/left).
+ *   syndromes [n][n_stab] uint8 in.
+ *   frames    [n][2][W] uint32 out: the pure error e0.
+ *   e0_class  [n] int32 out (may be NULL): class code of e0.
+ * EINVAL as above. */
+int surfmcmc_start_frames(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L,
+                          uint32_t* frames, int32_t* e0_class, void* stream);
+
+/* The single-temperature decoder (Sec. IV.A, algorithm C) on n syndromes.
+ *   syndromes     [n][n_stab] uint8 in.
+ *   p             depolarizing rate, 0 < p <= 0.75.
+ *   opts          see surfmcmc_opts (NULL: defaults).
+ *   seed, id0     randomness key and id of syndrome 0; syndrome i uses id
+ *                 id0 + i, so a result does not depend on the batch it is in.
+ *   out_class     [n] int32 out: class code with the smallest sum of sampled
+ *                 n (lowest code on ties).
+ *   out_class_sum [n][4] uint64 out (may be NULL): S_k, the sum over the R
+ *                 chains of class k of n sampled after every colour phase of
+ *                 every sweep t >= burn_in (4 R (n_sweeps - burn_in) samples).
+ *   out_log_ratio [n][4] double out (may be NULL): -beta_bar (<n>_k -
+ *                 min_k <n>_k), a single-temperature proxy of log Z_k/Z_best.
+ * Randomness: Philox4x32-10 with key (seed_lo, seed_hi); acceptance of a
+ * proposal with Delta n = d > 0 iff u < floor(r*^d 2^32), r* = e^{-beta*},
+ * u assembled from bit planes as described for surfmcmc_decode_ex.
+ * EINVAL: bad L, p, n, options or NULL required pointers. */
+int surfmcmc_decode(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L, double p,
+                    const surfmcmc_opts* opts, uint64_t seed, uint32_t id0, int32_t* out_class,
+                    uint64_t* out_class_sum, double* out_log_ratio, void* stream);
+
+/* surfmcmc_decode with per-chain state in and out, for resuming a run and for
+ * checking single chains.  Runs sweeps sweep_begin .. opts->n_sweeps-1.
+ *   init_frames     [n][C][2][W] uint32 in (may be NULL): chain states at
+ *                   sweep_begin; NULL starts from the start frames (then
+ *                   sweep_begin must be 0).  C = 4 * chains_per_class; chain
+ *                   c has class c / chains_per_class.
+ *   init_chain_sum  [n][C] uint64 in (may be NULL = zeros): sums so far.
+ *   out_chain_sum   [n][C] uint64 out (may be NULL).
+ *   out_chain_n     [n][C] int32 out (may be NULL): final n of every chain.
+ *   out_chain_frames[n][C][2][W] uint32 out (may be NULL): final states.
+ * The per-chain uniform: G = min(32, smallest power of two >= C) is the plane
+ * width, chain c has group w = c/G and lane b = c%G.  For the proposal of
+ * the m-th generator of colour col (row-major order within the colour) in
+ * sweep t of syndrome id s, Philox blocks j = 0, 1, .. with counter
+ * (s, t, (col<<24)|m, (w<<8)|j) form a bit stream (block j = bits 128j..,
+ * word i of a block = the next 32 bits, least significant first); plane k is
+ * stream bits kG .. kG+G-1 and u_c = sum_k bit(kG+b) 2^(31-k). */
+int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L, double p,
+                       const surfmcmc_opts* opts, uint64_t seed, uint32_t id0, uint32_t sweep_begin,
+                       const uint32_t* init_frames, const uint64_t* init_chain_sum, int32_t* out_class,
+                       uint64_t* out_class_sum, double* out_log_ratio, uint64_t* out_chain_sum,
+                       int32_t* out_chain_n, uint32_t* out_chain_frames, void* stream);
+
+/* Instrumentation (the paper has no counterpart): with enable != 0 every
+ * later decode call records a pair of CUDA events on its stream around its
+ * sweep kernel.  surfmcmc_sweep_time waits for the recorded events, returns
+ * in *ms the summed sweep-kernel time in milliseconds and in *launches the
+ * number of sweep launches since the previous query (either pointer may be
+ * NULL), and clears the record.  EINVAL for a NULL ctx. */
+int surfmcmc_set_timing(surfmcmc_ctx* ctx, int enable);
+int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SURFMCMC_H */

@@ -1,0 +1,233 @@
+"""GB300 (sm_103a) single-temperature MCMC decoder for the planar surface code.
+
+Thin Python binding over the C ABI of ``libsurfmcmc.so`` (declared in
+``include/surfmcmc.h``): the names follow the C entry points, and every
+function only marshals arguments.  Tensors may be torch tensors (CUDA or CPU)
+or numpy arrays; CUDA tensors are passed as device pointers on the current
+torch stream, everything else as host pointers.  There is no CPU fallback: if
+the compiled library is missing, every call raises.
+
+Reference: Hutter, Wootton, Loss, "An efficient Markov chain Monte Carlo
+algorithm for the surface code", arXiv:1302.2669 (Sec. IV.A, algorithm C).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsurfmcmc.so")
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ENODEV = 0, -1, -2, -3, -4
+MAX_L = 31
+
+
+class SurfmcmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"surfmcmc error {code}: {msg}")
+        self.code = code
+
+
+class _Opts(C.Structure):
+    _fields_ = [("n_classes", C.c_int32), ("chains_per_class", C.c_int32), ("n_sweeps", C.c_uint32),
+                ("burn_in", C.c_uint32), ("beta_scale", C.c_double), ("lanes_per_bundle", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+@dataclasses.dataclass
+class Opts:
+    """Mirror of ``surfmcmc_opts``."""
+    n_classes: int = 4
+    chains_per_class: int = 4
+    n_sweeps: int = 2000
+    burn_in: int = 0
+    beta_scale: float = 1.0
+    lanes_per_bundle: int = 0
+
+    def c(self) -> _Opts:
+        return _Opts(self.n_classes, self.chains_per_class, self.n_sweeps, self.burn_in, self.beta_scale,
+                     self.lanes_per_bundle, 0)
+
+
+EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surfmcmc_strerror",
+           "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_start_frames", "surfmcmc_decode",
+           "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time")
+
+
+def lib():
+    """Loads libsurfmcmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1302_2669_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, u32, u64, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_uint32, C.c_uint64, C.c_double
+        L.surfmcmc_default_opts.argtypes = [C.POINTER(_Opts)]
+        L.surfmcmc_default_opts.restype = None
+        L.surfmcmc_create.argtypes = [C.POINTER(vp), C.c_int]
+        L.surfmcmc_destroy.argtypes = [vp]
+        L.surfmcmc_destroy.restype = None
+        L.surfmcmc_strerror.argtypes = [C.c_int]
+        L.surfmcmc_strerror.restype = C.c_char_p
+        L.surfmcmc_last_error.argtypes = [vp]
+        L.surfmcmc_last_error.restype = C.c_char_p
+        L.surfmcmc_gen_syndromes.argtypes = [vp, u64, u32, i64, i32, dbl, vp, vp, vp]
+        L.surfmcmc_start_frames.argtypes = [vp, vp, i64, i32, vp, vp, vp]
+        L.surfmcmc_decode.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
+        L.surfmcmc_decode_ex.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, u32, vp, vp, vp, vp,
+                                         vp, vp, vp, vp, vp]
+        L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
+        L.surfmcmc_sweep_time.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
+        _lib = L
+    return _lib
+
+
+def n_qubits(L: int) -> int:
+    return 2 * L * L - 2 * L + 1
+
+
+def n_stabs(L: int) -> int:
+    return 2 * L * (L - 1)
+
+
+def n_words(L: int) -> int:
+    return (n_qubits(L) + 31) // 32
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _empty(like, shape, np_dtype):
+    """Output buffer on the same side (torch CUDA / torch CPU / numpy) as `like`."""
+    if like is not None and _is_torch(like):
+        import torch
+        tdt = {np.uint8: torch.uint8, np.int32: torch.int32, np.uint32: torch.uint32, np.uint64: torch.uint64,
+               np.float64: torch.float64}[np_dtype]
+        return torch.empty(shape, dtype=tdt, device=like.device)
+    return np.empty(shape, dtype=np_dtype)
+
+
+def _stream_of(*xs):
+    for x in xs:
+        if x is not None and _is_torch(x) and x.is_cuda:
+            import torch
+            return torch.cuda.current_stream(x.device).cuda_stream
+    return None
+
+
+class Context:
+    """One surfmcmc_ctx bound to a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        rc = lib().surfmcmc_create(C.byref(self._h), device)
+        if rc != OK:
+            raise SurfmcmcError(rc, lib().surfmcmc_strerror(rc).decode())
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().surfmcmc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SurfmcmcError(rc, lib().surfmcmc_last_error(self._h).decode() or
+                                lib().surfmcmc_strerror(rc).decode())
+
+    def gen_syndromes(self, seed, id0, n, L, p, like=None, syndromes=None, true_class=None, stream=None):
+        """surfmcmc_gen_syndromes; outputs are allocated beside `like` if not given."""
+        if syndromes is None:
+            syndromes = _empty(like, (n, n_stabs(L)), np.uint8)
+        if true_class is None:
+            true_class = _empty(like, (n,), np.int32)
+        st = stream if stream is not None else _stream_of(syndromes)
+        self._check(lib().surfmcmc_gen_syndromes(self._h, seed, id0, n, L, p, _ptr(syndromes), _ptr(true_class),
+                                                 st))
+        return syndromes, true_class
+
+    def start_frames(self, syndromes, L, frames=None, e0_class=None, stream=None):
+        """surfmcmc_start_frames; returns (frames [n][2][W] uint32, e0_class [n])."""
+        n = syndromes.shape[0]
+        if frames is None:
+            frames = _empty(syndromes, (n, 2, n_words(L)), np.uint32)
+        if e0_class is None:
+            e0_class = _empty(syndromes, (n,), np.int32)
+        st = stream if stream is not None else _stream_of(syndromes, frames)
+        self._check(lib().surfmcmc_start_frames(self._h, _ptr(syndromes), n, L, _ptr(frames), _ptr(e0_class), st))
+        return frames, e0_class
+
+    def decode(self, syndromes, L, p, opts: Opts | None = None, seed=0, id0=0, out_class=None,
+               out_class_sum=None, out_log_ratio=None, want_sums=True, stream=None):
+        """surfmcmc_decode; returns (class, class_sum or None, log_ratio or None)."""
+        opts = opts or Opts()
+        n = syndromes.shape[0]
+        K = opts.n_classes
+        if out_class is None:
+            out_class = _empty(syndromes, (n,), np.int32)
+        if want_sums and out_class_sum is None:
+            out_class_sum = _empty(syndromes, (n, K), np.uint64)
+        if want_sums and out_log_ratio is None:
+            out_log_ratio = _empty(syndromes, (n, K), np.float64)
+        st = stream if stream is not None else _stream_of(syndromes, out_class)
+        o = opts.c()
+        self._check(lib().surfmcmc_decode(self._h, _ptr(syndromes), n, L, p, C.byref(o), seed, id0,
+                                          _ptr(out_class), _ptr(out_class_sum), _ptr(out_log_ratio), st))
+        return out_class, out_class_sum, out_log_ratio
+
+    def decode_ex(self, syndromes, L, p, opts: Opts | None = None, seed=0, id0=0, sweep_begin=0,
+                  init_frames=None, init_chain_sum=None, chain_sum=True, chain_n=True, chain_frames=True,
+                  stream=None):
+        """surfmcmc_decode_ex; returns a dict of the outputs (per-chain ones on request)."""
+        opts = opts or Opts()
+        n = syndromes.shape[0]
+        K = opts.n_classes
+        Cn = K * opts.chains_per_class
+        out = {"cls": _empty(syndromes, (n,), np.int32), "class_sum": _empty(syndromes, (n, K), np.uint64),
+               "log_ratio": _empty(syndromes, (n, K), np.float64)}
+        out["chain_sum"] = _empty(syndromes, (n, Cn), np.uint64) if chain_sum else None
+        out["chain_n"] = _empty(syndromes, (n, Cn), np.int32) if chain_n else None
+        out["chain_frames"] = _empty(syndromes, (n, Cn, 2, n_words(L)), np.uint32) if chain_frames else None
+        st = stream if stream is not None else _stream_of(syndromes, out["cls"])
+        o = opts.c()
+        self._check(lib().surfmcmc_decode_ex(
+            self._h, _ptr(syndromes), n, L, p, C.byref(o), seed, id0, sweep_begin, _ptr(init_frames),
+            _ptr(init_chain_sum), _ptr(out["cls"]), _ptr(out["class_sum"]), _ptr(out["log_ratio"]),
+            _ptr(out["chain_sum"]), _ptr(out["chain_n"]), _ptr(out["chain_frames"]), st))
+        return out
+
+    def set_timing(self, enable: bool):
+        """surfmcmc_set_timing: record CUDA events around every sweep kernel."""
+        self._check(lib().surfmcmc_set_timing(self._h, 1 if enable else 0))
+
+    def sweep_time(self):
+        """surfmcmc_sweep_time: (summed sweep-kernel ms, launches) since the last query."""
+        ms, n = C.c_double(), C.c_int64()
+        self._check(lib().surfmcmc_sweep_time(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value

@@ -1,0 +1,160 @@
+// Syndrome generation, start frames and the per-syndrome decision: the small
+// kernels around the sweep kernel.  One thread per syndrome; frames are kept
+// as packed bit planes in registers/local memory.
+#include "common.cuh"
+
+namespace surfmcmc {
+
+__device__ __forceinline__ int getb(const uint32_t* w, int q) { return (w[q >> 5] >> (q & 31)) & 1; }
+__device__ __forceinline__ void flipb(uint32_t* w, int q) { w[q >> 5] ^= 1u << (q & 31); }
+
+// Anticommutation parities of every generator, in syndrome order (sigma_x
+// generators first, row-major; then sigma_z generators): a sigma_x generator
+// sees the z plane, a sigma_z generator the x plane (Sec. II).
+__device__ void write_syndrome(int L, const uint32_t* ex, const uint32_t* ez, uint8_t* out) {
+    const int n = 2 * L - 1;
+    int g = 0;
+    for (int i = 0; i < L - 1; ++i)
+        for (int j = 0; j < L; ++j, ++g) {
+            const int r = 2 * i + 1, c = 2 * j, base = r * n + c;
+            int par = getb(ez, (base - n) / 2) ^ getb(ez, (base + n) / 2);
+            if (c > 0) par ^= getb(ez, (base - 1) / 2);
+            if (c < n - 1) par ^= getb(ez, (base + 1) / 2);
+            out[g] = (uint8_t)par;
+        }
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < L - 1; ++j, ++g) {
+            const int r = 2 * i, c = 2 * j + 1, base = r * n + c;
+            int par = getb(ex, (base - 1) / 2) ^ getb(ex, (base + 1) / 2);
+            if (r > 0) par ^= getb(ex, (base - n) / 2);
+            if (r < n - 1) par ^= getb(ex, (base + n) / 2);
+            out[g] = (uint8_t)par;
+        }
+}
+
+// Class code a + 2b: a = x parity on column 0 (qubits i(2L-1)), b = z parity
+// on row 0 (qubits 0..L-1).
+__device__ int class_code(int L, const uint32_t* ex, const uint32_t* ez) {
+    int a = 0, b = 0;
+    for (int i = 0; i < L; ++i) a ^= getb(ex, i * (2 * L - 1));
+    for (int j = 0; j < L; ++j) b ^= getb(ez, j);
+    return a + 2 * b;
+}
+
+__global__ void gen_syndromes_kernel(RoundKeys rk, uint32_t id0, long long n, int L, uint32_t tau1,
+                                     uint32_t tau2, uint32_t tau3, uint8_t* syn, int32_t* true_class) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nq = n_qubits(L), W = n_words(L);
+    uint32_t ex[kMaxWords], ez[kMaxWords];
+    for (int w = 0; w < W; ++w) ex[w] = ez[w] = 0;
+    const uint32_t id = id0 + (uint32_t)i;
+    for (int q0 = 0; q0 < nq; q0 += 4) {
+        const uint4 b = philox10(make_uint4(id, (uint32_t)(q0 / 4), 0u, 0u), rk);
+        const uint32_t u[4] = {b.x, b.y, b.z, b.w};
+        for (int k = 0; k < 4 && q0 + k < nq; ++k) {
+            // X for u < tau, Y for tau <= u < 2 tau, Z for 2 tau <= u < 3 tau
+            if (u[k] < tau2) flipb(ex, q0 + k);
+            if (u[k] >= tau1 && u[k] < tau3) flipb(ez, q0 + k);
+        }
+    }
+    write_syndrome(L, ex, ez, syn + i * n_stabs(L));
+    if (true_class) true_class[i] = class_code(L, ex, ez);
+}
+
+// Pure error: a straight string from every anyon to its nearer absorbing
+// boundary (Sec. III), s-anyons vertically (z string), p-anyons horizontally
+// (x string); ties go up/left.
+__global__ void start_frames_kernel(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int W = n_words(L), n2 = 2 * L - 1;
+    uint32_t ex[kMaxWords], ez[kMaxWords];
+    for (int w = 0; w < W; ++w) ex[w] = ez[w] = 0;
+    const uint8_t* s = syn + i * n_stabs(L);
+    int g = 0;
+    for (int a = 0; a < L - 1; ++a)
+        for (int b = 0; b < L; ++b, ++g) {
+            if (!s[g]) continue;
+            const int r = 2 * a + 1, c = 2 * b;
+            if ((r + 1) / 2 <= L - (r + 1) / 2)
+                for (int rr = r - 1; rr >= 0; rr -= 2) flipb(ez, (rr * n2 + c) / 2);
+            else
+                for (int rr = r + 1; rr < n2; rr += 2) flipb(ez, (rr * n2 + c) / 2);
+        }
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L - 1; ++b, ++g) {
+            if (!s[g]) continue;
+            const int r = 2 * a, c = 2 * b + 1;
+            if ((c + 1) / 2 <= L - (c + 1) / 2)
+                for (int cc = c - 1; cc >= 0; cc -= 2) flipb(ex, (r * n2 + cc) / 2);
+            else
+                for (int cc = c + 1; cc < n2; cc += 2) flipb(ex, (r * n2 + cc) / 2);
+        }
+    uint32_t* f = frames + i * 2 * W;
+    for (int w = 0; w < W; ++w) {
+        f[w] = ex[w];
+        f[W + w] = ez[w];
+    }
+    if (code) code[i] = class_code(L, ex, ez);
+}
+
+// Sec. IV.A decision: S_k = sum over the R chains of class k; the class with
+// the smallest S_k (lowest k on ties); log-ratio proxy -beta_bar (<n>_k -
+// <n>_best) in double precision.
+__global__ void decide_kernel(DecideParams p) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    const uint64_t* cs = p.chain_sum + i * p.K * p.R;
+    uint64_t S[4];
+    int best = 0;
+    for (int k = 0; k < p.K; ++k) {
+        uint64_t s = 0;
+        for (int r = 0; r < p.R; ++r) s += cs[k * p.R + r];
+        S[k] = s;
+        if (s < S[best]) best = k;
+    }
+    p.out_class[i] = best;
+    if (p.out_class_sum)
+        for (int k = 0; k < p.K; ++k) p.out_class_sum[i * p.K + k] = S[k];
+    if (p.out_log_ratio)
+        for (int k = 0; k < p.K; ++k) {
+            double v = 0.0;
+            if (p.samples) {
+                const double mk = (double)S[k] / (double)p.samples;
+                const double mb = (double)S[best] / (double)p.samples;
+                v = -p.beta_bar * (mk - mb);
+            }
+            p.out_log_ratio[i * p.K + k] = v;
+        }
+}
+
+cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p, uint8_t* syn,
+                                 int32_t* true_class, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    RoundKeys rk;
+    make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u, &rk);
+    const uint64_t tau = (uint64_t)floor((p / 3.0) * 4294967296.0);
+    const int bs = 128;
+    gen_syndromes_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rk, id0, n, L, (uint32_t)tau,
+                                                                      (uint32_t)(2 * tau), (uint32_t)(3 * tau),
+                                                                      syn, true_class);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
+                                cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int bs = 128;
+    start_frames_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(syn, n, L, frames, code);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decide(const DecideParams& p, cudaStream_t s) {
+    if (p.n == 0) return cudaSuccess;
+    const int bs = 128;
+    decide_kernel<<<(unsigned)((p.n + bs - 1) / bs), bs, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace surfmcmc

@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libsurfmcmc.
+// Device helpers: Philox4x32-10, code geometry, and the parameter blocks of
+// the kernels.  Nothing here is visible through the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace surfmcmc {
+
+constexpr int kMaxL = 31;
+constexpr int kMaxWords = (2 * kMaxL * kMaxL - 2 * kMaxL + 1 + 31) / 32;  // 59
+constexpr int kCountBits = 11;  // n_q(31) = 1861 < 2^11
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The ten round keys are
+// precomputed on the host (key + i * Weyl constants), so a round is two
+// 32x32->64 multiplications and two three-input XORs.
+// ---------------------------------------------------------------------------
+struct RoundKeys {
+    uint32_t k[20];  // k[2i], k[2i+1]: key words used in round i
+};
+
+__device__ __forceinline__ uint4 philox10(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k[2 * i], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk.k[2 * i + 1], (uint32_t)p0);
+    }
+    return c;
+}
+
+inline void make_round_keys(uint32_t k0, uint32_t k1, RoundKeys* rk) {
+    for (int i = 0; i < 10; ++i) {
+        rk->k[2 * i] = k0;
+        rk->k[2 * i + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of the unrotated planar code on the (2L-1)x(2L-1) grid.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int n_qubits(int L) { return 2 * L * L - 2 * L + 1; }
+__host__ __device__ __forceinline__ int n_stabs(int L) { return 2 * L * (L - 1); }
+__host__ __device__ __forceinline__ int n_words(int L) { return (n_qubits(L) + 31) / 32; }
+
+// Grid point of the m-th generator of colour col.  Colours 0/1 are the
+// sigma_x generators ((L-1) x L cells at (2i+1, 2j)) with i+j even/odd,
+// colours 2/3 the sigma_z generators (L x (L-1) cells at (2i, 2j+1)).  Within
+// a colour the cells are taken row-major.  With an odd number of columns the
+// row-major cell index g has the parity of i+j, so the colour's cells are
+// g = 2m + parity; with an even number every row holds half of them.
+__host__ __device__ __forceinline__ void colour_cell(int L, int col, int m, int* r, int* c) {
+    const int par = col & 1;
+    const int wdt = col < 2 ? L : L - 1;
+    int i, j;
+    if (wdt & 1) {
+        const int g = 2 * m + par;
+        i = g / wdt;
+        j = g - i * wdt;
+    } else {
+        const int half = wdt / 2;
+        i = m / half;
+        j = 2 * (m - i * half) + ((i + par) & 1);
+    }
+    if (col < 2) { *r = 2 * i + 1; *c = 2 * j; }
+    else { *r = 2 * i; *c = 2 * j + 1; }
+}
+
+// Support of the m-th generator of colour col: up, down, left, right
+// neighbours of its grid point.  A neighbour outside the grid (boundary
+// generators have weight 3) is replaced by a dummy slot: nq for sigma_x
+// generators, nq+1 for sigma_z generators.  The dummy's "other" plane is
+// all ones, so it never changes n.
+__host__ __device__ __forceinline__ void colour_support(int L, int col, int m, int q[4]) {
+    int r, c;
+    colour_cell(L, col, m, &r, &c);
+    const int n = 2 * L - 1, nq = n_qubits(L);
+    const int dummy = col < 2 ? nq : nq + 1;
+    const int base = r * n + c;  // odd
+    q[0] = r > 0 ? (base - n) / 2 : dummy;
+    q[1] = r < n - 1 ? (base + n) / 2 : dummy;
+    q[2] = c > 0 ? (base - 1) / 2 : dummy;
+    q[3] = c < n - 1 ? (base + 1) / 2 : dummy;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep kernel parameters.
+// ---------------------------------------------------------------------------
+struct SweepParams {
+    int L, nq, W, nc;          // size, qubits, words per plane, generators per colour
+    int C, R, G;               // chains per syndrome, per class, plane width
+    int bps, spb;              // bundles per syndrome (G == 32), syndromes per bundle (G < 32)
+    long long n;               // syndromes
+    long long n_bundles;
+    uint32_t id0;
+    const uint32_t* ids;       // per-syndrome ids (NULL: id0 + index)
+    uint32_t t_begin, t_end, burn_in;
+    int accept_all;            // r* == 1: every proposal accepted
+    int reject_all;            // T[1] == 0: no uphill proposal accepted
+    int lz;                    // leading planes where every threshold bit is 0
+    RoundKeys rk;
+    // Threshold bits of plane k as the algebraic normal form of the map
+    // d-1 = e0 + 2 e1 -> bit (31-k) of T[d]: f = c0 ^ e0 c1 ^ e1 c2 ^ e0 e1 c3.
+    uint32_t pc[4][32];
+    const uint32_t* e0;        // [n][2][W] pure errors
+    const int32_t* e0code;     // [n]
+    const uint32_t* init_frames;  // [n][C][2][W] or NULL
+    const uint64_t* init_sum;     // [n][C] or NULL
+    uint64_t* chain_sum;       // [n][C] out
+    int32_t* chain_n;          // [n][C] out or NULL
+    uint32_t* chain_frames;    // [n][C][2][W] out or NULL
+};
+
+struct DecideParams {
+    long long n;
+    int K, R;
+    uint64_t samples;          // 4 R (n_sweeps - burn_in)
+    double beta_bar;
+    const uint64_t* chain_sum; // [n][K R]
+    int32_t* out_class;        // [n]
+    uint64_t* out_class_sum;   // [n][K] or NULL
+    double* out_log_ratio;     // [n][K] or NULL
+};
+
+// Launchers (return cudaGetLastError() after the launch).
+cudaError_t launch_sweep(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
+size_t sweep_smem_bytes(const SweepParams& p, int lanes_per_bundle, int warps);
+cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p,
+                                 uint8_t* syn, int32_t* true_class, cudaStream_t s);
+cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
+                                cudaStream_t s);
+cudaError_t launch_decide(const DecideParams& p, cudaStream_t s);
+
+}  // namespace surfmcmc

@@ -1,0 +1,401 @@
+// The Metropolis sweep kernel (Sec. IV / IV.A, parallelised as in Sec. V).
+//
+// Data layout.  Chains are bit-sliced: a "bundle" holds 32 chains, and each
+// data qubit of a bundle is two 32-bit words in shared memory, X[q] and Z[q],
+// whose bit b is the x (z) part of the Pauli frame of the bundle's chain b.
+// One proposal of generator g is therefore evaluated for 32 chains at once
+// with bitwise logic on the 3-4 words of its support.
+//
+// Work split.  A warp holds 32/LAM bundles; LAM lanes share a bundle and
+// split the generators of the current colour (Sec. V: the four groups have
+// no qubit in common, so their proposals are independent and any order
+// within a colour gives the sequential result).  After each colour phase the
+// lanes recount n for all 32 chains (carry-save counters plus a butterfly
+// over the LAM lanes) and add it to the chains' sums.
+//
+// Acceptance.  Delta n <= 0 is accepted; Delta n = d > 0 is accepted iff the
+// chain's uniform u < T[d].  u is compared digit by digit, most significant
+// first: plane k of Philox output supplies digit 31-k of u for the 32 chains,
+// and a chain is decided at its first digit that differs from T[d]'s.  The
+// warp stops drawing planes once every chain of its proposals is decided.
+#include "common.cuh"
+
+namespace surfmcmc {
+
+__device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+// n of the 32 chains of a bundle as kCountBits bit planes, identical in all
+// LAM lanes of the bundle.
+template <int LAM>
+__device__ __forceinline__ void recount(const uint32_t* X, const uint32_t* Z, int nq, int sub,
+                                        uint32_t cnt[kCountBits]) {
+    uint32_t ones = 0, twos = 0, fours = 0;
+    uint32_t hi[kCountBits - 3];
+#pragma unroll
+    for (int k = 0; k < kCountBits - 3; ++k) hi[k] = 0;
+    for (int base = sub; base < nq; base += 8 * LAM) {
+        uint32_t x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int q = base + i * LAM;
+            x[i] = q < nq ? (X[q] | Z[q]) : 0u;
+        }
+        uint32_t ta, tb, fa, fb, e;
+        csa(ta, ones, ones, x[0], x[1]);
+        csa(tb, ones, ones, x[2], x[3]);
+        csa(fa, twos, twos, ta, tb);
+        csa(ta, ones, ones, x[4], x[5]);
+        csa(tb, ones, ones, x[6], x[7]);
+        csa(fb, twos, twos, ta, tb);
+        csa(e, fours, fours, fa, fb);
+#pragma unroll
+        for (int k = 0; k < kCountBits - 3; ++k) {
+            const uint32_t c = hi[k] & e;
+            hi[k] ^= e;
+            e = c;
+        }
+    }
+    cnt[0] = ones;
+    cnt[1] = twos;
+    cnt[2] = fours;
+#pragma unroll
+    for (int k = 0; k < kCountBits - 3; ++k) cnt[3 + k] = hi[k];
+#pragma unroll
+    for (int off = 1; off < LAM; off <<= 1) {
+        uint32_t carry = 0;
+#pragma unroll
+        for (int k = 0; k < kCountBits; ++k) {
+            const uint32_t o = __shfl_xor_sync(0xffffffffu, cnt[k], off);
+            const uint32_t a = cnt[k];
+            cnt[k] = a ^ o ^ carry;
+            carry = (a & o) | (carry & (a ^ o));
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t bit_of(const uint32_t cnt[kCountBits], int b) {
+    uint32_t n = 0;
+#pragma unroll
+    for (int k = 0; k < kCountBits; ++k) n |= ((cnt[k] >> b) & 1u) << k;
+    return n;
+}
+
+// Planes of one batch.  G = 32: one block per syndrome group, 4 planes per
+// block (word i = plane i).  G < 32: 32/G syndromes share a bundle, each
+// block holds 128/G planes of G bits; the bundle's plane word takes bits
+// [kG, kG+G) of every slot's block and puts slot s at bits [sG, sG+G).
+template <int G>
+struct PlaneBatch {
+    static constexpr int SLOTS = G == 32 ? 1 : 32 / G;
+    static constexpr int PPB = G == 32 ? 4 : 128 / G;
+    uint32_t pl[PPB];
+
+    __device__ __forceinline__ void make(const SweepParams& p, const uint32_t* sid, uint32_t w, uint32_t t,
+                                         uint32_t colm, uint32_t bt) {
+        if constexpr (G == 32) {
+            const uint4 b = philox10(make_uint4(sid[0], t, colm, (w << 8) | bt), p.rk);
+            pl[0] = b.x; pl[1] = b.y; pl[2] = b.z; pl[3] = b.w;
+        } else if constexpr (G == 16) {
+            const uint4 a = philox10(make_uint4(sid[0], t, colm, bt), p.rk);
+            const uint4 c = philox10(make_uint4(sid[1], t, colm, bt), p.rk);
+            const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                pl[2 * i] = __byte_perm(aw[i], cw[i], 0x5410);
+                pl[2 * i + 1] = __byte_perm(aw[i], cw[i], 0x7632);
+            }
+        } else if constexpr (G == 8) {
+            uint32_t bw[4][4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const uint4 b = philox10(make_uint4(sid[s], t, colm, bt), p.rk);
+                bw[s][0] = b.x; bw[s][1] = b.y; bw[s][2] = b.z; bw[s][3] = b.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int wi = k / 4, by = k % 4;
+                const uint32_t sel = (uint32_t)(by | ((4 + by) << 4));
+                const uint32_t lo = __byte_perm(bw[0][wi], bw[1][wi], sel);
+                const uint32_t hi = __byte_perm(bw[2][wi], bw[3][wi], sel);
+                pl[k] = __byte_perm(lo, hi, 0x5410);
+            }
+        } else {  // G == 4
+            uint32_t bw[8][4];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint4 b = philox10(make_uint4(sid[s], t, colm, bt), p.rk);
+                bw[s][0] = b.x; bw[s][1] = b.y; bw[s][2] = b.z; bw[s][3] = b.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int wi = k / 8, sh = 4 * (k % 8);
+                uint32_t v = 0;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) v |= ((bw[s][wi] >> sh) & 0xFu) << (4 * s);
+                pl[k] = v;
+            }
+        }
+    }
+};
+
+// Accept mask of the undecided uphill chains U (all have Delta n = d > 0,
+// d - 1 = E0 + 2 E1 bitwise): chains whose u < T[d].
+template <int G>
+__device__ __forceinline__ uint32_t bernoulli(const SweepParams& p, uint32_t U, uint32_t E0, uint32_t E1,
+                                              const uint32_t* sid, uint32_t w, uint32_t t, uint32_t colm) {
+    using PB = PlaneBatch<G>;
+    constexpr int PPB = PB::PPB;
+    constexpr int NBATCH = 32 / PPB;
+    const uint32_t E01 = E0 & E1;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int bt = 0; bt < NBATCH; ++bt) {
+        PB pb;
+        pb.make(p, sid, w, t, colm, (uint32_t)bt);
+        if ((bt + 1) * PPB <= p.lz) {
+            // every threshold digit is 0 here: a 1 digit rejects
+#pragma unroll
+            for (int i = 0; i < PPB; ++i) U &= ~pb.pl[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < PPB; ++i) {
+                const int k = bt * PPB + i;
+                const uint32_t f = p.pc[0][k] ^ (E0 & p.pc[1][k]) ^ (E1 & p.pc[2][k]) ^ (E01 & p.pc[3][k]);
+                acc |= U & f & ~pb.pl[i];
+                U &= ~(f ^ pb.pl[i]);
+            }
+        }
+        if (!U) break;
+    }
+    return acc;
+}
+
+template <int G, int LAM>
+__global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ SweepParams p) {
+    constexpr int B = 32 / LAM;                       // bundles per warp
+    constexpr int NJ = 32 / LAM;                      // chains owned per lane
+    constexpr int SLOTS = PlaneBatch<G>::SLOTS;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int nc = p.nc, nq = p.nq, L = p.L;
+    const int stride = 2 * (nq + 2);
+    ushort4* tab = reinterpret_cast<ushort4*>(smem);
+    uint32_t* frames = smem + 8 * nc;
+
+    for (int idx = threadIdx.x; idx < 4 * nc; idx += blockDim.x) {
+        const int col = idx / nc, m = idx - col * nc;
+        int q[4];
+        colour_support(L, col, m, q);
+        tab[idx] = make_ushort4((unsigned short)q[0], (unsigned short)q[1], (unsigned short)q[2],
+                                (unsigned short)q[3]);
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = lane / LAM, sub = lane % LAM;
+    const long long bid = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * B + slot;
+    const bool active = bid < p.n_bundles;
+    uint32_t* X = frames + (warp * B + slot) * stride;
+    uint32_t* Z = X + nq + 2;
+
+    // Syndromes and chains of the bundle.
+    long long syn[SLOTS];
+    uint32_t sid[SLOTS];
+    uint32_t w = 0, valid = 0;
+    if constexpr (G == 32) {
+        syn[0] = active ? bid / p.bps : 0;
+        w = active ? (uint32_t)(bid % p.bps) : 0;
+        sid[0] = p.ids ? p.ids[syn[0]] : p.id0 + (uint32_t)syn[0];
+        const int left = p.C - 32 * (int)w;
+        valid = !active ? 0u : left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+    } else {
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            syn[s] = bid * SLOTS + s;
+            const bool ok = active && syn[s] < p.n;
+            if (!ok) syn[s] = bid * SLOTS;  // any in-range syndrome; its bits are masked
+            if (!active) syn[s] = 0;
+            sid[s] = p.ids ? p.ids[syn[s]] : p.id0 + (uint32_t)syn[s];
+            if (ok) valid |= ((1u << p.C) - 1u) << (s * G);
+        }
+    }
+    // chain index and syndrome of bundle bit b
+    auto chain_of = [&](int b) -> int { return G == 32 ? 32 * (int)w + b : b % G; };
+    auto syn_of = [&](int b) -> long long { return G == 32 ? syn[0] : syn[G == 32 ? 0 : b / G]; };
+
+    // Start state: pure error times the logical that gives chain c the class
+    // code c / R (bit 0: X-bar on row 0, bit 1: Z-bar on column 0).
+    uint32_t lx = 0, lzm = 0;
+    for (int b = 0; b < 32 && !p.init_frames; ++b) {
+        if (!((valid >> b) & 1u)) continue;
+        const int k = chain_of(b) / p.R;
+        const int l = k ^ p.e0code[syn_of(b)];
+        lx |= (uint32_t)(l & 1) << b;
+        lzm |= (uint32_t)((l >> 1) & 1) << b;
+    }
+    const int W = p.W;
+    for (int q = sub; q < nq; q += LAM) {
+        uint32_t xw = 0, zw = 0;
+        if (p.init_frames) {
+            for (int b = 0; b < 32; ++b) {
+                if (!((valid >> b) & 1u)) continue;
+                const uint32_t* f = p.init_frames + ((size_t)syn_of(b) * p.C + chain_of(b)) * 2 * W;
+                xw |= ((f[q >> 5] >> (q & 31)) & 1u) << b;
+                zw |= ((f[W + (q >> 5)] >> (q & 31)) & 1u) << b;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) {
+                const uint32_t vm = G == 32 ? valid : (valid & (((1u << (G & 31)) - 1u) << (s * G)));
+                if (!vm) continue;
+                const uint32_t* e = p.e0 + (size_t)syn[s] * 2 * W;
+                if ((e[q >> 5] >> (q & 31)) & 1u) xw |= vm;
+                if ((e[W + (q >> 5)] >> (q & 31)) & 1u) zw |= vm;
+            }
+            if (q < L) xw ^= lx;                  // row-0 qubits: X-bar
+            if (q % (2 * L - 1) == 0) zw ^= lzm;  // column-0 qubits: Z-bar
+        }
+        X[q] = xw;
+        Z[q] = zw;
+    }
+    if (sub == 0) {
+        X[nq] = 0u; Z[nq] = 0xFFFFFFFFu;          // dummy of sigma_x generators
+        X[nq + 1] = 0xFFFFFFFFu; Z[nq + 1] = 0u;  // dummy of sigma_z generators
+    }
+    uint64_t S[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int b = sub + j * LAM;
+        S[j] = (p.init_sum && ((valid >> b) & 1u)) ? p.init_sum[(size_t)syn_of(b) * p.C + chain_of(b)] : 0ull;
+    }
+    __syncwarp();
+
+    for (uint32_t t = p.t_begin; t < p.t_end; ++t) {
+#pragma unroll 1
+        for (int col = 0; col < 4; ++col) {
+            uint32_t* own = col < 2 ? X : Z;          // plane the generator flips
+            const uint32_t* oth = col < 2 ? Z : X;    // plane it only reads
+            const uint32_t colm = (uint32_t)col << 24;
+            const ushort4* tc = tab + col * nc;
+            if (active) {
+                for (int m = sub; m < nc; m += LAM) {
+                    const ushort4 sp = tc[m];
+                    const uint32_t o0 = own[sp.x], o1 = own[sp.y], o2 = own[sp.z], o3 = own[sp.w];
+                    // movable qubits (the flip changes their weight): other part 0
+                    const uint32_t m0 = ~oth[sp.x], m1 = ~oth[sp.y], m2 = ~oth[sp.z], m3 = ~oth[sp.w];
+                    // W = number of movable qubits, bits w2 w1 w0
+                    const uint32_t s3 = m0 ^ m1 ^ m2, c3 = (m0 & m1) | (m2 & (m0 ^ m1));
+                    const uint32_t w0 = s3 ^ m3, cc = s3 & m3, w1 = c3 ^ cc, w2 = c3 & cc;
+                    // D = number of movable qubits whose error the flip removes
+                    const uint32_t d0 = m0 & o0, d1 = m1 & o1, d2 = m2 & o2, d3 = m3 & o3;
+                    const uint32_t ds = d0 ^ d1 ^ d2, dc = (d0 & d1) | (d2 & (d0 ^ d1));
+                    const uint32_t Z0 = ~(ds | dc | d3), D1 = ~dc & (ds ^ d3);
+                    // Delta n = W - 2D > 0  iff  (D = 0, W >= 1) or (D = 1, W >= 3)
+                    const uint32_t Wge1 = w0 | w1 | w2, Wge3 = w2 | (w1 & w0);
+                    const uint32_t P = (Z0 & Wge1) | (D1 & Wge3);
+                    uint32_t acc = ~P & valid;
+                    if (p.accept_all) {
+                        acc = valid;
+                    } else {
+                        const uint32_t U = P & valid;
+                        if (U && !p.reject_all) {
+                            // Delta n - 1 = E0 + 2 E1 on the uphill chains
+                            const uint32_t E0 = ~w0, E1 = Z0 & Wge3;
+                            acc |= bernoulli<G>(p, U, E0, E1, sid, w, t, colm | (uint32_t)m);
+                        }
+                    }
+                    if (acc) {
+                        own[sp.x] = o0 ^ acc;
+                        own[sp.y] = o1 ^ acc;
+                        own[sp.z] = o2 ^ acc;
+                        own[sp.w] = o3 ^ acc;
+                    }
+                }
+            }
+            __syncwarp();
+            if (t >= p.burn_in) {
+                uint32_t cnt[kCountBits];
+                recount<LAM>(X, Z, nq, sub, cnt);
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) S[j] += bit_of(cnt, sub + j * LAM);
+                __syncwarp();
+            }
+        }
+    }
+
+    uint32_t cnt[kCountBits];
+    recount<LAM>(X, Z, nq, sub, cnt);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int b = sub + j * LAM;
+        if (!((valid >> b) & 1u)) continue;
+        const size_t ci = (size_t)syn_of(b) * p.C + chain_of(b);
+        p.chain_sum[ci] = S[j];
+        if (p.chain_n) p.chain_n[ci] = (int32_t)bit_of(cnt, b);
+        if (p.chain_frames) {
+            uint32_t* f = p.chain_frames + ci * 2 * W;
+            for (int wi = 0; wi < W; ++wi) {
+                uint32_t xw = 0, zw = 0;
+                for (int i = 0; i < 32; ++i) {
+                    const int q = 32 * wi + i;
+                    if (q >= nq) break;
+                    xw |= ((X[q] >> b) & 1u) << i;
+                    zw |= ((Z[q] >> b) & 1u) << i;
+                }
+                f[wi] = xw;
+                f[W + wi] = zw;
+            }
+        }
+    }
+}
+
+constexpr int kWarps = 4;
+
+size_t sweep_smem_bytes(const SweepParams& p, int lam, int warps) {
+    return (size_t)8 * p.nc * 4 + (size_t)warps * (32 / lam) * 2 * (p.nq + 2) * 4;
+}
+
+template <int G, int LAM>
+static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
+    constexpr int B = 32 / LAM;
+    const size_t smem = sweep_smem_bytes(p, LAM, kWarps);
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    const long long per_block = (long long)kWarps * B;
+    const long long blocks = (p.n_bundles + per_block - 1) / per_block;
+    if (blocks == 0) return cudaSuccess;
+    sweep_kernel<G, LAM><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int G>
+static cudaError_t launch_g(const SweepParams& p, int lam, cudaStream_t s) {
+    switch (lam) {
+        case 2: return launch_t<G, 2>(p, s);
+        case 4: return launch_t<G, 4>(p, s);
+        case 8: return launch_t<G, 8>(p, s);
+        case 16: return launch_t<G, 16>(p, s);
+        case 32: return launch_t<G, 32>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sweep(const SweepParams& p, int lam, cudaStream_t s) {
+    switch (p.G) {
+        case 4: return launch_g<4>(p, lam, s);
+        case 8: return launch_g<8>(p, lam, s);
+        case 16: return launch_g<16>(p, lam, s);
+        case 32: return launch_g<32>(p, lam, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace surfmcmc
