@@ -88,6 +88,11 @@ __host__ __device__ __forceinline__ void colour_support(int L, int col, int m, i
     q[3] = c < n - 1 ? (base + 1) / 2 : dummy;
 }
 
+// Shared-memory words of one bundle: X[0..nq+1] then Z[0..nq+1] (two dummy
+// slots each).  The stride is odd so that the bundles of a warp fall on banks
+// of opposite parity: same-colour generators in a row are two qubits apart.
+__host__ __device__ __forceinline__ int bundle_stride(int nq) { return 2 * (nq + 2) + 1; }
+
 // ---------------------------------------------------------------------------
 // Sweep kernel parameters.
 // ---------------------------------------------------------------------------

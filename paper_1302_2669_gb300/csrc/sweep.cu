@@ -9,9 +9,10 @@
 // Work split.  A warp holds 32/LAM bundles; LAM lanes share a bundle and
 // split the generators of the current colour (Sec. V: the four groups have
 // no qubit in common, so their proposals are independent and any order
-// within a colour gives the sequential result).  After each colour phase the
-// lanes recount n for all 32 chains (carry-save counters plus a butterfly
-// over the LAM lanes) and add it to the chains' sums.
+// within a colour gives the sequential result).  After each colour phase
+// every lane adds the occupancy of its slice of the qubits into a running
+// carry-save counter; the LAM lanes' counters are added together and credited
+// to the chains' sums only when a counter could overflow and at the end.
 //
 // Acceptance.  Delta n <= 0 is accepted; Delta n = d > 0 is accepted iff the
 // chain's uniform u < T[d].  u is compared digit by digit, most significant
@@ -82,6 +83,86 @@ __device__ __forceinline__ uint32_t bit_of(const uint32_t cnt[kCountBits], int b
 #pragma unroll
     for (int k = 0; k < kCountBits; ++k) n |= ((cnt[k] >> b) & 1u) << k;
     return n;
+}
+
+// Running per-lane count of occupied qubits, summed over colour phases, in
+// carry-save form: value = ones + 2 twos + 4 fours + 8 hi (hi a bit-sliced
+// counter of kAccHi planes).  Each lane accumulates only its own slice of the
+// qubits; the slices of a bundle's LAM lanes are added together only when the
+// accumulator is flushed into the chains' 64-bit sums.
+constexpr int kAccHi = 16;
+constexpr uint32_t kAccCapacity = 8u * (1u << kAccHi) - 1u;
+constexpr int kFlushPlanes = 3 + kAccHi + 5;  // + butterfly growth over <= 32 lanes
+
+struct OccAcc {
+    uint32_t ones, twos, fours, hi[kAccHi];
+    __device__ __forceinline__ void clear() {
+        ones = twos = fours = 0;
+#pragma unroll
+        for (int k = 0; k < kAccHi; ++k) hi[k] = 0;
+    }
+};
+
+template <int LAM>
+__device__ __forceinline__ void accumulate_phase(OccAcc& a, const uint32_t* X, const uint32_t* Z, int nq, int sub) {
+    for (int base = sub; base < nq; base += 8 * LAM) {
+        uint32_t x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int q = base + i * LAM;
+            x[i] = q < nq ? (X[q] | Z[q]) : 0u;
+        }
+        uint32_t ta, tb, fa, fb, e;
+        csa(ta, a.ones, a.ones, x[0], x[1]);
+        csa(tb, a.ones, a.ones, x[2], x[3]);
+        csa(fa, a.twos, a.twos, ta, tb);
+        csa(ta, a.ones, a.ones, x[4], x[5]);
+        csa(tb, a.ones, a.ones, x[6], x[7]);
+        csa(fb, a.twos, a.twos, ta, tb);
+        csa(e, a.fours, a.fours, fa, fb);
+#pragma unroll
+        for (int k = 0; k < kAccHi; ++k) {
+            if (!e) break;
+            const uint32_t c = a.hi[k] & e;
+            a.hi[k] ^= e;
+            e = c;
+        }
+    }
+}
+
+// Adds the accumulated counts of the bundle's LAM lanes (butterfly) and
+// credits every owned chain's sum; clears the accumulator.
+template <int LAM, typename ChainIndex>
+__device__ __forceinline__ void flush_acc(OccAcc& a, int sub, uint32_t valid, uint64_t* sums, ChainIndex ci_of) {
+    uint32_t v[kFlushPlanes];
+    v[0] = a.ones;
+    v[1] = a.twos;
+    v[2] = a.fours;
+#pragma unroll
+    for (int k = 0; k < kAccHi; ++k) v[3 + k] = a.hi[k];
+#pragma unroll
+    for (int k = 3 + kAccHi; k < kFlushPlanes; ++k) v[k] = 0;
+#pragma unroll
+    for (int off = 1; off < LAM; off <<= 1) {
+        uint32_t carry = 0;
+#pragma unroll
+        for (int k = 0; k < kFlushPlanes; ++k) {
+            const uint32_t o = __shfl_xor_sync(0xffffffffu, v[k], off);
+            const uint32_t x = v[k];
+            v[k] = x ^ o ^ carry;
+            carry = (x & o) | (carry & (x ^ o));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32 / LAM; ++j) {
+        const int b = sub + j * LAM;
+        if (!((valid >> b) & 1u)) continue;
+        uint64_t n = 0;
+#pragma unroll
+        for (int k = 0; k < kFlushPlanes; ++k) n |= (uint64_t)((v[k] >> b) & 1u) << k;
+        sums[ci_of(b)] += n;
+    }
+    a.clear();
 }
 
 // Planes of one batch.  G = 32: one block per syndrome group, 4 planes per
@@ -181,7 +262,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
     constexpr int SLOTS = PlaneBatch<G>::SLOTS;
     extern __shared__ __align__(16) uint32_t smem[];
     const int nc = p.nc, nq = p.nq, L = p.L;
-    const int stride = 2 * (nq + 2);
+    const int stride = bundle_stride(nq);
     ushort4* tab = reinterpret_cast<ushort4*>(smem);
     uint32_t* frames = smem + 8 * nc;
 
@@ -265,12 +346,20 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
         X[nq] = 0u; Z[nq] = 0xFFFFFFFFu;          // dummy of sigma_x generators
         X[nq + 1] = 0xFFFFFFFFu; Z[nq + 1] = 0u;  // dummy of sigma_z generators
     }
-    uint64_t S[NJ];
+    // Owned chains' sums live in the output array; flushes add to them.
+    auto ci_of = [&](int b) -> size_t { return (size_t)syn_of(b) * p.C + chain_of(b); };
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
         const int b = sub + j * LAM;
-        S[j] = (p.init_sum && ((valid >> b) & 1u)) ? p.init_sum[(size_t)syn_of(b) * p.C + chain_of(b)] : 0ull;
+        if (!((valid >> b) & 1u)) continue;
+        const size_t ci = ci_of(b);
+        p.chain_sum[ci] = p.init_sum ? p.init_sum[ci] : 0ull;
     }
+    OccAcc occ;
+    occ.clear();
+    const uint32_t qpl = (uint32_t)((nq + LAM - 1) / LAM);  // qubits counted per lane and phase
+    const uint32_t flush_every = kAccCapacity / qpl;       // phases before the accumulator could overflow
+    uint32_t since_flush = 0;
     __syncwarp();
 
     for (uint32_t t = p.t_begin; t < p.t_end; ++t) {
@@ -317,15 +406,17 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
             }
             __syncwarp();
             if (t >= p.burn_in) {
-                uint32_t cnt[kCountBits];
-                recount<LAM>(X, Z, nq, sub, cnt);
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) S[j] += bit_of(cnt, sub + j * LAM);
+                accumulate_phase<LAM>(occ, X, Z, nq, sub);
+                if (++since_flush == flush_every) {
+                    flush_acc<LAM>(occ, sub, valid, p.chain_sum, ci_of);
+                    since_flush = 0;
+                }
                 __syncwarp();
             }
         }
     }
 
+    flush_acc<LAM>(occ, sub, valid, p.chain_sum, ci_of);
     uint32_t cnt[kCountBits];
     recount<LAM>(X, Z, nq, sub, cnt);
 #pragma unroll
@@ -333,7 +424,6 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
         const int b = sub + j * LAM;
         if (!((valid >> b) & 1u)) continue;
         const size_t ci = (size_t)syn_of(b) * p.C + chain_of(b);
-        p.chain_sum[ci] = S[j];
         if (p.chain_n) p.chain_n[ci] = (int32_t)bit_of(cnt, b);
         if (p.chain_frames) {
             uint32_t* f = p.chain_frames + ci * 2 * W;
@@ -355,7 +445,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
 constexpr int kWarps = 4;
 
 size_t sweep_smem_bytes(const SweepParams& p, int lam, int warps) {
-    return (size_t)8 * p.nc * 4 + (size_t)warps * (32 / lam) * 2 * (p.nq + 2) * 4;
+    return (size_t)8 * p.nc * 4 + (size_t)warps * (32 / lam) * bundle_stride(p.nq) * 4;
 }
 
 template <int G, int LAM>
