@@ -9,7 +9,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/surfmcmc.h"
+#include "surfmcmc.h"
 #include "common.cuh"
 
 using namespace surfmcmc;
