@@ -147,9 +147,7 @@ void acceptance_table(double p, double beta_scale, uint64_t T[5], double* beta_b
 
 int pick_lanes(int L, int requested, int* lam_out) {
     const int nq = n_qubits(L), nc = L * (L - 1) / 2;
-    auto smem_ok = [&](int lam) {
-        return (size_t)32 * nc + (size_t)4 * (32 / lam) * bundle_stride(nq) * 4 <= 200 * 1024;
-    };
+    auto smem_ok = [&](int lam) { return sweep_smem_bytes(nq, nc, lam) <= 200 * 1024; };
     if (requested) {
         if (requested != 2 && requested != 4 && requested != 8 && requested != 16 && requested != 32)
             return SURFMCMC_EINVAL;

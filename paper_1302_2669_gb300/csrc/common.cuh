@@ -134,7 +134,7 @@ struct DecideParams {
 
 // Launchers (return cudaGetLastError() after the launch).
 cudaError_t launch_sweep(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
-size_t sweep_smem_bytes(const SweepParams& p, int lanes_per_bundle, int warps);
+size_t sweep_smem_bytes(int nq, int nc, int lanes_per_bundle);  // dynamic shared memory of a block
 cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p,
                                  uint8_t* syn, int32_t* true_class, cudaStream_t s);
 cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,

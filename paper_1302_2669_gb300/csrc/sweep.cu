@@ -224,17 +224,17 @@ struct PlaneBatch {
 };
 
 // Accept mask of the undecided uphill chains U (all have Delta n = d > 0,
-// d - 1 = E0 + 2 E1 bitwise): chains whose u < T[d].
-template <int G>
-__device__ __forceinline__ uint32_t bernoulli(const SweepParams& p, uint32_t U, uint32_t E0, uint32_t E1,
-                                              const uint32_t* sid, uint32_t w, uint32_t t, uint32_t colm) {
+// d - 1 = E0 + 2 E1 bitwise): chains whose u < T[d], deciding with the digit
+// planes of batches BT0 .. BT1-1.  U keeps the chains still undecided.
+template <int G, int BT0, int BT1>
+__device__ __forceinline__ uint32_t bernoulli_range(const SweepParams& p, uint32_t& U, uint32_t E0, uint32_t E1,
+                                                    const uint32_t* sid, uint32_t w, uint32_t t, uint32_t colm) {
     using PB = PlaneBatch<G>;
     constexpr int PPB = PB::PPB;
-    constexpr int NBATCH = 32 / PPB;
     const uint32_t E01 = E0 & E1;
     uint32_t acc = 0;
 #pragma unroll
-    for (int bt = 0; bt < NBATCH; ++bt) {
+    for (int bt = BT0; bt < BT1; ++bt) {
         PB pb;
         pb.make(p, sid, w, t, colm, (uint32_t)bt);
         if ((bt + 1) * PPB <= p.lz) {
@@ -253,6 +253,19 @@ __device__ __forceinline__ uint32_t bernoulli(const SweepParams& p, uint32_t U, 
         if (!U) break;
     }
     return acc;
+}
+
+// Proposals whose chains are not all decided after the first kHeadPlanes
+// digit planes are queued per warp and finished after the colour's inline
+// pass by all lanes together, so that one slow proposal does not hold the
+// warp's other lanes.
+constexpr int kHeadPlanes = 8;
+constexpr int kQueueCap = 64;
+constexpr int kQueueItem = 5;  // (m | slot << 16), U, E0, E1, accepted so far
+constexpr int kMaxSlots = 8;
+
+__host__ __device__ __forceinline__ int warp_aux_words(int bundles) {
+    return 1 + kQueueCap * kQueueItem + bundles * (kMaxSlots + 1);
 }
 
 template <int G, int LAM>
@@ -281,6 +294,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
     const bool active = bid < p.n_bundles;
     uint32_t* X = frames + (warp * B + slot) * stride;
     uint32_t* Z = X + nq + 2;
+    uint32_t* q_cnt = frames + (blockDim.x >> 5) * B * stride + warp * warp_aux_words(B);
+    uint32_t* q_items = q_cnt + 1;
+    uint32_t* binfo = q_items + kQueueCap * kQueueItem;  // per slot: w, sid[SLOTS]
 
     // Syndromes and chains of the bundle.
     long long syn[SLOTS];
@@ -302,6 +318,11 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
             sid[s] = p.ids ? p.ids[syn[s]] : p.id0 + (uint32_t)syn[s];
             if (ok) valid |= ((1u << p.C) - 1u) << (s * G);
         }
+    }
+    if (sub == 0) {
+        binfo[slot * (kMaxSlots + 1)] = w;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) binfo[slot * (kMaxSlots + 1) + 1 + s] = sid[s];
     }
     // chain index and syndrome of bundle bit b
     auto chain_of = [&](int b) -> int { return G == 32 ? 32 * (int)w + b : b % G; };
@@ -369,6 +390,11 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
             const uint32_t* oth = col < 2 ? Z : X;    // plane it only reads
             const uint32_t colm = (uint32_t)col << 24;
             const ushort4* tc = tab + col * nc;
+            constexpr int PPB = PlaneBatch<G>::PPB;
+            constexpr int NBATCH = 32 / PPB;
+            constexpr int HEAD = kHeadPlanes / PPB > 0 ? kHeadPlanes / PPB : 1;
+            if (lane == 0) *q_cnt = 0u;
+            __syncwarp();
             if (active) {
                 for (int m = sub; m < nc; m += LAM) {
                     const ushort4 sp = tc[m];
@@ -389,11 +415,27 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
                     if (p.accept_all) {
                         acc = valid;
                     } else {
-                        const uint32_t U = P & valid;
+                        uint32_t U = P & valid;
                         if (U && !p.reject_all) {
                             // Delta n - 1 = E0 + 2 E1 on the uphill chains
                             const uint32_t E0 = ~w0, E1 = Z0 & Wge3;
-                            acc |= bernoulli<G>(p, U, E0, E1, sid, w, t, colm | (uint32_t)m);
+                            const uint32_t cm = colm | (uint32_t)m;
+                            acc |= bernoulli_range<G, 0, HEAD>(p, U, E0, E1, sid, w, t, cm);
+                            if constexpr (HEAD < NBATCH) {
+                                if (U) {
+                                    const uint32_t qi = atomicAdd(q_cnt, 1u);
+                                    if (qi < (uint32_t)kQueueCap) {
+                                        uint32_t* it = q_items + kQueueItem * qi;
+                                        it[0] = (uint32_t)m | ((uint32_t)slot << 16);
+                                        it[1] = U;
+                                        it[2] = E0;
+                                        it[3] = E1;
+                                        it[4] = acc;
+                                        continue;  // flipped after the queue is resolved
+                                    }
+                                    acc |= bernoulli_range<G, HEAD, NBATCH>(p, U, E0, E1, sid, w, t, cm);
+                                }
+                            }
                         }
                     }
                     if (acc) {
@@ -405,6 +447,32 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
                 }
             }
             __syncwarp();
+            if constexpr (HEAD < NBATCH) {
+                // Finish the queued proposals, one per lane.
+                const uint32_t n_items = min(*q_cnt, (uint32_t)kQueueCap);
+                for (uint32_t i = lane; i < n_items; i += 32) {
+                    const uint32_t* it = q_items + kQueueItem * i;
+                    const int qm = (int)(it[0] & 0xFFFFu), qs = (int)(it[0] >> 16);
+                    uint32_t U = it[1];
+                    uint32_t acc = it[4];
+                    const uint32_t* info = binfo + qs * (kMaxSlots + 1);
+                    uint32_t qsid[SLOTS];
+#pragma unroll
+                    for (int s = 0; s < SLOTS; ++s) qsid[s] = info[1 + s];
+                    acc |= bernoulli_range<G, HEAD, NBATCH>(p, U, it[2], it[3], qsid, info[0], t,
+                                                            colm | (uint32_t)qm);
+                    if (acc) {
+                        uint32_t* qx = frames + (warp * B + qs) * stride;
+                        uint32_t* qown = col < 2 ? qx : qx + nq + 2;
+                        const ushort4 sp = tc[qm];
+                        qown[sp.x] ^= acc;
+                        qown[sp.y] ^= acc;
+                        qown[sp.z] ^= acc;
+                        qown[sp.w] ^= acc;
+                    }
+                }
+                __syncwarp();
+            }
             if (t >= p.burn_in) {
                 accumulate_phase<LAM>(occ, X, Z, nq, sub);
                 if (++since_flush == flush_every) {
@@ -444,14 +512,15 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
 
 constexpr int kWarps = 4;
 
-size_t sweep_smem_bytes(const SweepParams& p, int lam, int warps) {
-    return (size_t)8 * p.nc * 4 + (size_t)warps * (32 / lam) * bundle_stride(p.nq) * 4;
+size_t sweep_smem_bytes(int nq, int nc, int lam) {
+    const int B = 32 / lam;
+    return (size_t)8 * nc * 4 + (size_t)kWarps * ((size_t)B * bundle_stride(nq) + warp_aux_words(B)) * 4;
 }
 
 template <int G, int LAM>
 static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
     constexpr int B = 32 / LAM;
-    const size_t smem = sweep_smem_bytes(p, LAM, kWarps);
+    const size_t smem = sweep_smem_bytes(p.nq, p.nc, LAM);
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
