@@ -44,6 +44,7 @@
 #ifndef SURFMCMC_H
 #define SURFMCMC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -179,6 +180,38 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
  * NULL), and clears the record.  EINVAL for a NULL ctx. */
 int surfmcmc_set_timing(surfmcmc_ctx* ctx, int enable);
 int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches);
+
+/* Allocation-free decoding.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory, for example a
+ * host program whose device memory is already entirely reserved by another
+ * allocator, or one that runs under a fixed device-memory budget.  It does the
+ * same work as surfmcmc_decode with the same results, but calls no cudaMalloc,
+ * cudaFree or allocating library routine and needs no context: its scratch
+ * (pure errors, their class codes and the per-chain sums) is one fixed
+ * SURFMCMC_NOALLOC_SCRATCH_BYTES array in the library's device memory, which
+ * every GPU that loads the library holds until the process exits.
+ *   Buffers: syndromes, out_class and (if not NULL) out_class_sum and
+ *   out_log_ratio must be device memory of the current device; the layouts
+ *   and results are those of surfmcmc_decode.  opts->lanes_per_bundle must
+ *   be 0.  With stream == NULL the call returns after the results are
+ *   written; otherwise it is stream-ordered.
+ *   Scratch: the call needs surfmcmc_noalloc_scratch_needed(n, L, R) bytes;
+ *   a batch needing more than SURFMCMC_NOALLOC_SCRATCH_BYTES is rejected with
+ *   EINVAL before any work is queued (split it into smaller batches).
+ *   Sharing: every call on a device uses the same array and leaves its
+ *   contents behind; the call initialises all of it that it reads.  Calls
+ *   whose work overlaps on the GPU (other host threads, or other streams not
+ *   ordered with this one) race on the array and give wrong results.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Errors: EINVAL for bad arguments, host pointers or an oversized batch,
+ *   ECUDA if a CUDA call fails. */
+#define SURFMCMC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+size_t surfmcmc_noalloc_scratch_needed(int64_t n, int32_t L, int32_t chains_per_class);
+int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int32_t L, double p, const surfmcmc_opts* opts,
+                            uint64_t seed, uint32_t id0, int32_t* out_class, uint64_t* out_class_sum,
+                            double* out_log_ratio, void* stream);
 
 #ifdef __cplusplus
 }

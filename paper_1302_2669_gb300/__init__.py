@@ -55,7 +55,9 @@ class Opts:
 
 EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surfmcmc_strerror",
            "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_start_frames", "surfmcmc_decode",
-           "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time")
+           "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time", "surfmcmc_noalloc_scratch_needed",
+           "surfmcmc_decode_noalloc")
+NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
 def lib():
@@ -81,6 +83,9 @@ def lib():
         L.surfmcmc_decode.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
         L.surfmcmc_decode_ex.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, u32, vp, vp, vp, vp,
                                          vp, vp, vp, vp, vp]
+        L.surfmcmc_noalloc_scratch_needed.argtypes = [i64, i32, i32]
+        L.surfmcmc_noalloc_scratch_needed.restype = C.c_size_t
+        L.surfmcmc_decode_noalloc.argtypes = [vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
         L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
         L.surfmcmc_sweep_time.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         _lib = L
