@@ -73,9 +73,16 @@ typedef struct surfmcmc_ctx surfmcmc_ctx;
  *   beta_scale       beta* = beta_scale * beta_bar (Sec. IV.A sets beta* =
  *                    beta_bar, i.e. 1.0); 0 <= beta_scale <= +infinity.
  *   lanes_per_bundle GPU tuning knob: threads sharing one 32-chain bundle, a
- *                    power of two in 1..32, or 0 for automatic.  Results do
+ *                    power of two in 2..32, or 0 for automatic.  Results do
  *                    not depend on it.
- *   reserved         must be 0. */
+ *   anneal_stages    S >= 0.  With S > 0 the burn-in prepares the start
+ *                    (Sec. IV wants each chain to start near the low-energy
+ *                    configurations of its class, since heating up from them
+ *                    is fast and cooling down is slow): burn-in sweeps
+ *                    floor(jB/S) .. floor((j+1)B/S)-1 (B = burn_in) run at
+ *                    beta* (a0 + (1 - a0) j / S), j = 0..S-1; needs
+ *                    S <= burn_in and S <= 64.
+ *   anneal_beta0     a0 in (0, 1], the first stage's fraction of beta*. */
 typedef struct {
     int32_t n_classes;
     int32_t chains_per_class;
@@ -83,11 +90,12 @@ typedef struct {
     uint32_t burn_in;
     double beta_scale;
     int32_t lanes_per_bundle;
-    int32_t reserved;
+    int32_t anneal_stages;
+    double anneal_beta0;
 } surfmcmc_opts;
 
 /* Fills opts with K = 4, R = 4, 2000 sweeps, no burn-in, beta* = beta_bar,
- * automatic tuning. */
+ * no annealing (a0 = 1), automatic tuning. */
 void surfmcmc_default_opts(surfmcmc_opts* opts);
 
 /* Creates a context bound to CUDA device `device`; *ctx receives it.
@@ -138,7 +146,8 @@ int surfmcmc_start_frames(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n
  *                 n (lowest code on ties).
  *   out_class_sum [n][4] uint64 out (may be NULL): S_k, the sum over the R
  *                 chains of class k of n sampled after every colour phase of
- *                 every sweep t >= burn_in (4 R (n_sweeps - burn_in) samples).
+ *                 every sweep t >= burn_in (4 R (n_sweeps - burn_in) samples);
+ *                 sweeps t count from 0 through the burn-in.
  *   out_log_ratio [n][4] double out (may be NULL): -beta_bar (<n>_k -
  *                 min_k <n>_k), a single-temperature proxy of log Z_k/Z_best.
  * Randomness: Philox4x32-10 with key (seed_lo, seed_hi); acceptance of a
@@ -192,8 +201,8 @@ int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches);
  * every GPU that loads the library holds until the process exits.
  *   Buffers: syndromes, out_class and (if not NULL) out_class_sum and
  *   out_log_ratio must be device memory of the current device; the layouts
- *   and results are those of surfmcmc_decode.  opts->lanes_per_bundle must
- *   be 0.  With stream == NULL the call returns after the results are
+ *   and results are those of surfmcmc_decode.  opts->lanes_per_bundle and
+ *   opts->anneal_stages must be 0.  With stream == NULL the call returns after the results are
  *   written; otherwise it is stream-ordered.
  *   Scratch: the call needs surfmcmc_noalloc_scratch_needed(n, L, R) bytes;
  *   a batch needing more than SURFMCMC_NOALLOC_SCRATCH_BYTES is rejected with

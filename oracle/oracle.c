@@ -24,7 +24,10 @@
  *   - Start state: instead of enhanced MWPM (Sec. III, needs Blossom V) each
  *     anyon is joined by a straight string to its nearer absorbing boundary
  *     (s-anyons: top/bottom, p-anyons: left/right, Sec. III), and class k
- *     multiplies that pure error by a logical operator.
+ *     multiplies that pure error by a logical operator.  Optionally the
+ *     burn-in anneals these starts from a higher temperature down to beta*
+ *     (see orc_anneal_scale), standing in for the low-energy starts of
+ *     Sec. IV.
  *   - Sweep: the four non-overlapping groups of Sec. V become four colours of
  *     generators; a sweep proposes every generator once, colour by colour.
  *   - n is sampled after every colour phase (one "group step" of Sec. V).
@@ -385,7 +388,29 @@ typedef struct {
     double p, beta_scale;
     uint64_t seed;
     uint32_t id;
+    int32_t anneal_stages;
+    double anneal_beta0;
 } orc_run_t;
+
+/* Start preparation (reading of Sec. IV: the chains should start near the
+ * low-energy configurations of their class, because heating up from them is
+ * fast while cooling down from a high-energy start is slow).  The burn-in
+ * sweeps 0 .. B-1 are split into S stages; stage j covers sweeps
+ * floor(jB/S) .. floor((j+1)B/S)-1 and runs at beta = beta* times
+ * a0 + (1 - a0) j / S.  Nothing is sampled during the burn-in. */
+double orc_anneal_scale(double beta_scale, double a0, int j, int S)
+{
+    return beta_scale * (a0 + (1.0 - a0) * (double)j / (double)S);
+}
+
+int orc_anneal_stage(uint32_t t, uint32_t B, int S)
+{
+    for (int j = 0; j < S; ++j) {
+        uint64_t lo = (uint64_t)j * B / (uint64_t)S, hi = (uint64_t)(j + 1) * B / (uint64_t)S;
+        if (t >= lo && t < hi) return j;
+    }
+    return -1;
+}
 
 /* Run all K*R chains of one syndrome over sweeps t_begin .. t_end-1.
  *   frames_x/z [C][nq]: in: state at t_begin (if start_from_syndrome the
@@ -400,8 +425,10 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                     int32_t* chain_n, uint64_t* accepts, int32_t* trace)
 {
     int L = a->L, nq = orc_nq(L), C = a->K * a->R;
-    uint64_t T[5];
-    orc_thresholds(a->p, a->beta_scale, T, NULL);
+    uint64_t Tmain[5], Tst[64][5];
+    orc_thresholds(a->p, a->beta_scale, Tmain, NULL);
+    for (int j = 0; j < a->anneal_stages && j < 64; ++j)
+        orc_thresholds(a->p, orc_anneal_scale(a->beta_scale, a->anneal_beta0, j, a->anneal_stages), Tst[j], NULL);
     int ncol[4], members[4][ORC_MAX_L * ORC_MAX_L];
     for (int col = 0; col < 4; ++col) {
         ncol[col] = orc_colour_count(L, col);
@@ -413,6 +440,8 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
         if (start_from_syndrome) orc_start_frame(L, syn, c / a->R, ex, ez);
         int n = weight(nq, ex, ez);
         for (uint32_t t = a->t_begin; t < a->t_end; ++t) {
+            int stage = a->anneal_stages > 0 ? orc_anneal_stage(t, a->burn_in, a->anneal_stages) : -1;
+            const uint64_t* T = stage >= 0 ? Tst[stage] : Tmain;
             for (int col = 0; col < 4; ++col) {
                 int type = col / 2;
                 for (int m = 0; m < ncol[col]; ++m) {
@@ -469,12 +498,12 @@ int orc_decide(int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_ba
 
 /* Full decode of one syndrome from its start frames. */
 int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in,
-                   double beta_scale, uint64_t seed, uint32_t id, const uint8_t* syn,
-                   uint64_t* class_sum, double* log_ratio, uint64_t* chain_sum, int32_t* chain_n,
-                   uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts)
+                   double beta_scale, int anneal_stages, double anneal_beta0, uint64_t seed, uint32_t id,
+                   const uint8_t* syn, uint64_t* class_sum, double* log_ratio, uint64_t* chain_sum,
+                   int32_t* chain_n, uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts)
 {
     int nq = orc_nq(L), C = K * R;
-    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id};
+    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0};
     uint8_t* fx = frames_x ? frames_x : malloc((size_t)C * nq);
     uint8_t* fz = frames_z ? frames_z : malloc((size_t)C * nq);
     uint64_t* cs = chain_sum ? chain_sum : malloc(sizeof(uint64_t) * C);

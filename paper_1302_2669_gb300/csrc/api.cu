@@ -145,6 +145,32 @@ void acceptance_table(double p, double beta_scale, uint64_t T[5], double* beta_b
     *beta_bar = -log(r);
 }
 
+// Burn-in stage j of S runs at beta* (a0 + (1 - a0) j / S).
+double anneal_scale(double beta_scale, double a0, int j, int S) {
+    return beta_scale * (a0 + (1.0 - a0) * (double)j / (double)S);
+}
+
+// Acceptance thresholds of one launch as kernel parameters: flags, the
+// number of leading all-zero digit planes, and per plane k the algebraic
+// normal form of d-1 -> bit (31-k) of T[d].
+void set_temperature(SweepParams& sp, double p, double beta_scale) {
+    uint64_t T[5];
+    double beta_bar;
+    acceptance_table(p, beta_scale, T, &beta_bar);
+    sp.accept_all = T[1] >= 4294967296ull;
+    sp.reject_all = T[1] == 0;
+    sp.lz = sp.accept_all ? 0 : (T[1] == 0 ? 32 : __builtin_clz((uint32_t)T[1]));
+    for (int k = 0; k < 32; ++k) {
+        uint32_t t[5] = {0, 0, 0, 0, 0};
+        if (!sp.accept_all)
+            for (int d = 1; d <= 4; ++d) t[d] = (uint32_t)((T[d] >> (31 - k)) & 1u);
+        sp.pc[0][k] = t[1] ? ~0u : 0u;
+        sp.pc[1][k] = (t[1] ^ t[2]) ? ~0u : 0u;
+        sp.pc[2][k] = (t[1] ^ t[3]) ? ~0u : 0u;
+        sp.pc[3][k] = (t[1] ^ t[2] ^ t[3] ^ t[4]) ? ~0u : 0u;
+    }
+}
+
 int pick_lanes(int L, int requested, int* lam_out) {
     const int nq = n_qubits(L), nc = L * (L - 1) / 2;
     auto smem_ok = [&](int lam) { return sweep_smem_bytes(nq, nc, lam) <= 200 * 1024; };
@@ -179,7 +205,8 @@ void surfmcmc_default_opts(surfmcmc_opts* o) {
     o->burn_in = 0;
     o->beta_scale = 1.0;
     o->lanes_per_bundle = 0;
-    o->reserved = 0;
+    o->anneal_stages = 0;
+    o->anneal_beta0 = 1.0;
 }
 
 const char* surfmcmc_strerror(int code) {
@@ -318,7 +345,10 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     if (!(o.beta_scale >= 0.0)) return fail(ctx, SURFMCMC_EINVAL, "beta_scale must be >= 0");
     if (std::isinf(o.beta_scale) && p == 0.75)
         return fail(ctx, SURFMCMC_EINVAL, "infinite beta_scale needs p < 0.75 (beta_bar = 0)");
-    if (o.reserved != 0) return fail(ctx, SURFMCMC_EINVAL, "reserved option must be 0");
+    if (o.anneal_stages < 0 || o.anneal_stages > 64)
+        return fail(ctx, SURFMCMC_EINVAL, "anneal_stages=%d outside 0..64", o.anneal_stages);
+    if (o.anneal_stages > 0 && ((uint32_t)o.anneal_stages > o.burn_in || !(o.anneal_beta0 > 0.0 && o.anneal_beta0 <= 1.0)))
+        return fail(ctx, SURFMCMC_EINVAL, "annealing needs anneal_stages <= burn_in and 0 < anneal_beta0 <= 1");
     if (sweep_begin > o.n_sweeps) return fail(ctx, SURFMCMC_EINVAL, "sweep_begin > n_sweeps");
     if (!init_frames && sweep_begin != 0)
         return fail(ctx, SURFMCMC_EINVAL, "sweep_begin > 0 needs init_frames");
@@ -351,24 +381,24 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     sp.n_bundles = G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
     sp.id0 = id0;
     sp.ids = nullptr;
-    sp.t_begin = sweep_begin;
-    sp.t_end = o.n_sweeps;
-    sp.burn_in = o.burn_in;
-    uint64_t T[5];
-    double beta_bar;
-    acceptance_table(p, o.beta_scale, T, &beta_bar);
-    sp.accept_all = T[1] >= 4294967296ull;
-    sp.reject_all = T[1] == 0;
-    sp.lz = sp.accept_all ? 0 : (T[1] == 0 ? 32 : __builtin_clz((uint32_t)T[1]));
-    for (int k = 0; k < 32 && !sp.accept_all; ++k) {
-        uint32_t t[5];
-        for (int d = 1; d <= 4; ++d) t[d] = (uint32_t)((T[d] >> (31 - k)) & 1u);
-        sp.pc[0][k] = t[1] ? ~0u : 0u;
-        sp.pc[1][k] = (t[1] ^ t[2]) ? ~0u : 0u;
-        sp.pc[2][k] = (t[1] ^ t[3]) ? ~0u : 0u;
-        sp.pc[3][k] = (t[1] ^ t[2] ^ t[3] ^ t[4]) ? ~0u : 0u;
-    }
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
+
+    // Launch segments: the annealing stages of the burn-in (no sampling),
+    // then the rest of the run at beta*.  Sweep indices are absolute.
+    struct Segment { uint32_t t0, t1; double scale; bool anneal; };
+    std::vector<Segment> segs;
+    const uint32_t B = o.burn_in;
+    const int S = o.anneal_stages;
+    for (int j = 0; j < S; ++j) {
+        const uint32_t lo = (uint32_t)((uint64_t)j * B / (uint64_t)S);
+        const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * B / (uint64_t)S);
+        const uint32_t a = lo > sweep_begin ? lo : sweep_begin;
+        if (a < hi) segs.push_back({a, hi, anneal_scale(o.beta_scale, o.anneal_beta0, j, S), true});
+    }
+    {
+        const uint32_t main0 = S > 0 && B > sweep_begin ? B : sweep_begin;
+        segs.push_back({main0, o.n_sweeps, o.beta_scale, false});
+    }
 
     Carver cv;
     Buf b_syn, b_if, b_is, b_cls, b_csum, b_lr, b_chn, b_chf;
@@ -385,6 +415,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     const size_t off_chs = chs_scratch ? cv.reserve((size_t)n * Cn * 8) : 0;
     const size_t off_e0 = init_frames ? 0 : cv.reserve((size_t)n * 2 * W * 4);
     const size_t off_code = init_frames ? 0 : cv.reserve((size_t)n * 4);
+    const size_t off_state = segs.size() > 1 ? cv.reserve((size_t)sp.n_bundles * 2 * nq * 4) : 0;
     if ((rc = ensure_arena(ctx, cv.off))) return rc;
     Buf* all[] = {&b_syn, &b_if, &b_is, &b_cls, &b_csum, &b_lr, &b_chn, &b_chf};
     for (Buf* b : all) bind(*b, ctx);
@@ -392,33 +423,47 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     uint64_t* chain_sum = chs_scratch ? (uint64_t*)(base + off_chs) : out_chain_sum;
     uint32_t* e0 = init_frames ? nullptr : (uint32_t*)(base + off_e0);
     int32_t* code = init_frames ? nullptr : (int32_t*)(base + off_code);
+    uint32_t* state = segs.size() > 1 ? (uint32_t*)(base + off_state) : nullptr;
 
     if ((rc = copy_in(ctx, b_syn, s)) || (rc = copy_in(ctx, b_if, s)) || (rc = copy_in(ctx, b_is, s))) return rc;
     if (!init_frames) CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
-    sp.e0 = e0;
-    sp.e0code = code;
-    sp.init_frames = (const uint32_t*)b_if.dev;
-    sp.init_sum = (const uint64_t*)b_is.dev;
-    sp.chain_sum = chain_sum;
-    sp.chain_n = (int32_t*)b_chn.dev;
-    sp.chain_frames = (uint32_t*)b_chf.dev;
-    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-    if (ctx->timing) {
-        if (!ctx->spare.empty()) {
-            ev = ctx->spare.back();
-            ctx->spare.pop_back();
-        } else {
-            CK(cudaEventCreate(&ev.first));
-            CK(cudaEventCreate(&ev.second));
+
+    for (size_t i = 0; i < segs.size(); ++i) {
+        const bool first = i == 0, last = i + 1 == segs.size();
+        set_temperature(sp, p, segs[i].scale);
+        sp.t_begin = segs[i].t0;
+        sp.t_end = segs[i].t1;
+        sp.burn_in = segs[i].anneal ? segs[i].t1 : B;
+        sp.e0 = first ? e0 : nullptr;
+        sp.e0code = first ? code : nullptr;
+        sp.init_frames = first ? (const uint32_t*)b_if.dev : nullptr;
+        sp.state_in = first ? nullptr : state;
+        sp.state_out = last ? nullptr : state;
+        sp.init_sum = last ? (const uint64_t*)b_is.dev : nullptr;
+        sp.chain_sum = last ? chain_sum : nullptr;
+        sp.chain_n = last ? (int32_t*)b_chn.dev : nullptr;
+        sp.chain_frames = last ? (uint32_t*)b_chf.dev : nullptr;
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (ctx->timing) {
+            if (!ctx->spare.empty()) {
+                ev = ctx->spare.back();
+                ctx->spare.pop_back();
+            } else {
+                CK(cudaEventCreate(&ev.first));
+                CK(cudaEventCreate(&ev.second));
+            }
+            CK(cudaEventRecord(ev.first, s));
         }
-        CK(cudaEventRecord(ev.first, s));
-    }
-    CK(launch_sweep(sp, lam, s));
-    if (ctx->timing) {
-        CK(cudaEventRecord(ev.second, s));
-        ctx->pending.push_back(ev);
+        CK(launch_sweep(sp, lam, s));
+        if (ctx->timing) {
+            CK(cudaEventRecord(ev.second, s));
+            ctx->pending.push_back(ev);
+        }
     }
 
+    uint64_t T[5];
+    double beta_bar;
+    acceptance_table(p, 1.0, T, &beta_bar);
     DecideParams dp;
     dp.n = n;
     dp.K = K;

@@ -115,6 +115,8 @@ struct SweepParams {
     const uint32_t* e0;        // [n][2][W] pure errors
     const int32_t* e0code;     // [n]
     const uint32_t* init_frames;  // [n][C][2][W] or NULL
+    const uint32_t* state_in;     // [n_bundles][2][nq] bit-sliced state from an earlier launch, or NULL
+    uint32_t* state_out;          // [n_bundles][2][nq] state at t_end for a later launch, or NULL
     const uint64_t* init_sum;     // [n][C] or NULL
     uint64_t* chain_sum;       // [n][C] out
     int32_t* chain_n;          // [n][C] out or NULL

@@ -160,7 +160,7 @@ __device__ __forceinline__ void flush_acc(OccAcc& a, int sub, uint32_t valid, ui
         uint64_t n = 0;
 #pragma unroll
         for (int k = 0; k < kFlushPlanes; ++k) n |= (uint64_t)((v[k] >> b) & 1u) << k;
-        sums[ci_of(b)] += n;
+        if (sums) sums[ci_of(b)] += n;
     }
     a.clear();
 }
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
     // Start state: pure error times the logical that gives chain c the class
     // code c / R (bit 0: X-bar on row 0, bit 1: Z-bar on column 0).
     uint32_t lx = 0, lzm = 0;
-    for (int b = 0; b < 32 && !p.init_frames; ++b) {
+    for (int b = 0; b < 32 && !p.init_frames && !p.state_in; ++b) {
         if (!((valid >> b) & 1u)) continue;
         const int k = chain_of(b) / p.R;
         const int l = k ^ p.e0code[syn_of(b)];
@@ -339,9 +339,15 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
         lzm |= (uint32_t)((l >> 1) & 1) << b;
     }
     const int W = p.W;
+    const uint32_t* st_in = p.state_in ? p.state_in + (size_t)(active ? bid : 0) * 2 * nq : nullptr;
     for (int q = sub; q < nq; q += LAM) {
         uint32_t xw = 0, zw = 0;
-        if (p.init_frames) {
+        if (st_in) {
+            if (active) {
+                xw = st_in[q];
+                zw = st_in[nq + q];
+            }
+        } else if (p.init_frames) {
             for (int b = 0; b < 32; ++b) {
                 if (!((valid >> b) & 1u)) continue;
                 const uint32_t* f = p.init_frames + ((size_t)syn_of(b) * p.C + chain_of(b)) * 2 * W;
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
         const int b = sub + j * LAM;
         if (!((valid >> b) & 1u)) continue;
         const size_t ci = ci_of(b);
-        p.chain_sum[ci] = p.init_sum ? p.init_sum[ci] : 0ull;
+        if (p.chain_sum) p.chain_sum[ci] = p.init_sum ? p.init_sum[ci] : 0ull;
     }
     OccAcc occ;
     occ.clear();
@@ -485,6 +491,13 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
     }
 
     flush_acc<LAM>(occ, sub, valid, p.chain_sum, ci_of);
+    if (p.state_out && active) {
+        uint32_t* st = p.state_out + (size_t)bid * 2 * nq;
+        for (int q = sub; q < nq; q += LAM) {
+            st[q] = X[q];
+            st[nq + q] = Z[q];
+        }
+    }
     uint32_t cnt[kCountBits];
     recount<LAM>(X, Z, nq, sub, cnt);
 #pragma unroll

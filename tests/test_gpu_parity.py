@@ -182,7 +182,10 @@ def test_empty_and_invalid(ctx, pkg):
     bad = [dict(L=1), dict(L=32), dict(p=0.0), dict(p=0.8), dict(opts=pkg.Opts(n_classes=3)),
            dict(opts=pkg.Opts(chains_per_class=0)), dict(opts=pkg.Opts(n_sweeps=5, burn_in=6)),
            dict(opts=pkg.Opts(lanes_per_bundle=3)), dict(opts=pkg.Opts(beta_scale=-1.0)),
-           dict(p=0.75, opts=pkg.Opts(beta_scale=float("inf")))]
+           dict(p=0.75, opts=pkg.Opts(beta_scale=float("inf"))),
+           dict(opts=pkg.Opts(n_sweeps=10, burn_in=3, anneal_stages=4, anneal_beta0=0.3)),
+           dict(opts=pkg.Opts(n_sweeps=10, burn_in=8, anneal_stages=4, anneal_beta0=0.0)),
+           dict(opts=pkg.Opts(n_sweeps=10, burn_in=8, anneal_stages=-1))]
     for kw in bad:
         args = dict(L=5, p=0.1, opts=pkg.Opts(n_sweeps=2))
         args.update(kw)
@@ -206,3 +209,41 @@ def test_ler_below_p_at_l7(ctx, pkg):
     torch.cuda.synchronize()
     ler = float((cls != tc).float().mean())
     assert ler < p
+
+
+@pytest.mark.parametrize("L,R,S,a0,burn,sweeps", [(5, 4, 4, 0.3, 40, 80), (9, 16, 3, 0.5, 7, 20), (4, 1, 2, 0.25, 9, 12),
+                                                   (13, 16, 4, 0.3, 8, 10)])
+def test_annealed_decode(ctx, pkg, L, R, S, a0, burn, sweeps):
+    p, n = 0.13, 7
+    syn, _ = _oracle_syndromes(8001 + L, n, L, p)
+    opts = pkg.Opts(chains_per_class=R, n_sweeps=sweeps, burn_in=burn, anneal_stages=S, anneal_beta0=a0)
+    out = ctx.decode_ex(torch.from_numpy(syn).cuda(), L, p, opts, seed=12, id0=3)
+    torch.cuda.synchronize()
+    for i in range(n):
+        ref = O.decode_one(L, p, 4, R, sweeps, 12, 3 + i, syn[i], burn_in=burn, anneal_stages=S, anneal_beta0=a0)
+        _compare_decode(out, ref, i, 4 * R, L)
+
+
+def test_annealed_resume_after_burn_in(ctx, pkg):
+    L, p, R, T, T1, B, S = 7, 0.13, 8, 40, 23, 16, 4
+    syn, _ = _oracle_syndromes(9001, 5, L, p)
+    dsyn = torch.from_numpy(syn).cuda()
+    mk = lambda t: pkg.Opts(chains_per_class=R, n_sweeps=t, burn_in=B, anneal_stages=S, anneal_beta0=0.3)
+    full = ctx.decode_ex(dsyn, L, p, mk(T), seed=4)
+    a = ctx.decode_ex(dsyn, L, p, mk(T1), seed=4)
+    b = ctx.decode_ex(dsyn, L, p, mk(T), seed=4, sweep_begin=T1, init_frames=a["chain_frames"],
+                      init_chain_sum=a["chain_sum"])
+    torch.cuda.synchronize()
+    for k in ("cls", "class_sum", "chain_sum", "chain_n", "chain_frames"):
+        assert (_np(b[k]) == _np(full[k])).all(), k
+
+
+def test_annealed_ler_l13(ctx, pkg):
+    """With the annealed start the L=13 decoder is well below threshold at
+    p = 10% (the paper's threshold for this algorithm is 15-16%)."""
+    L, p, n = 13, 0.10, 2048
+    syn, tc = ctx.gen_syndromes(7000, 0, n, L, p, like=torch.zeros(1, device="cuda"))
+    opts = pkg.Opts(chains_per_class=16, n_sweeps=4000, burn_in=800, anneal_stages=4, anneal_beta0=0.3)
+    cls, _, _ = ctx.decode(syn, L, p, opts, seed=7100)
+    torch.cuda.synchronize()
+    assert float((cls != tc).float().mean()) < 0.02

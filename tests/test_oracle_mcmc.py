@@ -201,3 +201,45 @@ def test_decoder_below_p_at_l7():
     res = O.decode_batch(L, p, K, R, sweeps, 4343, range(n), syn, burn_in=burn)
     fails = sum(d["cls"] != t for d, t in zip(res, tc))
     assert fails / n < p
+
+
+def test_anneal_stages_partition_the_burn_in():
+    for B, S in [(800, 4), (7, 3), (5, 5), (1000, 7)]:
+        stages = [O.anneal_stage(t, B, S) for t in range(B)]
+        assert stages[0] == 0 and stages[-1] == S - 1
+        assert all(b - a in (0, 1) for a, b in zip(stages, stages[1:]))
+        assert O.anneal_stage(B, B, S) == -1
+    assert O.anneal_scale(1.0, 0.3, 0, 4) == 0.3
+    assert abs(O.anneal_scale(2.0, 0.3, 2, 4) - 2.0 * (0.3 + 0.7 * 0.5)) < 1e-15
+
+
+def test_annealed_run_is_the_composition_of_fixed_temperature_runs():
+    """The annealed burn-in is nothing but fixed-beta Metropolis runs (each
+    pinned above) chained through their states, sweep index continuing."""
+    L, p, K, R, S, B, T, a0 = 5, 0.12, 4, 4, 4, 18, 30, 0.3
+    syn, _ = O.gen_syndromes(31, 0, 1, L, p)
+    full = O.run_chains(L, K, R, p, 3, 0, syn[0], 0, T, burn_in=B, anneal_stages=S, anneal_beta0=a0)
+    fr, cs = None, None
+    bounds = [j * B // S for j in range(S + 1)]
+    for j in range(S):
+        o = O.run_chains(L, K, R, p, 3, 0, syn[0], bounds[j], bounds[j + 1], burn_in=bounds[j + 1],
+                         beta_scale=O.anneal_scale(1.0, a0, j, S), frames=fr, chain_sum=cs)
+        fr, cs = (o["frames_x"], o["frames_z"]), o["chain_sum"]
+    o = O.run_chains(L, K, R, p, 3, 0, syn[0], B, T, burn_in=B, frames=fr, chain_sum=cs)
+    assert (o["chain_sum"] == full["chain_sum"]).all()
+    assert (o["frames_x"] == full["frames_x"]).all() and (o["frames_z"] == full["frames_z"]).all()
+    assert (cs == 0).all()
+
+
+def test_annealed_start_lowers_the_logical_error_rate():
+    """Starting near low-energy configurations (Sec. IV) matters: the same
+    sweep budget with the burn-in annealed from 0.3 beta_bar decodes better
+    than with a burn-in at beta_bar, and stays below p at L=7, p=13%."""
+    L, p, K, R, sweeps, burn = 7, 0.13, 4, 4, 600, 200
+    n = 240
+    syn, tc = O.gen_syndromes(4242, 0, n, L, p)
+    plain = O.decode_batch(L, p, K, R, sweeps, 4343, range(n), syn, burn_in=burn)
+    ann = O.decode_batch(L, p, K, R, sweeps, 4343, range(n), syn, burn_in=burn, anneal_stages=4, anneal_beta0=0.3)
+    f_plain = sum(d["cls"] != t for d, t in zip(plain, tc)) / n
+    f_ann = sum(d["cls"] != t for d, t in zip(ann, tc)) / n
+    assert f_ann < p and f_ann < f_plain
