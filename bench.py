@@ -180,6 +180,7 @@ def main():
     import torch
     import paper_1302_2669_gb300 as pkg
     from paper_1302_2669_gb300 import build as b
+    from paper_1302_2669_gb300 import shard
 
     rank, world, local = dist_env()
     if world > 1:
@@ -194,7 +195,7 @@ def main():
     burn = min(BURN_IN, sweeps)
     opts = pkg.Opts(n_classes=K_CLASSES, chains_per_class=R_CHAINS, n_sweeps=sweeps, burn_in=burn,
                     anneal_stages=ANNEAL_STAGES if burn >= ANNEAL_STAGES else 0, anneal_beta0=ANNEAL_BETA0)
-    id0 = rank * n
+    id0 = shard.weak_id0(rank, n)
     like = torch.zeros(1, device=dev)
     syn, tcls = [], []
     for p, s in zip(PS, SYN_SEEDS):
@@ -242,11 +243,9 @@ def main():
     clk = clocks.stop()
     sweep_ms, sweep_launches = ctx.sweep_time()
     ctx.set_timing(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t)
+    total_ms = shard.max_value(sum(step_ms), device=dev)
+    merged = shard.sum_counts([v for p in PS for v in fails[p]], device=dev)
+    fails = {p: merged[2 * i:2 * i + 2] for i, p in enumerate(PS)}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -262,11 +261,7 @@ def main():
             i = j % 4
             ctx.decode(hsyn[i], L, PS[i], opts, seed=SYN_SEEDS[i] + 100, id0=id0, out_class=hcls, out_class_sum=hsum,
                        out_log_ratio=hlr)
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t)
+        e2e_s = shard.max_value(time.perf_counter() - t0, device=dev)
         e2e = {"value": world * n * args.steps / e2e_s, "unit": "syndromes/s", "h2d_bytes_per_step": n * NSTAB,
                "d2h_bytes_per_step": n * (4 + 8 * K_CLASSES + 8 * K_CLASSES)}
 

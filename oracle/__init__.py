@@ -26,7 +26,8 @@ def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``liboracle.so`` with plain gcc -O2."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp,
+                               _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,6 +72,9 @@ def lib():
         L.orc_anneal_scale.restype = C.c_double
         L.orc_anneal_stage.argtypes = [C.c_uint32, C.c_uint32, C.c_int]
         L.orc_exact_histogram.argtypes = [C.c_int, u8p, u64p]
+        L.orc_simpson_integral.argtypes = [C.c_int, C.c_int, f64p, C.c_double, f64p]
+        L.orc_decode_ti.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double,
+                                    C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32, u8p, f64p, f64p]
         _lib = L
     return _lib
 
@@ -307,3 +311,27 @@ def decode_batch(L, p, K, R, n_sweeps, seed, ids, syns, burn_in=0, beta_scale=1.
         return [_decode_worker(j) for j in jobs]
     with mp.get_context("spawn").Pool(processes or os.cpu_count()) as pool:
         return pool.map(_decode_worker, jobs, chunksize=1)
+
+
+def simpson_integral(mean, beta_bar):
+    """Composite Simpson integral over the grid beta_j = j beta_bar/(N-1) of
+    mean[k][j] (Eq. 6); returns I[k]."""
+    mean = np.ascontiguousarray(mean, np.float64)
+    K, N = mean.shape
+    I = np.zeros(K, np.float64)
+    if lib().orc_simpson_integral(K, N, mean, beta_bar, I) != 0:
+        raise ValueError("Simpson needs an odd number >= 3 of grid points")
+    return I
+
+
+def decode_ti(L, p, K, R, n_sweeps, seed, ident, syn, n_beta=21, burn_in=0, beta_scale=1.0, anneal_stages=0,
+              anneal_beta0=1.0):
+    """Thermodynamic-integration decode (Eq. 6, Simpson over n_beta points):
+    returns (class, log Z_k - max log Z, means [K][n_beta])."""
+    mean = np.zeros((K, n_beta), np.float64)
+    lz = np.zeros(K, np.float64)
+    k = lib().orc_decode_ti(L, p, K, R, n_sweeps, burn_in, beta_scale, anneal_stages, anneal_beta0, n_beta, seed,
+                            ident, np.ascontiguousarray(syn, np.uint8), mean, lz)
+    if k < 0:
+        raise ValueError("bad TI arguments")
+    return k, lz, mean

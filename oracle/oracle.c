@@ -554,3 +554,73 @@ int orc_exact_histogram(int L, const uint8_t* syn, uint64_t* hist /* [4][nq+1] *
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Thermodynamic integration (Eq. 6): log Z_E(beta_bar) = -int_0^beta_bar    */
+/* <n>_{beta,E} d beta + n_stab log 2.  The integral is taken with the       */
+/* composite Simpson rule (Sec. IV) on the equidistant grid                  */
+/* beta_j = j beta_bar / (N-1), j = 0..N-1 (N odd; Sec. IV.A uses N = 21),   */
+/* with <n> at beta = 0 equal to 3/4 n_qubits (Sec. IV.A).  mean[k*N + j] is */
+/* <n>_{beta_j, k}; I[k] receives the integral of class k.                   */
+/* ------------------------------------------------------------------------ */
+int orc_simpson_integral(int K, int N, const double* mean, double beta_bar, double* I)
+{
+    if (N < 3 || N % 2 == 0) return -1;
+    double h = beta_bar / (double)(N - 1);
+    for (int k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) {
+            double w = (j == 0 || j == N - 1) ? 1.0 : (j % 2 == 1 ? 4.0 : 2.0);
+            double term = w * mean[k * N + j];
+            acc = acc + term;
+        }
+        I[k] = acc * (h / 3.0);
+    }
+    return 0;
+}
+
+/* TI decode of one syndrome: chains at beta_j = beta* j/(N-1), j = 1..N-1
+ * (seed + j for the randomness of grid point j, the same options otherwise,
+ * the burn-in annealing scaled with beta_j), <n> at j = 0 set to 3/4 n_q;
+ * class = argmin_k I_k (argmax log Z_k, lowest k on ties);
+ * log_z[k] = -(I_k - min_k I_k).  mean_out[k*N + j] receives the means. */
+int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_scale,
+                  int anneal_stages, double anneal_beta0, int N, uint64_t seed, uint32_t id,
+                  const uint8_t* syn, double* mean_out, double* log_z)
+{
+    int nq = orc_nq(L), C = K * R;
+    if (N < 3 || N % 2 == 0 || N > 129 || K > 64) return -1;
+    uint64_t samples = n_sweeps > burn_in ? (uint64_t)4 * (uint64_t)R * (n_sweeps - burn_in) : 0;
+    if (samples == 0) return -1;
+    uint8_t* fx = malloc((size_t)C * nq);
+    uint8_t* fz = malloc((size_t)C * nq);
+    uint64_t* cs = malloc(sizeof(uint64_t) * C);
+    double* mean = malloc(sizeof(double) * K * N);
+    for (int k = 0; k < K; ++k) mean[k * N] = 0.75 * (double)nq;
+    for (int j = 1; j < N; ++j) {
+        double bs = beta_scale * (double)j / (double)(N - 1);
+        orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, bs, seed + (uint64_t)j, id, anneal_stages, anneal_beta0};
+        memset(cs, 0, sizeof(uint64_t) * C);
+        orc_run_chains(&a, syn, 1, fx, fz, cs, NULL, NULL, NULL);
+        for (int k = 0; k < K; ++k) {
+            uint64_t S = 0;
+            for (int r = 0; r < R; ++r) S += cs[k * R + r];
+            mean[k * N + j] = (double)S / (double)samples;
+        }
+    }
+    double beta_bar;
+    uint64_t T[5];
+    orc_thresholds(p, 1.0, T, &beta_bar);
+    double I[64];
+    orc_simpson_integral(K, N, mean, beta_scale * beta_bar, I);
+    int best = 0;
+    for (int k = 1; k < K; ++k)
+        if (I[k] < I[best]) best = k;
+    for (int k = 0; k < K; ++k) log_z[k] = -(I[k] - I[best]);
+    if (mean_out) memcpy(mean_out, mean, sizeof(double) * K * N);
+    free(fx);
+    free(fz);
+    free(cs);
+    free(mean);
+    return best;
+}

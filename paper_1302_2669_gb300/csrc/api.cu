@@ -193,6 +193,126 @@ int pick_lanes(int L, int requested, int* lam_out) {
     return SURFMCMC_OK;
 }
 
+
+int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
+    if (!(p > 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside (0, 0.75]", p);
+    if (o.n_classes != 4) return fail(ctx, SURFMCMC_EINVAL, "n_classes must be 4 (planar code)");
+    if (o.chains_per_class < 1 || 4 * o.chains_per_class > 1024)
+        return fail(ctx, SURFMCMC_EINVAL, "chains_per_class=%d outside 1..256", o.chains_per_class);
+    if (o.burn_in > o.n_sweeps) return fail(ctx, SURFMCMC_EINVAL, "burn_in > n_sweeps");
+    if (!(o.beta_scale >= 0.0)) return fail(ctx, SURFMCMC_EINVAL, "beta_scale must be >= 0");
+    if (std::isinf(o.beta_scale) && p == 0.75)
+        return fail(ctx, SURFMCMC_EINVAL, "infinite beta_scale needs p < 0.75 (beta_bar = 0)");
+    if (o.anneal_stages < 0 || o.anneal_stages > 64)
+        return fail(ctx, SURFMCMC_EINVAL, "anneal_stages=%d outside 0..64", o.anneal_stages);
+    if (o.anneal_stages > 0 && ((uint32_t)o.anneal_stages > o.burn_in || !(o.anneal_beta0 > 0.0 && o.anneal_beta0 <= 1.0)))
+        return fail(ctx, SURFMCMC_EINVAL, "annealing needs anneal_stages <= burn_in and 0 < anneal_beta0 <= 1");
+    return SURFMCMC_OK;
+}
+
+// Geometry and bundle layout of a run: C chains per syndrome, plane width G,
+// bundles of 32 chains (G = 32: C/32 bundles per syndrome; G < 32: 32/G
+// syndromes per bundle).
+void init_geometry(SweepParams& sp, int L, int Cn, int R, int64_t n, uint32_t id0) {
+    memset(&sp, 0, sizeof sp);
+    int G = 1;
+    while (G < Cn && G < 32) G *= 2;
+    sp.L = L;
+    sp.nq = n_qubits(L);
+    sp.W = n_words(L);
+    sp.nc = L * (L - 1) / 2;
+    sp.C = Cn;
+    sp.R = R;
+    sp.G = G;
+    sp.bps = G == 32 ? (Cn + 31) / 32 : 1;
+    sp.spb = G == 32 ? 1 : 32 / G;
+    sp.n = n;
+    sp.n_bundles = G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
+    sp.id0 = id0;
+    sp.ids = nullptr;
+}
+
+// Launch segments of one run: the annealing stages of the burn-in (no
+// sampling), then the rest of the run at beta*.  Sweep indices are absolute.
+struct Segment {
+    uint32_t t0, t1;
+    double scale;
+    bool anneal;
+};
+
+std::vector<Segment> plan_segments(const surfmcmc_opts& o, double beta_scale, uint32_t sweep_begin) {
+    std::vector<Segment> segs;
+    const uint32_t B = o.burn_in;
+    const int S = o.anneal_stages;
+    for (int j = 0; j < S; ++j) {
+        const uint32_t lo = (uint32_t)((uint64_t)j * B / (uint64_t)S);
+        const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * B / (uint64_t)S);
+        const uint32_t a = lo > sweep_begin ? lo : sweep_begin;
+        if (a < hi) segs.push_back({a, hi, anneal_scale(beta_scale, o.anneal_beta0, j, S), true});
+    }
+    const uint32_t main0 = S > 0 && B > sweep_begin ? B : sweep_begin;
+    segs.push_back({main0, o.n_sweeps, beta_scale, false});
+    return segs;
+}
+
+// Where one run reads its start and writes its results.
+struct SweepIO {
+    uint32_t* e0 = nullptr;
+    int32_t* e0code = nullptr;
+    const uint32_t* init_frames = nullptr;
+    const uint64_t* init_sum = nullptr;
+    uint64_t* chain_sum = nullptr;
+    int32_t* chain_n = nullptr;
+    uint32_t* chain_frames = nullptr;
+    uint32_t* state = nullptr;  // bundle state between segments
+};
+
+int record_start(surfmcmc_ctx* ctx, std::pair<cudaEvent_t, cudaEvent_t>* ev, cudaStream_t s) {
+    if (!ctx->timing) return SURFMCMC_OK;
+    if (!ctx->spare.empty()) {
+        *ev = ctx->spare.back();
+        ctx->spare.pop_back();
+    } else {
+        CK(cudaEventCreate(&ev->first));
+        CK(cudaEventCreate(&ev->second));
+    }
+    CK(cudaEventRecord(ev->first, s));
+    return SURFMCMC_OK;
+}
+
+int record_end(surfmcmc_ctx* ctx, std::pair<cudaEvent_t, cudaEvent_t> ev, cudaStream_t s) {
+    if (!ctx->timing) return SURFMCMC_OK;
+    CK(cudaEventRecord(ev.second, s));
+    ctx->pending.push_back(ev);
+    return SURFMCMC_OK;
+}
+
+int run_segments(surfmcmc_ctx* ctx, SweepParams sp, const std::vector<Segment>& segs, uint32_t burn_in, double p,
+                 int lam, const SweepIO& io, cudaStream_t s) {
+    int rc;
+    for (size_t i = 0; i < segs.size(); ++i) {
+        const bool first = i == 0, last = i + 1 == segs.size();
+        set_temperature(sp, p, segs[i].scale);
+        sp.t_begin = segs[i].t0;
+        sp.t_end = segs[i].t1;
+        sp.burn_in = segs[i].anneal ? segs[i].t1 : burn_in;
+        sp.e0 = first ? io.e0 : nullptr;
+        sp.e0code = first ? io.e0code : nullptr;
+        sp.init_frames = first ? io.init_frames : nullptr;
+        sp.state_in = first ? nullptr : io.state;
+        sp.state_out = last ? nullptr : io.state;
+        sp.init_sum = last ? io.init_sum : nullptr;
+        sp.chain_sum = last ? io.chain_sum : nullptr;
+        sp.chain_n = last ? io.chain_n : nullptr;
+        sp.chain_frames = last ? io.chain_frames : nullptr;
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if ((rc = record_start(ctx, &ev, s))) return rc;
+        CK(launch_sweep(sp, lam, s));
+        if ((rc = record_end(ctx, ev, s))) return rc;
+    }
+    return SURFMCMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -337,18 +457,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     surfmcmc_opts o;
     surfmcmc_default_opts(&o);
     if (opts_in) o = *opts_in;
-    if (!(p > 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside (0, 0.75]", p);
-    if (o.n_classes != 4) return fail(ctx, SURFMCMC_EINVAL, "n_classes must be 4 (planar code)");
-    if (o.chains_per_class < 1 || 4 * o.chains_per_class > 1024)
-        return fail(ctx, SURFMCMC_EINVAL, "chains_per_class=%d outside 1..256", o.chains_per_class);
-    if (o.burn_in > o.n_sweeps) return fail(ctx, SURFMCMC_EINVAL, "burn_in > n_sweeps");
-    if (!(o.beta_scale >= 0.0)) return fail(ctx, SURFMCMC_EINVAL, "beta_scale must be >= 0");
-    if (std::isinf(o.beta_scale) && p == 0.75)
-        return fail(ctx, SURFMCMC_EINVAL, "infinite beta_scale needs p < 0.75 (beta_bar = 0)");
-    if (o.anneal_stages < 0 || o.anneal_stages > 64)
-        return fail(ctx, SURFMCMC_EINVAL, "anneal_stages=%d outside 0..64", o.anneal_stages);
-    if (o.anneal_stages > 0 && ((uint32_t)o.anneal_stages > o.burn_in || !(o.anneal_beta0 > 0.0 && o.anneal_beta0 <= 1.0)))
-        return fail(ctx, SURFMCMC_EINVAL, "annealing needs anneal_stages <= burn_in and 0 < anneal_beta0 <= 1");
+    if ((rc = check_opts(ctx, o, p))) return rc;
     if (sweep_begin > o.n_sweeps) return fail(ctx, SURFMCMC_EINVAL, "sweep_begin > n_sweeps");
     if (!init_frames && sweep_begin != 0)
         return fail(ctx, SURFMCMC_EINVAL, "sweep_begin > 0 needs init_frames");
@@ -367,38 +476,8 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     while (G < Cn && G < 32) G *= 2;
 
     SweepParams sp;
-    memset(&sp, 0, sizeof sp);
-    sp.L = L;
-    sp.nq = nq;
-    sp.W = W;
-    sp.nc = L * (L - 1) / 2;
-    sp.C = Cn;
-    sp.R = R;
-    sp.G = G;
-    sp.bps = G == 32 ? (Cn + 31) / 32 : 1;
-    sp.spb = G == 32 ? 1 : 32 / G;
-    sp.n = n;
-    sp.n_bundles = G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
-    sp.id0 = id0;
-    sp.ids = nullptr;
+    init_geometry(sp, L, Cn, R, n, id0);
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
-
-    // Launch segments: the annealing stages of the burn-in (no sampling),
-    // then the rest of the run at beta*.  Sweep indices are absolute.
-    struct Segment { uint32_t t0, t1; double scale; bool anneal; };
-    std::vector<Segment> segs;
-    const uint32_t B = o.burn_in;
-    const int S = o.anneal_stages;
-    for (int j = 0; j < S; ++j) {
-        const uint32_t lo = (uint32_t)((uint64_t)j * B / (uint64_t)S);
-        const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * B / (uint64_t)S);
-        const uint32_t a = lo > sweep_begin ? lo : sweep_begin;
-        if (a < hi) segs.push_back({a, hi, anneal_scale(o.beta_scale, o.anneal_beta0, j, S), true});
-    }
-    {
-        const uint32_t main0 = S > 0 && B > sweep_begin ? B : sweep_begin;
-        segs.push_back({main0, o.n_sweeps, o.beta_scale, false});
-    }
 
     Carver cv;
     Buf b_syn, b_if, b_is, b_cls, b_csum, b_lr, b_chn, b_chf;
@@ -415,6 +494,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     const size_t off_chs = chs_scratch ? cv.reserve((size_t)n * Cn * 8) : 0;
     const size_t off_e0 = init_frames ? 0 : cv.reserve((size_t)n * 2 * W * 4);
     const size_t off_code = init_frames ? 0 : cv.reserve((size_t)n * 4);
+    const std::vector<Segment> segs = plan_segments(o, o.beta_scale, sweep_begin);
     const size_t off_state = segs.size() > 1 ? cv.reserve((size_t)sp.n_bundles * 2 * nq * 4) : 0;
     if ((rc = ensure_arena(ctx, cv.off))) return rc;
     Buf* all[] = {&b_syn, &b_if, &b_is, &b_cls, &b_csum, &b_lr, &b_chn, &b_chf};
@@ -428,38 +508,16 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     if ((rc = copy_in(ctx, b_syn, s)) || (rc = copy_in(ctx, b_if, s)) || (rc = copy_in(ctx, b_is, s))) return rc;
     if (!init_frames) CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
 
-    for (size_t i = 0; i < segs.size(); ++i) {
-        const bool first = i == 0, last = i + 1 == segs.size();
-        set_temperature(sp, p, segs[i].scale);
-        sp.t_begin = segs[i].t0;
-        sp.t_end = segs[i].t1;
-        sp.burn_in = segs[i].anneal ? segs[i].t1 : B;
-        sp.e0 = first ? e0 : nullptr;
-        sp.e0code = first ? code : nullptr;
-        sp.init_frames = first ? (const uint32_t*)b_if.dev : nullptr;
-        sp.state_in = first ? nullptr : state;
-        sp.state_out = last ? nullptr : state;
-        sp.init_sum = last ? (const uint64_t*)b_is.dev : nullptr;
-        sp.chain_sum = last ? chain_sum : nullptr;
-        sp.chain_n = last ? (int32_t*)b_chn.dev : nullptr;
-        sp.chain_frames = last ? (uint32_t*)b_chf.dev : nullptr;
-        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-        if (ctx->timing) {
-            if (!ctx->spare.empty()) {
-                ev = ctx->spare.back();
-                ctx->spare.pop_back();
-            } else {
-                CK(cudaEventCreate(&ev.first));
-                CK(cudaEventCreate(&ev.second));
-            }
-            CK(cudaEventRecord(ev.first, s));
-        }
-        CK(launch_sweep(sp, lam, s));
-        if (ctx->timing) {
-            CK(cudaEventRecord(ev.second, s));
-            ctx->pending.push_back(ev);
-        }
-    }
+    SweepIO io;
+    io.e0 = e0;
+    io.e0code = code;
+    io.init_frames = (const uint32_t*)b_if.dev;
+    io.init_sum = (const uint64_t*)b_is.dev;
+    io.chain_sum = chain_sum;
+    io.chain_n = (int32_t*)b_chn.dev;
+    io.chain_frames = (uint32_t*)b_chf.dev;
+    io.state = state;
+    if ((rc = run_segments(ctx, sp, segs, o.burn_in, p, lam, io, s))) return rc;
 
     uint64_t T[5];
     double beta_bar;
@@ -483,6 +541,88 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     }
     if (out_chain_sum && chs_scratch) {
         CK(cudaMemcpyAsync(out_chain_sum, chain_sum, (size_t)n * Cn * 8, cudaMemcpyDeviceToHost, s));
+        any_host = true;
+    }
+    if (!stream || any_host) CK(cudaStreamSynchronize(s));
+    return SURFMCMC_OK;
+}
+
+
+int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L, double p,
+                       const surfmcmc_opts* opts_in, int32_t n_beta, uint64_t seed, uint32_t id0, int32_t* out_class,
+                       double* out_log_z, double* out_mean, void* stream) {
+    int rc = check_common(ctx, n, L, id0);
+    if (rc) return rc;
+    surfmcmc_opts o;
+    surfmcmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if ((rc = check_opts(ctx, o, p))) return rc;
+    if (!(o.beta_scale < INFINITY)) return fail(ctx, SURFMCMC_EINVAL, "thermodynamic integration needs finite beta*");
+    if (n_beta < 3 || n_beta > 129 || n_beta % 2 == 0)
+        return fail(ctx, SURFMCMC_EINVAL, "n_beta=%d must be odd in 3..129", n_beta);
+    if (o.n_sweeps <= o.burn_in) return fail(ctx, SURFMCMC_EINVAL, "no sampled sweeps");
+    if (n > 0 && (!syndromes || !out_class)) return fail(ctx, SURFMCMC_EINVAL, "NULL syndromes or out_class");
+    int lam = 0;
+    if (pick_lanes(L, o.lanes_per_bundle, &lam))
+        return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
+    if (n == 0) return SURFMCMC_OK;
+    ctx->last_error.clear();
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = 4, R = o.chains_per_class, Cn = K * R, N = n_beta;
+    SweepParams sp;
+    init_geometry(sp, L, Cn, R, n, id0);
+    const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
+
+    Carver cv;
+    Buf b_syn, b_cls, b_lz, b_mean;
+    plan(b_syn, (void*)syndromes, (size_t)n * n_stabs(L), cv);
+    plan(b_cls, out_class, (size_t)n * 4, cv);
+    plan(b_lz, out_log_z, out_log_z ? (size_t)n * K * 8 : 0, cv);
+    const bool mean_scratch = !out_mean || !is_device_ptr(out_mean);
+    const size_t off_mean = mean_scratch ? cv.reserve((size_t)n * K * N * 8) : 0;
+    const size_t off_chs = cv.reserve((size_t)n * Cn * 8);
+    const size_t off_e0 = cv.reserve((size_t)n * 2 * sp.W * 4);
+    const size_t off_code = cv.reserve((size_t)n * 4);
+    const size_t off_state = segs0.size() > 1 ? cv.reserve((size_t)sp.n_bundles * 2 * sp.nq * 4) : 0;
+    if ((rc = ensure_arena(ctx, cv.off))) return rc;
+    for (Buf* b : {&b_syn, &b_cls, &b_lz}) bind(*b, ctx);
+    char* base = (char*)ctx->arena;
+    double* mean = mean_scratch ? (double*)(base + off_mean) : out_mean;
+    uint64_t* chain_sum = (uint64_t*)(base + off_chs);
+    uint32_t* e0 = (uint32_t*)(base + off_e0);
+    int32_t* code = (int32_t*)(base + off_code);
+    uint32_t* state = segs0.size() > 1 ? (uint32_t*)(base + off_state) : nullptr;
+
+    if ((rc = copy_in(ctx, b_syn, s))) return rc;
+    CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
+    const uint64_t samples = (uint64_t)4 * R * (o.n_sweeps - o.burn_in);
+    for (int j = 1; j < N; ++j) {
+        // grid point j: beta_j = beta* j/(N-1), randomness keyed by seed + j
+        const double bs = o.beta_scale * (double)j / (double)(N - 1);
+        const uint64_t sj = seed + (uint64_t)j;
+        make_round_keys((uint32_t)sj, (uint32_t)(sj >> 32), &sp.rk);
+        SweepIO io;
+        io.e0 = e0;
+        io.e0code = code;
+        io.chain_sum = chain_sum;
+        io.state = state;
+        if ((rc = run_segments(ctx, sp, plan_segments(o, bs, 0), o.burn_in, p, lam, io, s))) return rc;
+        CK(launch_class_means(n, K, R, N, j, samples, chain_sum, mean, s));
+    }
+    uint64_t T[5];
+    double beta_bar;
+    acceptance_table(p, 1.0, T, &beta_bar);
+    const double h = (o.beta_scale * beta_bar) / (double)(N - 1);
+    CK(launch_ti_decide(n, K, N, 0.75 * (double)sp.nq, h / 3.0, mean, (int32_t*)b_cls.dev, (double*)b_lz.dev, s));
+
+    bool any_host = false;
+    for (Buf* b : {&b_cls, &b_lz}) {
+        if ((rc = copy_out(ctx, *b, s))) return rc;
+        any_host |= b->staged;
+    }
+    if (out_mean && mean_scratch) {
+        CK(cudaMemcpyAsync(out_mean, mean, (size_t)n * K * N * 8, cudaMemcpyDeviceToHost, s));
         any_host = true;
     }
     if (!stream || any_host) CK(cudaStreamSynchronize(s));

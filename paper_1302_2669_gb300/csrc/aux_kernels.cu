@@ -129,6 +129,60 @@ __global__ void decide_kernel(DecideParams p) {
         }
 }
 
+// <n>_{beta_j,k} of every syndrome from the chain sums of the run at grid
+// point j: mean[i][k][j] = S_k / samples.
+__global__ void class_means_kernel(long long n, int K, int R, int N, int j, uint64_t samples,
+                                   const uint64_t* chain_sum, double* mean) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < K; ++k) {
+        uint64_t S = 0;
+        for (int r = 0; r < R; ++r) S += chain_sum[(i * K + k) * R + r];
+        mean[(i * K + k) * N + j] = (double)S / (double)samples;
+    }
+}
+
+// Eq. 6 by the composite Simpson rule over the N grid points (<n> at beta = 0
+// is 3/4 n_q, Sec. IV.A): I_k = h/3 sum_j w_j <n>_{beta_j,k}, w = 1 4 2 .. 4 1;
+// the class with the smallest I_k (largest Z_k) wins, lowest k on ties;
+// log_z[k] = -(I_k - I_best).  Explicit round-to-nearest operations keep the
+// summation order and rounding of the plain definition.
+__global__ void ti_decide_kernel(long long n, int K, int N, double mean0, double h3, double* mean,
+                                 int32_t* out_class, double* out_log_z) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double I[4];
+    int best = 0;
+    for (int k = 0; k < K; ++k) {
+        double* m = mean + (i * K + k) * N;
+        m[0] = mean0;
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) {
+            const double w = (j == 0 || j == N - 1) ? 1.0 : ((j & 1) ? 4.0 : 2.0);
+            acc = __dadd_rn(acc, __dmul_rn(w, m[j]));
+        }
+        I[k] = __dmul_rn(acc, h3);
+        if (I[k] < I[best]) best = k;
+    }
+    out_class[i] = best;
+    if (out_log_z)
+        for (int k = 0; k < K; ++k) out_log_z[i * K + k] = -__dsub_rn(I[k], I[best]);
+}
+
+cudaError_t launch_class_means(long long n, int K, int R, int N, int j, uint64_t samples, const uint64_t* chain_sum,
+                               double* mean, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    class_means_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, K, R, N, j, samples, chain_sum, mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ti_decide(long long n, int K, int N, double mean0, double h3, double* mean, int32_t* out_class,
+                             double* out_log_z, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    ti_decide_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, K, N, mean0, h3, mean, out_class, out_log_z);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p, uint8_t* syn,
                                  int32_t* true_class, cudaStream_t s) {
     if (n == 0) return cudaSuccess;

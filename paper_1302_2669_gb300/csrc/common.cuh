@@ -142,5 +142,9 @@ cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L
 cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
                                 cudaStream_t s);
 cudaError_t launch_decide(const DecideParams& p, cudaStream_t s);
+cudaError_t launch_class_means(long long n, int K, int R, int N, int j, uint64_t samples, const uint64_t* chain_sum,
+                               double* mean, cudaStream_t s);
+cudaError_t launch_ti_decide(long long n, int K, int N, double mean0, double h3, double* mean, int32_t* out_class,
+                             double* out_log_z, cudaStream_t s);
 
 }  // namespace surfmcmc
