@@ -181,6 +181,24 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
                        uint64_t* out_class_sum, double* out_log_ratio, uint64_t* out_chain_sum,
                        int32_t* out_chain_n, uint32_t* out_chain_frames, void* stream);
 
+/* Thermodynamic integration (Eq. 6: log Z_E(beta) = -int_0^beta <n>_{b,E} db
+ * + n_stab log 2; Sec. IV: the integral by Simpson's rule; Sec. IV.A: 21
+ * equidistant temperatures).  For grid point j = 1..n_beta-1 the chains run
+ * at beta_j = beta* j/(n_beta-1) with the options of surfmcmc_decode (burn-in
+ * annealing scaled to beta_j) and randomness key seed + j; <n> at beta = 0 is
+ * 3/4 n_q (Sec. IV.A).  I_k = h/3 sum_j w_j <n>_{beta_j,k} (w = 1,4,2,..,4,1,
+ * h = beta* / (n_beta-1)) in double precision, summed in order j = 0..n_beta-1.
+ *   n_beta        odd, 3..129 (21 in the paper).
+ *   out_class     [n] int32 out: argmin_k I_k (= argmax Z_k), lowest on ties.
+ *   out_log_z     [n][4] double out (may be NULL): log Z_k - max_k log Z_k
+ *                 = -(I_k - min_k I_k).
+ *   out_mean      [n][4][n_beta] double out (may be NULL): <n>_{beta_j,k}.
+ * EINVAL as for surfmcmc_decode, or for an even/out-of-range n_beta, an
+ * infinite beta*, or no sampled sweeps. */
+int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L, double p,
+                       const surfmcmc_opts* opts, int32_t n_beta, uint64_t seed, uint32_t id0, int32_t* out_class,
+                       double* out_log_z, double* out_mean, void* stream);
+
 /* Instrumentation (the paper has no counterpart): with enable != 0 every
  * later decode call records a pair of CUDA events on its stream around its
  * sweep kernel.  surfmcmc_sweep_time waits for the recorded events, returns

@@ -58,7 +58,7 @@ class Opts:
 EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surfmcmc_strerror",
            "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_start_frames", "surfmcmc_decode",
            "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time", "surfmcmc_noalloc_scratch_needed",
-           "surfmcmc_decode_noalloc")
+           "surfmcmc_decode_noalloc", "surfmcmc_decode_ti")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -88,6 +88,7 @@ def lib():
         L.surfmcmc_noalloc_scratch_needed.argtypes = [i64, i32, i32]
         L.surfmcmc_noalloc_scratch_needed.restype = C.c_size_t
         L.surfmcmc_decode_noalloc.argtypes = [vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
+        L.surfmcmc_decode_ti.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), i32, u64, u32, vp, vp, vp, vp]
         L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
         L.surfmcmc_sweep_time.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         _lib = L
@@ -228,6 +229,19 @@ class Context:
             _ptr(init_chain_sum), _ptr(out["cls"]), _ptr(out["class_sum"]), _ptr(out["log_ratio"]),
             _ptr(out["chain_sum"]), _ptr(out["chain_n"]), _ptr(out["chain_frames"]), st))
         return out
+
+    def decode_ti(self, syndromes, L, p, opts: Opts | None = None, n_beta=21, seed=0, id0=0, stream=None):
+        """surfmcmc_decode_ti; returns (class [n], log_z [n][4], mean [n][4][n_beta])."""
+        opts = opts or Opts()
+        n = syndromes.shape[0]
+        cls = _empty(syndromes, (n,), np.int32)
+        lz = _empty(syndromes, (n, 4), np.float64)
+        mean = _empty(syndromes, (n, 4, n_beta), np.float64)
+        st = stream if stream is not None else _stream_of(syndromes, cls)
+        o = opts.c()
+        self._check(lib().surfmcmc_decode_ti(self._h, _ptr(syndromes), n, L, p, C.byref(o), n_beta, seed, id0,
+                                             _ptr(cls), _ptr(lz), _ptr(mean), st))
+        return cls, lz, mean
 
     def set_timing(self, enable: bool):
         """surfmcmc_set_timing: record CUDA events around every sweep kernel."""

@@ -575,7 +575,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
 
     Carver cv;
-    Buf b_syn, b_cls, b_lz, b_mean;
+    Buf b_syn, b_cls, b_lz;
     plan(b_syn, (void*)syndromes, (size_t)n * n_stabs(L), cv);
     plan(b_cls, out_class, (size_t)n * 4, cv);
     plan(b_lz, out_log_z, out_log_z ? (size_t)n * K * 8 : 0, cv);

@@ -247,3 +247,20 @@ def test_annealed_ler_l13(ctx, pkg):
     cls, _, _ = ctx.decode(syn, L, p, opts, seed=7100)
     torch.cuda.synchronize()
     assert float((cls != tc).float().mean()) < 0.02
+
+
+@pytest.mark.parametrize("L,R,nb,anneal", [(3, 8, 21, False), (5, 4, 7, True), (9, 16, 5, False)])
+def test_decode_ti(ctx, pkg, L, R, nb, anneal):
+    """Thermodynamic integration (Eq. 6, Simpson) against the oracle, bit for bit."""
+    p, n, sweeps, burn = 0.14, 5, 24, 8
+    syn, _ = _oracle_syndromes(1201 + L, n, L, p)
+    kw = dict(anneal_stages=2, anneal_beta0=0.5) if anneal else {}
+    opts = pkg.Opts(chains_per_class=R, n_sweeps=sweeps, burn_in=burn, **kw)
+    cls, lz, mean = ctx.decode_ti(torch.from_numpy(syn).cuda(), L, p, opts, n_beta=nb, seed=55, id0=7)
+    torch.cuda.synchronize()
+    cls, lz, mean = _np(cls), _np(lz), _np(mean)
+    for i in range(n):
+        k, rlz, rmean = O.decode_ti(L, p, 4, R, sweeps, 55, 7 + i, syn[i], n_beta=nb, burn_in=burn, **kw)
+        assert cls[i] == k
+        assert (mean[i] == rmean).all()
+        assert (lz[i] == rlz).all()
