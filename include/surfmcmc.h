@@ -60,6 +60,7 @@ extern "C" {
 #define SURFMCMC_MAX_L 31       /* largest code size accepted */
 
 typedef struct surfmcmc_ctx surfmcmc_ctx;
+typedef struct surfmcmc_plan surfmcmc_plan;
 
 /* Decoder options.
  *   n_classes        number of equivalence classes; must be 4 (planar code,
@@ -180,6 +181,42 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
                        const uint32_t* init_frames, const uint64_t* init_chain_sum, int32_t* out_class,
                        uint64_t* out_class_sum, double* out_log_ratio, uint64_t* out_chain_sum,
                        int32_t* out_chain_n, uint32_t* out_chain_frames, void* stream);
+
+/* Ragged batches: syndromes of different code sizes (and sweep counts) in one
+ * call, with the algorithm of surfmcmc_decode applied to every item; item i
+ * gives exactly what surfmcmc_decode gives for it alone (same L_i, sweeps,
+ * id), since the randomness is keyed by the syndrome id.
+ *   syndromes     concatenated rows in item order, item i has n_stab(L_i)
+ *                 bytes (layout as for surfmcmc_decode).
+ *   Ls            [n] int32 code sizes (host or device).
+ *   n_sweeps      [n] uint32 sweeps per item (host or device), or NULL for
+ *                 opts->n_sweeps; item i's burn-in is
+ *                 floor(n_sweeps_i * opts->burn_in / opts->n_sweeps) and its
+ *                 annealing stages are those of opts.
+ *   ids           [n] uint32 syndrome ids, or NULL for id0 + i.
+ *   out_*         as for surfmcmc_decode, in item order.
+ * Items are grouped by (L, n_sweeps); one call takes at most 8 distinct
+ * groups.  All groups run in the same persistent kernel launches (one per
+ * annealing stage plus one), largest work first.  EINVAL: bad sizes, more than
+ * 8 groups, a burn-in shorter than the annealing stages, or as for
+ * surfmcmc_decode. */
+int surfmcmc_decode_ragged(surfmcmc_ctx* ctx, const uint8_t* syndromes, const int32_t* Ls, const uint32_t* n_sweeps,
+                           int64_t n, double p, const surfmcmc_opts* opts, uint64_t seed, const uint32_t* ids,
+                           uint32_t id0, int32_t* out_class, uint64_t* out_class_sum, double* out_log_ratio,
+                           void* stream);
+
+/* A captured ragged batch: the device work of surfmcmc_decode_ragged for a
+ * fixed shape (Ls, n_sweeps, options, seed) and fixed DEVICE buffers is
+ * recorded once as a CUDA graph; every surfmcmc_plan_launch replays it on
+ * the current contents of those buffers (refill syndromes and ids between
+ * launches).  The plan owns its scratch (allocated at creation) and must not
+ * outlive ctx.  Launches of one plan must not overlap on the GPU. */
+int surfmcmc_ragged_plan_create(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* n_sweeps, int64_t n, double p,
+                                const surfmcmc_opts* opts, uint64_t seed, const uint8_t* syndromes,
+                                const uint32_t* ids, uint32_t id0, int32_t* out_class, uint64_t* out_class_sum,
+                                double* out_log_ratio, surfmcmc_plan** plan);
+int surfmcmc_plan_launch(surfmcmc_plan* plan, void* stream);
+void surfmcmc_plan_destroy(surfmcmc_plan* plan);
 
 /* Thermodynamic integration (Eq. 6: log Z_E(beta) = -int_0^beta <n>_{b,E} db
  * + n_stab log 2; Sec. IV: the integral by Simpson's rule; Sec. IV.A: 21

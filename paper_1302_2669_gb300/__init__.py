@@ -58,7 +58,8 @@ class Opts:
 EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surfmcmc_strerror",
            "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_start_frames", "surfmcmc_decode",
            "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time", "surfmcmc_noalloc_scratch_needed",
-           "surfmcmc_decode_noalloc", "surfmcmc_decode_ti")
+           "surfmcmc_decode_noalloc", "surfmcmc_decode_ti", "surfmcmc_decode_ragged", "surfmcmc_ragged_plan_create",
+           "surfmcmc_plan_launch", "surfmcmc_plan_destroy")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -89,6 +90,12 @@ def lib():
         L.surfmcmc_noalloc_scratch_needed.restype = C.c_size_t
         L.surfmcmc_decode_noalloc.argtypes = [vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
         L.surfmcmc_decode_ti.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), i32, u64, u32, vp, vp, vp, vp]
+        L.surfmcmc_decode_ragged.argtypes = [vp, vp, vp, vp, i64, dbl, C.POINTER(_Opts), u64, vp, u32, vp, vp, vp, vp]
+        L.surfmcmc_ragged_plan_create.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(_Opts), u64, vp, vp, u32, vp, vp, vp,
+                                                  C.POINTER(vp)]
+        L.surfmcmc_plan_launch.argtypes = [vp, vp]
+        L.surfmcmc_plan_destroy.argtypes = [vp]
+        L.surfmcmc_plan_destroy.restype = None
         L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
         L.surfmcmc_sweep_time.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         _lib = L
@@ -243,6 +250,20 @@ class Context:
                                              _ptr(cls), _ptr(lz), _ptr(mean), st))
         return cls, lz, mean
 
+    def decode_ragged(self, syndromes, Ls, p, opts: Opts | None = None, n_sweeps=None, seed=0, ids=None, id0=0,
+                      stream=None):
+        """surfmcmc_decode_ragged; syndromes = concatenated rows; returns (class, class_sum, log_ratio)."""
+        opts = opts or Opts()
+        n = len(Ls)
+        cls = _empty(syndromes, (n,), np.int32)
+        csum = _empty(syndromes, (n, 4), np.uint64)
+        lr = _empty(syndromes, (n, 4), np.float64)
+        st = stream if stream is not None else _stream_of(syndromes, cls)
+        o = opts.c()
+        self._check(lib().surfmcmc_decode_ragged(self._h, _ptr(syndromes), _ptr(Ls), _ptr(n_sweeps), n, p, C.byref(o),
+                                                 seed, _ptr(ids), id0, _ptr(cls), _ptr(csum), _ptr(lr), st))
+        return cls, csum, lr
+
     def set_timing(self, enable: bool):
         """surfmcmc_set_timing: record CUDA events around every sweep kernel."""
         self._check(lib().surfmcmc_set_timing(self._h, 1 if enable else 0))
@@ -252,3 +273,33 @@ class Context:
         ms, n = C.c_double(), C.c_int64()
         self._check(lib().surfmcmc_sweep_time(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+
+class RaggedPlan:
+    """surfmcmc_ragged_plan_*: a ragged batch captured as a CUDA graph over
+    fixed device buffers; launch() replays it on their current contents."""
+
+    def __init__(self, ctx: Context, Ls, p, syndromes, out_class, out_class_sum=None, out_log_ratio=None,
+                 opts: Opts | None = None, n_sweeps=None, seed=0, ids=None, id0=0):
+        self._ctx = ctx
+        self._h = C.c_void_p()
+        self._keep = (Ls, n_sweeps, syndromes, ids, out_class, out_class_sum, out_log_ratio)
+        o = (opts or Opts()).c()
+        ctx._check(lib().surfmcmc_ragged_plan_create(ctx._h, _ptr(Ls), _ptr(n_sweeps), len(Ls), p, C.byref(o), seed,
+                                                     _ptr(syndromes), _ptr(ids), id0, _ptr(out_class),
+                                                     _ptr(out_class_sum), _ptr(out_log_ratio), C.byref(self._h)))
+
+    def launch(self, stream=None):
+        st = stream if stream is not None else _stream_of(self._keep[2])
+        self._ctx._check(lib().surfmcmc_plan_launch(self._h, st))
+
+    def close(self):
+        if self._h:
+            lib().surfmcmc_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

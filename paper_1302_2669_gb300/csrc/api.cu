@@ -5,6 +5,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -210,49 +212,75 @@ int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
     return SURFMCMC_OK;
 }
 
-// Geometry and bundle layout of a run: C chains per syndrome, plane width G,
-// bundles of 32 chains (G = 32: C/32 bundles per syndrome; G < 32: 32/G
-// syndromes per bundle).
-void init_geometry(SweepParams& sp, int L, int Cn, int R, int64_t n, uint32_t id0) {
+// Chain layout of a run: C chains per syndrome, plane width G, bundles of 32
+// chains (G = 32: C/32 bundles per syndrome; G < 32: 32/G syndromes per
+// bundle).
+void init_chains(SweepParams& sp, int Cn, int R, uint32_t id0) {
     memset(&sp, 0, sizeof sp);
     int G = 1;
     while (G < Cn && G < 32) G *= 2;
-    sp.L = L;
-    sp.nq = n_qubits(L);
-    sp.W = n_words(L);
-    sp.nc = L * (L - 1) / 2;
     sp.C = Cn;
     sp.R = R;
     sp.G = G;
     sp.bps = G == 32 ? (Cn + 31) / 32 : 1;
     sp.spb = G == 32 ? 1 : 32 / G;
-    sp.n = n;
-    sp.n_bundles = G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
     sp.id0 = id0;
     sp.ids = nullptr;
 }
 
-// Launch segments of one run: the annealing stages of the burn-in (no
-// sampling), then the rest of the run at beta*.  Sweep indices are absolute.
+long long bundles_of(const SweepParams& sp, long long n) {
+    return sp.G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
+}
+
+// Appends a group of n syndromes of size L (items item_base ..) whose
+// per-item rows start at the given word offsets.
+void add_group(SweepParams& sp, int L, long long n, long long item_base, long long e0_off, long long frames_off,
+               long long state_off, int lam) {
+    GroupDesc& g = sp.grp[sp.n_groups++];
+    g.L = L;
+    g.nq = n_qubits(L);
+    g.W = n_words(L);
+    g.nc = L * (L - 1) / 2;
+    g.n = n;
+    g.n_bundles = bundles_of(sp, n);
+    g.item_base = item_base;
+    g.e0_off = e0_off;
+    g.frames_off = frames_off;
+    g.state_off = state_off;
+    g.unit_base = sp.total_units;
+    sp.total_units += sweep_units(g.n_bundles, lam);
+    if (g.nq > sp.grp_nq_max) sp.grp_nq_max = g.nq;
+    if (g.nc > sp.grp_nc_max) sp.grp_nc_max = g.nc;
+}
+
+// Launch segments of one run: the S annealing stages of the burn-in (no
+// sampling), then the rest of the run at beta*.  Sweep indices are absolute;
+// with S > 0 there are always S + 1 segments (some may be empty when a run
+// resumes at sweep_begin), so that groups with different sweep counts line up.
 struct Segment {
     uint32_t t0, t1;
     double scale;
     bool anneal;
 };
 
-std::vector<Segment> plan_segments(const surfmcmc_opts& o, double beta_scale, uint32_t sweep_begin) {
+std::vector<Segment> plan_segments(uint32_t n_sweeps, uint32_t B, int S, double a0, double beta_scale,
+                                   uint32_t sweep_begin) {
     std::vector<Segment> segs;
-    const uint32_t B = o.burn_in;
-    const int S = o.anneal_stages;
     for (int j = 0; j < S; ++j) {
         const uint32_t lo = (uint32_t)((uint64_t)j * B / (uint64_t)S);
         const uint32_t hi = (uint32_t)((uint64_t)(j + 1) * B / (uint64_t)S);
-        const uint32_t a = lo > sweep_begin ? lo : sweep_begin;
-        if (a < hi) segs.push_back({a, hi, anneal_scale(beta_scale, o.anneal_beta0, j, S), true});
+        uint32_t a = lo > sweep_begin ? lo : sweep_begin;
+        if (a > hi) a = hi;
+        segs.push_back({a, hi, anneal_scale(beta_scale, a0, j, S), true});
     }
-    const uint32_t main0 = S > 0 && B > sweep_begin ? B : sweep_begin;
-    segs.push_back({main0, o.n_sweeps, beta_scale, false});
+    uint32_t main0 = S > 0 && B > sweep_begin ? B : sweep_begin;
+    if (main0 > n_sweeps) main0 = n_sweeps;
+    segs.push_back({main0, n_sweeps, beta_scale, false});
     return segs;
+}
+
+std::vector<Segment> plan_segments(const surfmcmc_opts& o, double beta_scale, uint32_t sweep_begin) {
+    return plan_segments(o.n_sweeps, o.burn_in, o.anneal_stages, o.anneal_beta0, beta_scale, sweep_begin);
 }
 
 // Where one run reads its start and writes its results.
@@ -264,7 +292,8 @@ struct SweepIO {
     uint64_t* chain_sum = nullptr;
     int32_t* chain_n = nullptr;
     uint32_t* chain_frames = nullptr;
-    uint32_t* state = nullptr;  // bundle state between segments
+    uint32_t* state = nullptr;           // bundle state between segments
+    unsigned int* unit_counter = nullptr;  // work queue of the persistent kernel
 };
 
 int record_start(surfmcmc_ctx* ctx, std::pair<cudaEvent_t, cudaEvent_t>* ev, cudaStream_t s) {
@@ -287,15 +316,21 @@ int record_end(surfmcmc_ctx* ctx, std::pair<cudaEvent_t, cudaEvent_t> ev, cudaSt
     return SURFMCMC_OK;
 }
 
-int run_segments(surfmcmc_ctx* ctx, SweepParams sp, const std::vector<Segment>& segs, uint32_t burn_in, double p,
-                 int lam, const SweepIO& io, cudaStream_t s) {
+// Runs the segments of every group: plans[g] holds group g's segments (all of
+// the same count); burn[g] its burn-in.  Segment i of every group runs in one
+// launch at the temperature of plans[0][i].
+int run_segments(surfmcmc_ctx* ctx, SweepParams sp, const std::vector<std::vector<Segment>>& plans,
+                 const std::vector<uint32_t>& burn, double p, int lam, const SweepIO& io, cudaStream_t s) {
     int rc;
-    for (size_t i = 0; i < segs.size(); ++i) {
-        const bool first = i == 0, last = i + 1 == segs.size();
-        set_temperature(sp, p, segs[i].scale);
-        sp.t_begin = segs[i].t0;
-        sp.t_end = segs[i].t1;
-        sp.burn_in = segs[i].anneal ? segs[i].t1 : burn_in;
+    const size_t ns = plans[0].size();
+    for (size_t i = 0; i < ns; ++i) {
+        const bool first = i == 0, last = i + 1 == ns;
+        set_temperature(sp, p, plans[0][i].scale);
+        for (int g = 0; g < sp.n_groups; ++g) {
+            sp.grp[g].t_begin = plans[g][i].t0;
+            sp.grp[g].t_end = plans[g][i].t1;
+            sp.grp[g].burn_in = plans[g][i].anneal ? plans[g][i].t1 : burn[g];
+        }
         sp.e0 = first ? io.e0 : nullptr;
         sp.e0code = first ? io.e0code : nullptr;
         sp.init_frames = first ? io.init_frames : nullptr;
@@ -305,6 +340,7 @@ int run_segments(surfmcmc_ctx* ctx, SweepParams sp, const std::vector<Segment>& 
         sp.chain_sum = last ? io.chain_sum : nullptr;
         sp.chain_n = last ? io.chain_n : nullptr;
         sp.chain_frames = last ? io.chain_frames : nullptr;
+        sp.unit_counter = io.unit_counter;
         std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
         if ((rc = record_start(ctx, &ev, s))) return rc;
         CK(launch_sweep(sp, lam, s));
@@ -313,7 +349,219 @@ int run_segments(surfmcmc_ctx* ctx, SweepParams sp, const std::vector<Segment>& 
     return SURFMCMC_OK;
 }
 
+int run_segments(surfmcmc_ctx* ctx, const SweepParams& sp, const std::vector<Segment>& segs, uint32_t burn_in,
+                 double p, int lam, const SweepIO& io, cudaStream_t s) {
+    return run_segments(ctx, sp, std::vector<std::vector<Segment>>{segs}, std::vector<uint32_t>{burn_in}, p, lam,
+                        io, s);
+}
+
+
+// ---------------------------------------------------------------------------
+// Ragged batches: items of several code sizes and sweep counts in one call.
+// ---------------------------------------------------------------------------
+struct RaggedGroup {
+    int L;
+    uint32_t sweeps, burn;
+    std::vector<long long> items;  // caller's indices
+    double work;
+};
+
+struct RaggedLayout {
+    std::vector<RaggedGroup> groups;       // in launch order (largest work first)
+    std::vector<long long> perm;           // internal index -> caller's index
+    std::vector<long long> src_off, dst_off;
+    std::vector<int32_t> len;
+    std::vector<uint64_t> samples;         // per internal item
+    long long syn_bytes = 0, e0_words = 0, state_words = 0;
+    int lam = 0;
+    SweepParams sp;
+};
+
+int ragged_layout(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* sweeps, int64_t n, const surfmcmc_opts& o,
+                  RaggedLayout& lay) {
+    std::map<std::pair<int, uint32_t>, int> key;
+    lay.src_off.resize(n);
+    long long off = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int L = Ls[i];
+        if (L < 2 || L > SURFMCMC_MAX_L) return fail(ctx, SURFMCMC_EINVAL, "item %lld: L=%d out of range", (long long)i, L);
+        const uint32_t sw = sweeps ? sweeps[i] : o.n_sweeps;
+        lay.src_off[i] = off;
+        off += n_stabs(L);
+        auto it = key.find({L, sw});
+        if (it == key.end()) {
+            if (key.size() == (size_t)kMaxGroups)
+                return fail(ctx, SURFMCMC_EINVAL, "more than %d distinct (L, n_sweeps) pairs", kMaxGroups);
+            const uint32_t burn = o.n_sweeps ? (uint32_t)((uint64_t)sw * o.burn_in / o.n_sweeps) : 0;
+            if (o.anneal_stages > 0 && burn < (uint32_t)o.anneal_stages)
+                return fail(ctx, SURFMCMC_EINVAL, "item %lld: burn-in %u shorter than the annealing stages", (long long)i,
+                            burn);
+            it = key.emplace(std::make_pair(L, sw), (int)lay.groups.size()).first;
+            lay.groups.push_back({L, sw, burn, {}, 0.0});
+        }
+        lay.groups[it->second].items.push_back(i);
+    }
+    lay.syn_bytes = off;
+    for (auto& g : lay.groups) g.work = (double)g.items.size() * g.sweeps * (double)n_stabs(g.L);
+    std::stable_sort(lay.groups.begin(), lay.groups.end(),
+                     [](const RaggedGroup& a, const RaggedGroup& b) { return a.work > b.work; });
+    // lanes per bundle for the heaviest group, widened until the largest size fits
+    int lmax = 0;
+    for (auto& g : lay.groups) lmax = std::max(lmax, g.L);
+    if (pick_lanes(lay.groups.empty() ? 2 : lay.groups[0].L, o.lanes_per_bundle, &lay.lam))
+        return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported", o.lanes_per_bundle);
+    while (sweep_smem_bytes(n_qubits(lmax), lmax * (lmax - 1) / 2, lay.lam) > 200 * 1024 && lay.lam < 32) lay.lam *= 2;
+    const int Cn = 4 * o.chains_per_class;
+    init_chains(lay.sp, Cn, o.chains_per_class, 0);
+    long long dst = 0, item = 0, e0w = 0, stw = 0;
+    for (auto& g : lay.groups) {
+        add_group(lay.sp, g.L, (long long)g.items.size(), item, e0w, 0, stw, lay.lam);
+        for (long long i : g.items) {
+            lay.perm.push_back(i);
+            lay.dst_off.push_back(dst);
+            lay.len.push_back(n_stabs(g.L));
+            lay.samples.push_back(g.sweeps > g.burn ? (uint64_t)4 * o.chains_per_class * (g.sweeps - g.burn) : 0);
+            dst += n_stabs(g.L);
+        }
+        item += (long long)g.items.size();
+        e0w += (long long)g.items.size() * 2 * n_words(g.L);
+        stw += lay.sp.grp[lay.sp.n_groups - 1].n_bundles * 2 * n_qubits(g.L);
+    }
+    lay.e0_words = e0w;
+    lay.state_words = stw;
+    return SURFMCMC_OK;
+}
+
+// Device scratch of a ragged run, carved from one base pointer.
+struct RaggedScratch {
+    uint8_t* syn;
+    uint32_t* ids;
+    long long *src_off, *dst_off, *perm;
+    int32_t* len;
+    uint64_t* samples;
+    uint32_t* e0;
+    int32_t* code;
+    uint64_t* chain_sum;
+    uint32_t* state;
+    unsigned int* ctr;
+};
+
+size_t ragged_scratch(const RaggedLayout& lay, long long n, int Cn, char* base, RaggedScratch* rs) {
+    Carver cv;
+    const size_t o_syn = cv.reserve(lay.syn_bytes), o_ids = cv.reserve(n * 4), o_src = cv.reserve(n * 8),
+                 o_dst = cv.reserve(n * 8), o_perm = cv.reserve(n * 8), o_len = cv.reserve(n * 4),
+                 o_smp = cv.reserve(n * 8), o_e0 = cv.reserve(lay.e0_words * 4), o_code = cv.reserve(n * 4),
+                 o_cs = cv.reserve((size_t)n * Cn * 8), o_st = cv.reserve(lay.state_words * 4),
+                 o_ctr = cv.reserve(sizeof(unsigned int));
+    if (base && rs) {
+        rs->syn = (uint8_t*)(base + o_syn);
+        rs->ids = (uint32_t*)(base + o_ids);
+        rs->src_off = (long long*)(base + o_src);
+        rs->dst_off = (long long*)(base + o_dst);
+        rs->perm = (long long*)(base + o_perm);
+        rs->len = (int32_t*)(base + o_len);
+        rs->samples = (uint64_t*)(base + o_smp);
+        rs->e0 = (uint32_t*)(base + o_e0);
+        rs->code = (int32_t*)(base + o_code);
+        rs->chain_sum = (uint64_t*)(base + o_cs);
+        rs->state = (uint32_t*)(base + o_st);
+        rs->ctr = (unsigned int*)(base + o_ctr);
+    }
+    return cv.off;
+}
+
+// Copies the host-side tables of the layout to the scratch (synchronously).
+int ragged_upload(surfmcmc_ctx* ctx, const RaggedLayout& lay, long long n, const RaggedScratch& rs, cudaStream_t s) {
+    if (n == 0) return SURFMCMC_OK;
+    // src_off is indexed by the caller's index in the gather kernel
+    CK(cudaMemcpyAsync(rs.src_off, lay.src_off.data(), n * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(rs.dst_off, lay.dst_off.data(), n * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(rs.perm, lay.perm.data(), n * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(rs.len, lay.len.data(), n * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(rs.samples, lay.samples.data(), n * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return SURFMCMC_OK;
+}
+
+// All device work of a ragged run (kernels and memsets only, so that it can
+// be captured into a graph): gather, start frames per group, the sweep
+// segments of every group, decision scattered to the caller's order.
+int ragged_enqueue(surfmcmc_ctx* ctx, const RaggedLayout& lay, long long n, const surfmcmc_opts& o, double p,
+                   uint64_t seed, const uint8_t* syn, const uint32_t* ids, uint32_t id0, const RaggedScratch& rs,
+                   int32_t* out_class, uint64_t* out_class_sum, double* out_log_ratio, cudaStream_t s) {
+    int rc;
+    if (n == 0) return SURFMCMC_OK;
+    CK(launch_gather_rows(n, syn, rs.src_off, rs.dst_off, rs.len, rs.perm, ids, id0, rs.syn, rs.ids, s));
+    SweepParams sp = lay.sp;
+    sp.ids = rs.ids;
+    make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
+    std::vector<std::vector<Segment>> plans;
+    std::vector<uint32_t> burn;
+    long long syn_off = 0;
+    for (size_t g = 0; g < lay.groups.size(); ++g) {
+        const GroupDesc& gd = sp.grp[g];
+        CK(launch_start_frames(rs.syn + syn_off, gd.n, gd.L, rs.e0 + gd.e0_off, rs.code + gd.item_base, s));
+        syn_off += gd.n * n_stabs(gd.L);
+        plans.push_back(plan_segments(lay.groups[g].sweeps, lay.groups[g].burn, o.anneal_stages, o.anneal_beta0,
+                                      o.beta_scale, 0));
+        burn.push_back(lay.groups[g].burn);
+    }
+    SweepIO io;
+    io.e0 = rs.e0;
+    io.e0code = rs.code;
+    io.chain_sum = rs.chain_sum;
+    io.state = rs.state;
+    io.unit_counter = rs.ctr;
+    if ((rc = run_segments(ctx, sp, plans, burn, p, lay.lam, io, s))) return rc;
+    uint64_t T[5];
+    double beta_bar;
+    acceptance_table(p, 1.0, T, &beta_bar);
+    DecideParams dp;
+    memset(&dp, 0, sizeof dp);
+    dp.n = n;
+    dp.K = 4;
+    dp.R = o.chains_per_class;
+    dp.samples_per_item = rs.samples;
+    dp.perm = rs.perm;
+    dp.beta_bar = beta_bar;
+    dp.chain_sum = rs.chain_sum;
+    dp.out_class = out_class;
+    dp.out_class_sum = out_class_sum;
+    dp.out_log_ratio = out_log_ratio;
+    CK(launch_decide(dp, s));
+    return SURFMCMC_OK;
+}
+
+int ragged_check(surfmcmc_ctx* ctx, const int32_t* Ls, int64_t n, const surfmcmc_opts& o, double p, const uint32_t* ids,
+                 uint32_t id0) {
+    int rc;
+    if (!ctx) return SURFMCMC_EINVAL;
+    if (n < 0) return fail(ctx, SURFMCMC_EINVAL, "n=%lld < 0", (long long)n);
+    if (n > 0 && !Ls) return fail(ctx, SURFMCMC_EINVAL, "NULL Ls");
+    if (!ids && (uint64_t)id0 + (uint64_t)n > 4294967296ull)
+        return fail(ctx, SURFMCMC_EINVAL, "syndrome ids id0+n exceed 2^32");
+    if ((rc = check_opts(ctx, o, p))) return rc;
+    return SURFMCMC_OK;
+}
+
+// Host copies of per-item arrays that may live on the device.
+template <typename T>
+int host_copy(surfmcmc_ctx* ctx, const T* ptr, int64_t n, std::vector<T>& out) {
+    out.resize(n);
+    if (n == 0 || !ptr) return SURFMCMC_OK;
+    if (is_device_ptr(ptr)) CK(cudaMemcpy(out.data(), ptr, n * sizeof(T), cudaMemcpyDeviceToHost));
+    else memcpy(out.data(), ptr, n * sizeof(T));
+    return SURFMCMC_OK;
+}
+
 }  // namespace
+
+struct surfmcmc_plan {
+    surfmcmc_ctx* ctx = nullptr;
+    void* scratch = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
 extern "C" {
 
@@ -476,7 +724,8 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     while (G < Cn && G < 32) G *= 2;
 
     SweepParams sp;
-    init_geometry(sp, L, Cn, R, n, id0);
+    init_chains(sp, Cn, R, id0);
+    add_group(sp, L, n, 0, 0, 0, 0, lam);
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
 
     Carver cv;
@@ -495,7 +744,8 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     const size_t off_e0 = init_frames ? 0 : cv.reserve((size_t)n * 2 * W * 4);
     const size_t off_code = init_frames ? 0 : cv.reserve((size_t)n * 4);
     const std::vector<Segment> segs = plan_segments(o, o.beta_scale, sweep_begin);
-    const size_t off_state = segs.size() > 1 ? cv.reserve((size_t)sp.n_bundles * 2 * nq * 4) : 0;
+    const size_t off_state = segs.size() > 1 ? cv.reserve((size_t)sp.grp[0].n_bundles * 2 * nq * 4) : 0;
+    const size_t off_ctr = cv.reserve(sizeof(unsigned int));
     if ((rc = ensure_arena(ctx, cv.off))) return rc;
     Buf* all[] = {&b_syn, &b_if, &b_is, &b_cls, &b_csum, &b_lr, &b_chn, &b_chf};
     for (Buf* b : all) bind(*b, ctx);
@@ -504,6 +754,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     uint32_t* e0 = init_frames ? nullptr : (uint32_t*)(base + off_e0);
     int32_t* code = init_frames ? nullptr : (int32_t*)(base + off_code);
     uint32_t* state = segs.size() > 1 ? (uint32_t*)(base + off_state) : nullptr;
+    unsigned int* ctr = (unsigned int*)(base + off_ctr);
 
     if ((rc = copy_in(ctx, b_syn, s)) || (rc = copy_in(ctx, b_if, s)) || (rc = copy_in(ctx, b_is, s))) return rc;
     if (!init_frames) CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
@@ -517,12 +768,14 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     io.chain_n = (int32_t*)b_chn.dev;
     io.chain_frames = (uint32_t*)b_chf.dev;
     io.state = state;
+    io.unit_counter = ctr;
     if ((rc = run_segments(ctx, sp, segs, o.burn_in, p, lam, io, s))) return rc;
 
     uint64_t T[5];
     double beta_bar;
     acceptance_table(p, 1.0, T, &beta_bar);
     DecideParams dp;
+    memset(&dp, 0, sizeof dp);
     dp.n = n;
     dp.K = K;
     dp.R = R;
@@ -571,8 +824,10 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     cudaStream_t s = (cudaStream_t)stream;
     const int K = 4, R = o.chains_per_class, Cn = K * R, N = n_beta;
     SweepParams sp;
-    init_geometry(sp, L, Cn, R, n, id0);
+    init_chains(sp, Cn, R, id0);
+    add_group(sp, L, n, 0, 0, 0, 0, lam);
     const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
+    const int W = n_words(L), nq = n_qubits(L);
 
     Carver cv;
     Buf b_syn, b_cls, b_lz;
@@ -582,9 +837,10 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     const bool mean_scratch = !out_mean || !is_device_ptr(out_mean);
     const size_t off_mean = mean_scratch ? cv.reserve((size_t)n * K * N * 8) : 0;
     const size_t off_chs = cv.reserve((size_t)n * Cn * 8);
-    const size_t off_e0 = cv.reserve((size_t)n * 2 * sp.W * 4);
+    const size_t off_e0 = cv.reserve((size_t)n * 2 * W * 4);
     const size_t off_code = cv.reserve((size_t)n * 4);
-    const size_t off_state = segs0.size() > 1 ? cv.reserve((size_t)sp.n_bundles * 2 * sp.nq * 4) : 0;
+    const size_t off_state = segs0.size() > 1 ? cv.reserve((size_t)sp.grp[0].n_bundles * 2 * nq * 4) : 0;
+    const size_t off_ctr = cv.reserve(sizeof(unsigned int));
     if ((rc = ensure_arena(ctx, cv.off))) return rc;
     for (Buf* b : {&b_syn, &b_cls, &b_lz}) bind(*b, ctx);
     char* base = (char*)ctx->arena;
@@ -593,6 +849,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     uint32_t* e0 = (uint32_t*)(base + off_e0);
     int32_t* code = (int32_t*)(base + off_code);
     uint32_t* state = segs0.size() > 1 ? (uint32_t*)(base + off_state) : nullptr;
+    unsigned int* ctr = (unsigned int*)(base + off_ctr);
 
     if ((rc = copy_in(ctx, b_syn, s))) return rc;
     CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
@@ -607,6 +864,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
         io.e0code = code;
         io.chain_sum = chain_sum;
         io.state = state;
+        io.unit_counter = ctr;
         if ((rc = run_segments(ctx, sp, plan_segments(o, bs, 0), o.burn_in, p, lam, io, s))) return rc;
         CK(launch_class_means(n, K, R, N, j, samples, chain_sum, mean, s));
     }
@@ -614,7 +872,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     double beta_bar;
     acceptance_table(p, 1.0, T, &beta_bar);
     const double h = (o.beta_scale * beta_bar) / (double)(N - 1);
-    CK(launch_ti_decide(n, K, N, 0.75 * (double)sp.nq, h / 3.0, mean, (int32_t*)b_cls.dev, (double*)b_lz.dev, s));
+    CK(launch_ti_decide(n, K, N, 0.75 * (double)nq, h / 3.0, mean, (int32_t*)b_cls.dev, (double*)b_lz.dev, s));
 
     bool any_host = false;
     for (Buf* b : {&b_cls, &b_lz}) {
@@ -627,6 +885,138 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     }
     if (!stream || any_host) CK(cudaStreamSynchronize(s));
     return SURFMCMC_OK;
+}
+
+
+int surfmcmc_decode_ragged(surfmcmc_ctx* ctx, const uint8_t* syndromes, const int32_t* Ls, const uint32_t* n_sweeps,
+                           int64_t n, double p, const surfmcmc_opts* opts_in, uint64_t seed, const uint32_t* ids,
+                           uint32_t id0, int32_t* out_class, uint64_t* out_class_sum, double* out_log_ratio,
+                           void* stream) {
+    surfmcmc_opts o;
+    surfmcmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    int rc = ragged_check(ctx, Ls, n, o, p, ids, id0);
+    if (rc) return rc;
+    if (n > 0 && (!syndromes || !out_class)) return fail(ctx, SURFMCMC_EINVAL, "NULL syndromes or out_class");
+    if (n == 0) return SURFMCMC_OK;
+    ctx->last_error.clear();
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int32_t> hL;
+    std::vector<uint32_t> hS;
+    if ((rc = host_copy(ctx, Ls, n, hL))) return rc;
+    if (n_sweeps && (rc = host_copy(ctx, n_sweeps, n, hS))) return rc;
+    RaggedLayout lay;
+    if ((rc = ragged_layout(ctx, hL.data(), n_sweeps ? hS.data() : nullptr, n, o, lay))) return rc;
+    const int Cn = 4 * o.chains_per_class;
+    Carver cv;
+    cv.off = ragged_scratch(lay, n, Cn, nullptr, nullptr);
+    Buf b_syn, b_ids, b_cls, b_csum, b_lr;
+    plan(b_syn, (void*)syndromes, lay.syn_bytes, cv);
+    plan(b_ids, (void*)ids, ids ? (size_t)n * 4 : 0, cv);
+    plan(b_cls, out_class, (size_t)n * 4, cv);
+    plan(b_csum, out_class_sum, out_class_sum ? (size_t)n * 32 : 0, cv);
+    plan(b_lr, out_log_ratio, out_log_ratio ? (size_t)n * 32 : 0, cv);
+    if ((rc = ensure_arena(ctx, cv.off))) return rc;
+    for (Buf* b : {&b_syn, &b_ids, &b_cls, &b_csum, &b_lr}) bind(*b, ctx);
+    RaggedScratch rs;
+    ragged_scratch(lay, n, Cn, (char*)ctx->arena, &rs);
+    if ((rc = ragged_upload(ctx, lay, n, rs, s))) return rc;
+    if ((rc = copy_in(ctx, b_syn, s)) || (rc = copy_in(ctx, b_ids, s))) return rc;
+    if ((rc = ragged_enqueue(ctx, lay, n, o, p, seed, (const uint8_t*)b_syn.dev, (const uint32_t*)b_ids.dev, id0, rs,
+                             (int32_t*)b_cls.dev, (uint64_t*)b_csum.dev, (double*)b_lr.dev, s)))
+        return rc;
+    bool any_host = false;
+    for (Buf* b : {&b_cls, &b_csum, &b_lr}) {
+        if ((rc = copy_out(ctx, *b, s))) return rc;
+        any_host |= b->staged;
+    }
+    if (!stream || any_host) CK(cudaStreamSynchronize(s));
+    return SURFMCMC_OK;
+}
+
+int surfmcmc_ragged_plan_create(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* n_sweeps, int64_t n, double p,
+                                const surfmcmc_opts* opts_in, uint64_t seed, const uint8_t* syndromes,
+                                const uint32_t* ids, uint32_t id0, int32_t* out_class, uint64_t* out_class_sum,
+                                double* out_log_ratio, surfmcmc_plan** out_plan) {
+    if (!out_plan) return ctx ? fail(ctx, SURFMCMC_EINVAL, "NULL plan") : SURFMCMC_EINVAL;
+    *out_plan = nullptr;
+    surfmcmc_opts o;
+    surfmcmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    int rc = ragged_check(ctx, Ls, n, o, p, ids, id0);
+    if (rc) return rc;
+    if (n <= 0) return fail(ctx, SURFMCMC_EINVAL, "a plan needs n > 0");
+    if (!is_device_ptr(syndromes) || !is_device_ptr(out_class) || (ids && !is_device_ptr(ids)) ||
+        (out_class_sum && !is_device_ptr(out_class_sum)) || (out_log_ratio && !is_device_ptr(out_log_ratio)))
+        return fail(ctx, SURFMCMC_EINVAL, "a plan works on device buffers only");
+    ctx->last_error.clear();
+    DeviceGuard g(ctx->device);
+    std::vector<int32_t> hL;
+    std::vector<uint32_t> hS;
+    if ((rc = host_copy(ctx, Ls, n, hL))) return rc;
+    if (n_sweeps && (rc = host_copy(ctx, n_sweeps, n, hS))) return rc;
+    RaggedLayout lay;
+    if ((rc = ragged_layout(ctx, hL.data(), n_sweeps ? hS.data() : nullptr, n, o, lay))) return rc;
+    const int Cn = 4 * o.chains_per_class;
+    surfmcmc_plan* pl = new surfmcmc_plan;
+    pl->ctx = ctx;
+    auto cleanup = [&](int code) {
+        if (pl->exec) cudaGraphExecDestroy(pl->exec);
+        if (pl->graph) cudaGraphDestroy(pl->graph);
+        if (pl->scratch) cudaFree(pl->scratch);
+        delete pl;
+        return code;
+    };
+    const size_t bytes = ragged_scratch(lay, n, Cn, nullptr, nullptr);
+    cudaError_t e = cudaMalloc(&pl->scratch, bytes);
+    if (e != cudaSuccess) return cleanup(fail(ctx, SURFMCMC_ENOMEM, "plan scratch: %s", cudaGetErrorString(e)));
+    RaggedScratch rs;
+    ragged_scratch(lay, n, Cn, (char*)pl->scratch, &rs);
+    cudaStream_t cap;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup(fail(ctx, SURFMCMC_ECUDA, "stream: %s", cudaGetErrorString(e)));
+    if ((rc = ragged_upload(ctx, lay, n, rs, cap)) ||
+        (e = prepare_sweep(lay.sp, lay.lam)) != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return cleanup(rc ? rc : fail(ctx, SURFMCMC_ECUDA, "prepare: %s", cudaGetErrorString(e)));
+    }
+    const bool timing = ctx->timing;
+    ctx->timing = false;  // no event nodes in the graph
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = ragged_enqueue(ctx, lay, n, o, p, seed, syndromes, ids, id0, rs, out_class, out_class_sum, out_log_ratio,
+                            cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &pl->graph);
+        if (!rc && e2 != cudaSuccess) e = e2;
+    }
+    ctx->timing = timing;
+    cudaStreamDestroy(cap);
+    if (rc) return cleanup(rc);
+    if (e != cudaSuccess) return cleanup(fail(ctx, SURFMCMC_ECUDA, "capture: %s", cudaGetErrorString(e)));
+    if ((e = cudaGraphInstantiate(&pl->exec, pl->graph, 0)) != cudaSuccess)
+        return cleanup(fail(ctx, SURFMCMC_ECUDA, "instantiate: %s", cudaGetErrorString(e)));
+    *out_plan = pl;
+    return SURFMCMC_OK;
+}
+
+int surfmcmc_plan_launch(surfmcmc_plan* plan, void* stream) {
+    if (!plan) return SURFMCMC_EINVAL;
+    surfmcmc_ctx* ctx = plan->ctx;
+    DeviceGuard g(ctx->device);
+    CK(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+    if (!stream) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return SURFMCMC_OK;
+}
+
+void surfmcmc_plan_destroy(surfmcmc_plan* plan) {
+    if (!plan) return;
+    DeviceGuard g(plan->ctx->device);
+    cudaDeviceSynchronize();
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->scratch) cudaFree(plan->scratch);
+    delete plan;
 }
 
 int surfmcmc_decode(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L, double p,

@@ -114,18 +114,20 @@ __global__ void decide_kernel(DecideParams p) {
         S[k] = s;
         if (s < S[best]) best = k;
     }
-    p.out_class[i] = best;
+    const long long o = p.perm ? p.perm[i] : i;  // caller's index of internal item i
+    const uint64_t samples = p.samples_per_item ? p.samples_per_item[i] : p.samples;
+    p.out_class[o] = best;
     if (p.out_class_sum)
-        for (int k = 0; k < p.K; ++k) p.out_class_sum[i * p.K + k] = S[k];
+        for (int k = 0; k < p.K; ++k) p.out_class_sum[o * p.K + k] = S[k];
     if (p.out_log_ratio)
         for (int k = 0; k < p.K; ++k) {
             double v = 0.0;
-            if (p.samples) {
-                const double mk = (double)S[k] / (double)p.samples;
-                const double mb = (double)S[best] / (double)p.samples;
+            if (samples) {
+                const double mk = (double)S[k] / (double)samples;
+                const double mb = (double)S[best] / (double)samples;
                 v = -p.beta_bar * (mk - mb);
             }
-            p.out_log_ratio[i * p.K + k] = v;
+            p.out_log_ratio[o * p.K + k] = v;
         }
 }
 
@@ -167,6 +169,28 @@ __global__ void ti_decide_kernel(long long n, int K, int N, double mean0, double
     out_class[i] = best;
     if (out_log_z)
         for (int k = 0; k < K; ++k) out_log_z[i * K + k] = -__dsub_rn(I[k], I[best]);
+}
+
+// Ragged batches: copies the caller's syndrome rows (item perm[i] of the
+// input) into group order and sets the internal ids.
+__global__ void gather_rows_kernel(long long n, const uint8_t* src, const long long* src_off, const long long* dst_off,
+                                   const int32_t* len, const long long* perm, const uint32_t* ids, uint32_t id0,
+                                   uint8_t* dst, uint32_t* ids_out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint8_t* a = src + src_off[perm[i]];
+    uint8_t* b = dst + dst_off[i];
+    for (int k = 0; k < len[i]; ++k) b[k] = a[k];
+    ids_out[i] = ids ? ids[perm[i]] : id0 + (uint32_t)perm[i];
+}
+
+cudaError_t launch_gather_rows(long long n, const uint8_t* src, const long long* src_off, const long long* dst_off,
+                               const int32_t* len, const long long* perm, const uint32_t* ids, uint32_t id0,
+                               uint8_t* dst, uint32_t* ids_out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    gather_rows_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, src, src_off, dst_off, len, perm, ids, id0, dst,
+                                                                   ids_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_class_means(long long n, int K, int R, int N, int j, uint64_t samples, const uint64_t* chain_sum,

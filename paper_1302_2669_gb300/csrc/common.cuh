@@ -94,17 +94,31 @@ __host__ __device__ __forceinline__ void colour_support(int L, int col, int m, i
 __host__ __device__ __forceinline__ int bundle_stride(int nq) { return 2 * (nq + 2) + 1; }
 
 // ---------------------------------------------------------------------------
-// Sweep kernel parameters.
+// Sweep kernel parameters.  One launch runs the chains of up to kMaxGroups
+// groups of syndromes; a group has one code size and one sweep range.  Items
+// (syndromes) are numbered globally across the groups; per-item arrays with a
+// size-dependent row (pure errors, frames, bundle state) are laid out group
+// after group at the given word offsets.
 // ---------------------------------------------------------------------------
+constexpr int kMaxGroups = 8;
+
+struct GroupDesc {
+    int L, nq, W, nc;            // size, qubits, words per plane, generators per colour
+    long long n;                 // syndromes of the group
+    long long n_bundles;         // 32-chain bundles of the group
+    long long item_base;         // global index of the group's first syndrome
+    long long e0_off;            // word offset of its pure errors ([n][2][W])
+    long long frames_off;        // word offset of its per-chain frames ([n][C][2][W])
+    long long state_off;         // word offset of its bundle state ([n_bundles][2][nq])
+    long long unit_base;         // first work unit of the group
+    uint32_t t_begin, t_end, burn_in;  // sweeps of this launch; sampling from burn_in on
+};
+
 struct SweepParams {
-    int L, nq, W, nc;          // size, qubits, words per plane, generators per colour
     int C, R, G;               // chains per syndrome, per class, plane width
     int bps, spb;              // bundles per syndrome (G == 32), syndromes per bundle (G < 32)
-    long long n;               // syndromes
-    long long n_bundles;
     uint32_t id0;
-    const uint32_t* ids;       // per-syndrome ids (NULL: id0 + index)
-    uint32_t t_begin, t_end, burn_in;
+    const uint32_t* ids;       // per-syndrome ids (NULL: id0 + global index)
     int accept_all;            // r* == 1: every proposal accepted
     int reject_all;            // T[1] == 0: no uphill proposal accepted
     int lz;                    // leading planes where every threshold bit is 0
@@ -112,21 +126,28 @@ struct SweepParams {
     // Threshold bits of plane k as the algebraic normal form of the map
     // d-1 = e0 + 2 e1 -> bit (31-k) of T[d]: f = c0 ^ e0 c1 ^ e1 c2 ^ e0 e1 c3.
     uint32_t pc[4][32];
-    const uint32_t* e0;        // [n][2][W] pure errors
-    const int32_t* e0code;     // [n]
-    const uint32_t* init_frames;  // [n][C][2][W] or NULL
-    const uint32_t* state_in;     // [n_bundles][2][nq] bit-sliced state from an earlier launch, or NULL
-    uint32_t* state_out;          // [n_bundles][2][nq] state at t_end for a later launch, or NULL
-    const uint64_t* init_sum;     // [n][C] or NULL
-    uint64_t* chain_sum;       // [n][C] out
-    int32_t* chain_n;          // [n][C] out or NULL
-    uint32_t* chain_frames;    // [n][C][2][W] out or NULL
+    const uint32_t* e0;        // pure errors
+    const int32_t* e0code;     // [items]
+    const uint32_t* init_frames;  // per-chain start frames, or NULL
+    const uint32_t* state_in;     // bit-sliced state from an earlier launch, or NULL
+    uint32_t* state_out;          // state at t_end for a later launch, or NULL
+    const uint64_t* init_sum;     // [items][C] or NULL
+    uint64_t* chain_sum;       // [items][C] out, or NULL
+    int32_t* chain_n;          // [items][C] out or NULL
+    uint32_t* chain_frames;    // per-chain final frames or NULL
+    int n_groups;
+    int grp_nq_max, grp_nc_max;   // largest group (shared-memory layout)
+    long long total_units;
+    unsigned int* unit_counter;   // work queue of the persistent blocks (reset by the launcher)
+    GroupDesc grp[kMaxGroups];
 };
 
 struct DecideParams {
     long long n;
     int K, R;
     uint64_t samples;          // 4 R (n_sweeps - burn_in)
+    const uint64_t* samples_per_item;  // per internal item, or NULL (then samples)
+    const long long* perm;     // caller's index of internal item i, or NULL (identity)
     double beta_bar;
     const uint64_t* chain_sum; // [n][K R]
     int32_t* out_class;        // [n]
@@ -136,12 +157,17 @@ struct DecideParams {
 
 // Launchers (return cudaGetLastError() after the launch).
 cudaError_t launch_sweep(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
+cudaError_t prepare_sweep(const SweepParams& p, int lanes_per_bundle);
 size_t sweep_smem_bytes(int nq, int nc, int lanes_per_bundle);  // dynamic shared memory of a block
+long long sweep_units(long long n_bundles, int lanes_per_bundle);  // work units of a group
 cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p,
                                  uint8_t* syn, int32_t* true_class, cudaStream_t s);
 cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
                                 cudaStream_t s);
 cudaError_t launch_decide(const DecideParams& p, cudaStream_t s);
+cudaError_t launch_gather_rows(long long n, const uint8_t* src, const long long* src_off, const long long* dst_off,
+                               const int32_t* len, const long long* perm, const uint32_t* ids, uint32_t id0,
+                               uint8_t* dst, uint32_t* ids_out, cudaStream_t s);
 cudaError_t launch_class_means(long long n, int K, int R, int N, int j, uint64_t samples, const uint64_t* chain_sum,
                                double* mean, cudaStream_t s);
 cudaError_t launch_ti_decide(long long n, int K, int N, double mean0, double h3, double* mean, int32_t* out_class,

@@ -56,7 +56,8 @@ size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 extern "C" size_t surfmcmc_noalloc_scratch_needed(int64_t n, int32_t L, int32_t chains_per_class) {
     if (n < 0 || L < 2 || L > SURFMCMC_MAX_L || chains_per_class < 1) return 0;
     const size_t Cn = 4 * (size_t)chains_per_class;
-    return round256((size_t)n * 2 * n_words(L) * 4) + round256((size_t)n * 4) + round256((size_t)n * Cn * 8);
+    return round256((size_t)n * 2 * n_words(L) * 4) + round256((size_t)n * 4) + round256((size_t)n * Cn * 8) +
+           round256(sizeof(unsigned int));
 }
 
 extern "C" int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int32_t L, double p,
@@ -91,6 +92,8 @@ extern "C" int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int3
     uint32_t* e0 = (uint32_t*)sp0;
     int32_t* code = (int32_t*)(sp0 + round256((size_t)n * 2 * W * 4));
     uint64_t* chain_sum = (uint64_t*)(sp0 + round256((size_t)n * 2 * W * 4) + round256((size_t)n * 4));
+    unsigned int* unit_counter =
+        (unsigned int*)(sp0 + round256((size_t)n * 2 * W * 4) + round256((size_t)n * 4) + round256((size_t)n * Cn * 8));
 
     // Lanes per bundle: the smallest power of two >= 2 whose lanes the
     // colour's generators fill to >= 90%, within the shared-memory limit.
@@ -104,23 +107,29 @@ extern "C" int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int3
 
     SweepParams sp;
     memset(&sp, 0, sizeof sp);
-    sp.L = L;
-    sp.nq = nq;
-    sp.W = W;
-    sp.nc = nc;
-    sp.C = Cn;
-    sp.R = R;
     int G = 1;
     while (G < Cn && G < 32) G *= 2;
+    sp.C = Cn;
+    sp.R = R;
     sp.G = G;
     sp.bps = G == 32 ? (Cn + 31) / 32 : 1;
     sp.spb = G == 32 ? 1 : 32 / G;
-    sp.n = n;
-    sp.n_bundles = G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
     sp.id0 = id0;
-    sp.t_begin = 0;
-    sp.t_end = o.n_sweeps;
-    sp.burn_in = o.burn_in;
+    sp.n_groups = 1;
+    GroupDesc& gd = sp.grp[0];
+    gd.L = L;
+    gd.nq = nq;
+    gd.W = W;
+    gd.nc = nc;
+    gd.n = n;
+    gd.n_bundles = G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
+    gd.t_begin = 0;
+    gd.t_end = o.n_sweeps;
+    gd.burn_in = o.burn_in;
+    sp.grp_nq_max = nq;
+    sp.grp_nc_max = nc;
+    sp.total_units = sweep_units(gd.n_bundles, lam);
+    sp.unit_counter = unit_counter;
     // Eq. 2 acceptance table, as in surfmcmc_decode.
     const double r = (p / 3.0) / (1.0 - p);
     const double rs = o.beta_scale == 1.0 ? r : exp(-o.beta_scale * -log(r));
@@ -150,6 +159,7 @@ extern "C" int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int3
     if (launch_start_frames(syndromes, n, L, e0, code, s) != cudaSuccess) return SURFMCMC_ECUDA;
     if (launch_sweep(sp, lam, s) != cudaSuccess) return SURFMCMC_ECUDA;
     DecideParams dp;
+    memset(&dp, 0, sizeof dp);
     dp.n = n;
     dp.K = K;
     dp.R = R;

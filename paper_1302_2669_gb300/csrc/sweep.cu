@@ -95,11 +95,12 @@ constexpr uint32_t kAccCapacity = 8u * (1u << kAccHi) - 1u;
 constexpr int kFlushPlanes = 3 + kAccHi + 5;  // + butterfly growth over <= 32 lanes
 
 struct OccAcc {
-    uint32_t ones, twos, fours, hi[kAccHi];
+    uint32_t ones, twos, fours;
+    uint32_t* hi;  // kAccHi planes in shared memory, plane k at hi[32 k] (lane-contiguous)
     __device__ __forceinline__ void clear() {
         ones = twos = fours = 0;
 #pragma unroll
-        for (int k = 0; k < kAccHi; ++k) hi[k] = 0;
+        for (int k = 0; k < kAccHi; ++k) hi[32 * k] = 0;
     }
 };
 
@@ -120,12 +121,11 @@ __device__ __forceinline__ void accumulate_phase(OccAcc& a, const uint32_t* X, c
         csa(tb, a.ones, a.ones, x[6], x[7]);
         csa(fb, a.twos, a.twos, ta, tb);
         csa(e, a.fours, a.fours, fa, fb);
-#pragma unroll
-        for (int k = 0; k < kAccHi; ++k) {
-            if (!e) break;
-            const uint32_t c = a.hi[k] & e;
-            a.hi[k] ^= e;
-            e = c;
+        // ripple the eights into the high planes (rarely more than a few)
+        for (int k = 0; k < kAccHi && e; ++k) {
+            const uint32_t h = a.hi[32 * k];
+            a.hi[32 * k] = h ^ e;
+            e &= h;
         }
     }
 }
@@ -139,7 +139,7 @@ __device__ __forceinline__ void flush_acc(OccAcc& a, int sub, uint32_t valid, ui
     v[1] = a.twos;
     v[2] = a.fours;
 #pragma unroll
-    for (int k = 0; k < kAccHi; ++k) v[3 + k] = a.hi[k];
+    for (int k = 0; k < kAccHi; ++k) v[3 + k] = a.hi[32 * k];
 #pragma unroll
     for (int k = 3 + kAccHi; k < kFlushPlanes; ++k) v[k] = 0;
 #pragma unroll
@@ -264,46 +264,42 @@ constexpr int kQueueCap = 64;
 constexpr int kQueueItem = 5;  // (m | slot << 16), U, E0, E1, accepted so far
 constexpr int kMaxSlots = 8;
 
+// Per warp after the frames: queue counter and items, the bundles' ids, and
+// the high planes of the lanes' occupancy counters.
 __host__ __device__ __forceinline__ int warp_aux_words(int bundles) {
-    return 1 + kQueueCap * kQueueItem + bundles * (kMaxSlots + 1);
+    return 1 + kQueueCap * kQueueItem + bundles * (kMaxSlots + 1) + 32 * kAccHi;
 }
 
+// One unit: the bundles of group g handled by this block (warps x 32/LAM
+// bundles); every warp runs its bundles' chains from gd.t_begin to gd.t_end.
 template <int G, int LAM>
-__global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ SweepParams p) {
+__device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& gd, long long unit,
+                                         uint32_t* smem, const ushort4* tab) {
     constexpr int B = 32 / LAM;                       // bundles per warp
     constexpr int NJ = 32 / LAM;                      // chains owned per lane
     constexpr int SLOTS = PlaneBatch<G>::SLOTS;
-    extern __shared__ __align__(16) uint32_t smem[];
-    const int nc = p.nc, nq = p.nq, L = p.L;
+    const int nc = gd.nc, nq = gd.nq, L = gd.L;
     const int stride = bundle_stride(nq);
-    ushort4* tab = reinterpret_cast<ushort4*>(smem);
-    uint32_t* frames = smem + 8 * nc;
-
-    for (int idx = threadIdx.x; idx < 4 * nc; idx += blockDim.x) {
-        const int col = idx / nc, m = idx - col * nc;
-        int q[4];
-        colour_support(L, col, m, q);
-        tab[idx] = make_ushort4((unsigned short)q[0], (unsigned short)q[1], (unsigned short)q[2],
-                                (unsigned short)q[3]);
-    }
-    __syncthreads();
+    uint32_t* frames = smem + 8 * p.grp_nc_max;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane / LAM, sub = lane % LAM;
-    const long long bid = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * B + slot;
-    const bool active = bid < p.n_bundles;
+    const long long bid = (unit * (blockDim.x >> 5) + warp) * B + slot;   // bundle within the group
+    const bool active = bid < gd.n_bundles;
     uint32_t* X = frames + (warp * B + slot) * stride;
     uint32_t* Z = X + nq + 2;
-    uint32_t* q_cnt = frames + (blockDim.x >> 5) * B * stride + warp * warp_aux_words(B);
+    uint32_t* q_cnt = frames + (blockDim.x >> 5) * B * bundle_stride(p.grp_nq_max) + warp * warp_aux_words(B);
     uint32_t* q_items = q_cnt + 1;
     uint32_t* binfo = q_items + kQueueCap * kQueueItem;  // per slot: w, sid[SLOTS]
+    uint32_t* acc_hi = binfo + B * (kMaxSlots + 1) + lane;  // this lane's high counter planes
 
     // Syndromes and chains of the bundle.
     long long syn[SLOTS];
     uint32_t sid[SLOTS];
     uint32_t w = 0, valid = 0;
+    // syn[]: the bundle's syndromes as global item indices
     if constexpr (G == 32) {
-        syn[0] = active ? bid / p.bps : 0;
+        syn[0] = gd.item_base + (active ? bid / p.bps : 0);
         w = active ? (uint32_t)(bid % p.bps) : 0;
         sid[0] = p.ids ? p.ids[syn[0]] : p.id0 + (uint32_t)syn[0];
         const int left = p.C - 32 * (int)w;
@@ -311,10 +307,11 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
     } else {
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
-            syn[s] = bid * SLOTS + s;
-            const bool ok = active && syn[s] < p.n;
-            if (!ok) syn[s] = bid * SLOTS;  // any in-range syndrome; its bits are masked
-            if (!active) syn[s] = 0;
+            long long li = bid * SLOTS + s;
+            const bool ok = active && li < gd.n;
+            if (!ok) li = bid * SLOTS;  // any in-range syndrome; its bits are masked
+            if (!active) li = 0;
+            syn[s] = gd.item_base + li;
             sid[s] = p.ids ? p.ids[syn[s]] : p.id0 + (uint32_t)syn[s];
             if (ok) valid |= ((1u << p.C) - 1u) << (s * G);
         }
@@ -338,8 +335,13 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
         lx |= (uint32_t)(l & 1) << b;
         lzm |= (uint32_t)((l >> 1) & 1) << b;
     }
-    const int W = p.W;
-    const uint32_t* st_in = p.state_in ? p.state_in + (size_t)(active ? bid : 0) * 2 * nq : nullptr;
+    const int W = gd.W;
+    // per-item arrays of the group: pure errors and frames are laid out per group
+    const uint32_t* e0g = p.e0 ? p.e0 + gd.e0_off - (size_t)gd.item_base * 2 * W : nullptr;
+    const uint32_t* ifg = p.init_frames ? p.init_frames + gd.frames_off - (size_t)gd.item_base * p.C * 2 * W
+                                        : nullptr;
+    uint32_t* cfg = p.chain_frames ? p.chain_frames + gd.frames_off - (size_t)gd.item_base * p.C * 2 * W : nullptr;
+    const uint32_t* st_in = p.state_in ? p.state_in + gd.state_off + (size_t)(active ? bid : 0) * 2 * nq : nullptr;
     for (int q = sub; q < nq; q += LAM) {
         uint32_t xw = 0, zw = 0;
         if (st_in) {
@@ -347,10 +349,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
                 xw = st_in[q];
                 zw = st_in[nq + q];
             }
-        } else if (p.init_frames) {
+        } else if (ifg) {
             for (int b = 0; b < 32; ++b) {
                 if (!((valid >> b) & 1u)) continue;
-                const uint32_t* f = p.init_frames + ((size_t)syn_of(b) * p.C + chain_of(b)) * 2 * W;
+                const uint32_t* f = ifg + ((size_t)syn_of(b) * p.C + chain_of(b)) * 2 * W;
                 xw |= ((f[q >> 5] >> (q & 31)) & 1u) << b;
                 zw |= ((f[W + (q >> 5)] >> (q & 31)) & 1u) << b;
             }
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
             for (int s = 0; s < SLOTS; ++s) {
                 const uint32_t vm = G == 32 ? valid : (valid & (((1u << (G & 31)) - 1u) << (s * G)));
                 if (!vm) continue;
-                const uint32_t* e = p.e0 + (size_t)syn[s] * 2 * W;
+                const uint32_t* e = e0g + (size_t)syn[s] * 2 * W;
                 if ((e[q >> 5] >> (q & 31)) & 1u) xw |= vm;
                 if ((e[W + (q >> 5)] >> (q & 31)) & 1u) zw |= vm;
             }
@@ -383,13 +385,14 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
         if (p.chain_sum) p.chain_sum[ci] = p.init_sum ? p.init_sum[ci] : 0ull;
     }
     OccAcc occ;
+    occ.hi = acc_hi;
     occ.clear();
     const uint32_t qpl = (uint32_t)((nq + LAM - 1) / LAM);  // qubits counted per lane and phase
     const uint32_t flush_every = kAccCapacity / qpl;       // phases before the accumulator could overflow
     uint32_t since_flush = 0;
     __syncwarp();
 
-    for (uint32_t t = p.t_begin; t < p.t_end; ++t) {
+    for (uint32_t t = gd.t_begin; t < gd.t_end; ++t) {
 #pragma unroll 1
         for (int col = 0; col < 4; ++col) {
             uint32_t* own = col < 2 ? X : Z;          // plane the generator flips
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
                 }
                 __syncwarp();
             }
-            if (t >= p.burn_in) {
+            if (t >= gd.burn_in) {
                 accumulate_phase<LAM>(occ, X, Z, nq, sub);
                 if (++since_flush == flush_every) {
                     flush_acc<LAM>(occ, sub, valid, p.chain_sum, ci_of);
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
 
     flush_acc<LAM>(occ, sub, valid, p.chain_sum, ci_of);
     if (p.state_out && active) {
-        uint32_t* st = p.state_out + (size_t)bid * 2 * nq;
+        uint32_t* st = p.state_out + gd.state_off + (size_t)bid * 2 * nq;
         for (int q = sub; q < nq; q += LAM) {
             st[q] = X[q];
             st[nq + q] = Z[q];
@@ -506,8 +509,8 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
         if (!((valid >> b) & 1u)) continue;
         const size_t ci = (size_t)syn_of(b) * p.C + chain_of(b);
         if (p.chain_n) p.chain_n[ci] = (int32_t)bit_of(cnt, b);
-        if (p.chain_frames) {
-            uint32_t* f = p.chain_frames + ci * 2 * W;
+        if (cfg) {
+            uint32_t* f = cfg + ci * 2 * W;
             for (int wi = 0; wi < W; ++wi) {
                 uint32_t xw = 0, zw = 0;
                 for (int i = 0; i < 32; ++i) {
@@ -523,6 +526,44 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Swee
     }
 }
 
+
+// Persistent sweep kernel: a block takes units (the bundles of one group that
+// fill its warps) first by its index, then from a queue counter, in the order
+// the host arranged (largest work first), and rebuilds the support table in
+// shared memory when the group's code size changes.
+template <int G, int LAM>
+__global__ void __launch_bounds__(128, (G >= 16 ? 5 : 3)) sweep_kernel(const __grid_constant__ SweepParams p) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ long long s_unit;
+    ushort4* tab = reinterpret_cast<ushort4*>(smem);
+    int cur = -1;
+    for (long long it = 0;; ++it) {
+        if (threadIdx.x == 0)
+            s_unit = it == 0 ? (long long)blockIdx.x
+                             : (long long)gridDim.x + (long long)atomicAdd(p.unit_counter, 1u);
+        __syncthreads();
+        const long long u = s_unit;
+        if (u >= p.total_units) break;
+        int g = 0;
+        while (g + 1 < p.n_groups && u >= p.grp[g + 1].unit_base) ++g;
+        const GroupDesc& gd = p.grp[g];
+        if (g != cur) {
+            for (int idx = threadIdx.x; idx < 4 * gd.nc; idx += blockDim.x) {
+                const int col = idx / gd.nc, m = idx - col * gd.nc;
+                int q[4];
+                colour_support(gd.L, col, m, q);
+                tab[idx] = make_ushort4((unsigned short)q[0], (unsigned short)q[1], (unsigned short)q[2],
+                                        (unsigned short)q[3]);
+            }
+            cur = g;
+            __syncthreads();
+        }
+        run_unit<G, LAM>(p, gd, u - gd.unit_base, smem, tab);
+        __syncthreads();
+        if (!p.unit_counter) break;
+    }
+}
+
 constexpr int kWarps = 4;
 
 size_t sweep_smem_bytes(int nq, int nc, int lam) {
@@ -530,10 +571,12 @@ size_t sweep_smem_bytes(int nq, int nc, int lam) {
     return (size_t)8 * nc * 4 + (size_t)kWarps * ((size_t)B * bundle_stride(nq) + warp_aux_words(B)) * 4;
 }
 
+long long sweep_units(long long n_bundles, int lam) { return (n_bundles + (long long)kWarps * (32 / lam) - 1) /
+                                                               ((long long)kWarps * (32 / lam)); }
+
 template <int G, int LAM>
 static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
-    constexpr int B = 32 / LAM;
-    const size_t smem = sweep_smem_bytes(p.nq, p.nc, LAM);
+    const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM);
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -541,11 +584,52 @@ static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    const long long per_block = (long long)kWarps * B;
-    const long long blocks = (p.n_bundles + per_block - 1) / per_block;
-    if (blocks == 0) return cudaSuccess;
+    if (p.total_units == 0) return cudaSuccess;
+    long long blocks = p.total_units;
+    if (p.unit_counter) {
+        // persistent: as many blocks as fit on the device at once
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM>, 32 * kWarps, smem);
+        if (e != cudaSuccess) return e;
+        const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        if (blocks > resident) blocks = resident;
+        e = cudaMemsetAsync(p.unit_counter, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+    }
     sweep_kernel<G, LAM><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int G, int LAM>
+static cudaError_t prepare_t(const SweepParams& p) {
+    const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM);
+    return cudaFuncSetAttribute(sweep_kernel<G, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int G>
+static cudaError_t prepare_g(const SweepParams& p, int lam) {
+    switch (lam) {
+        case 2: return prepare_t<G, 2>(p);
+        case 4: return prepare_t<G, 4>(p);
+        case 8: return prepare_t<G, 8>(p);
+        case 16: return prepare_t<G, 16>(p);
+        case 32: return prepare_t<G, 32>(p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Sets the kernel's shared-memory limit ahead of a stream capture.
+cudaError_t prepare_sweep(const SweepParams& p, int lam) {
+    switch (p.G) {
+        case 4: return prepare_g<4>(p, lam);
+        case 8: return prepare_g<8>(p, lam);
+        case 16: return prepare_g<16>(p, lam);
+        case 32: return prepare_g<32>(p, lam);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int G>
