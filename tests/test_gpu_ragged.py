@@ -42,15 +42,15 @@ def _mixed(seed, n, p, id0=0):
 
 
 def _sweeps(Ls, scale):
-    return np.array([max(4, (int(L) * int(L)) // scale) for L in Ls], np.uint32)
+    return np.array([max(10, (int(L) * int(L)) // scale) for L in Ls], np.uint32)
 
 
 @pytest.mark.parametrize("anneal", [False, True])
 def test_ragged_matches_per_size_decodes(ctx, pkg, anneal):
     p, n, R = 0.14, 37, 4
     Ls, cat, rows, _ = _mixed(3001, n, p)
-    sw = _sweeps(Ls, 8)
-    kw = dict(n_sweeps=100, burn_in=20, anneal_stages=4, anneal_beta0=0.3) if anneal else dict(n_sweeps=100)
+    sw = _sweeps(Ls, 4)
+    kw = dict(n_sweeps=100, burn_in=40, anneal_stages=4, anneal_beta0=0.3) if anneal else dict(n_sweeps=100)
     opts = pkg.Opts(chains_per_class=R, **kw)
     cls, csum, lr = ctx.decode_ragged(torch.from_numpy(cat).cuda(), torch.from_numpy(Ls).cuda(), p, opts,
                                       n_sweeps=torch.from_numpy(sw).cuda(), seed=3101, id0=0)
