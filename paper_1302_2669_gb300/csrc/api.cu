@@ -161,7 +161,15 @@ void set_temperature(SweepParams& sp, double p, double beta_scale) {
     acceptance_table(p, beta_scale, T, &beta_bar);
     sp.accept_all = T[1] >= 4294967296ull;
     sp.reject_all = T[1] == 0;
-    sp.lz = sp.accept_all ? 0 : (T[1] == 0 ? 32 : __builtin_clz((uint32_t)T[1]));
+    sp.qmodes = 0;
+    for (int q = 0; q < 8 && !sp.accept_all; ++q) {
+        uint32_t any1 = 0, any234 = 0;
+        for (int k = 4 * q; k < 4 * q + 4; ++k) {
+            any1 |= (uint32_t)(T[1] >> (31 - k)) & 1u;
+            for (int d = 2; d <= 4; ++d) any234 |= (uint32_t)(T[d] >> (31 - k)) & 1u;
+        }
+        sp.qmodes |= (any234 ? 2u : any1 ? 1u : 0u) << (2 * q);
+    }
     for (int k = 0; k < 32; ++k) {
         uint32_t t[5] = {0, 0, 0, 0, 0};
         if (!sp.accept_all)

@@ -121,7 +121,8 @@ struct SweepParams {
     const uint32_t* ids;       // per-syndrome ids (NULL: id0 + global index)
     int accept_all;            // r* == 1: every proposal accepted
     int reject_all;            // T[1] == 0: no uphill proposal accepted
-    int lz;                    // leading planes where every threshold bit is 0
+    uint32_t qmodes;           // per quad of planes 4q..4q+3, 2 bits: 0 every threshold digit is 0,
+                               // 1 only T[1] has nonzero digits, 2 general
     RoundKeys rk;
     // Threshold bits of plane k as the algebraic normal form of the map
     // d-1 = e0 + 2 e1 -> bit (31-k) of T[d]: f = c0 ^ e0 c1 ^ e1 c2 ^ e0 e1 c3.

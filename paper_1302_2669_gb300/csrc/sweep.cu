@@ -232,22 +232,38 @@ __device__ __forceinline__ uint32_t bernoulli_range(const SweepParams& p, uint32
     using PB = PlaneBatch<G>;
     constexpr int PPB = PB::PPB;
     const uint32_t E01 = E0 & E1;
+    const uint32_t M1 = ~(E0 | E1);  // chains with Delta n = 1
     uint32_t acc = 0;
 #pragma unroll
     for (int bt = BT0; bt < BT1; ++bt) {
         PB pb;
         pb.make(p, sid, w, t, colm, (uint32_t)bt);
-        if ((bt + 1) * PPB <= p.lz) {
-            // every threshold digit is 0 here: a 1 digit rejects
 #pragma unroll
-            for (int i = 0; i < PPB; ++i) U &= ~pb.pl[i];
-        } else {
+        for (int qd = 0; qd < PPB / 4; ++qd) {
+            const int k0 = bt * PPB + 4 * qd;
+            const uint32_t mode = (p.qmodes >> (2 * (k0 / 4))) & 3u;
+            if (mode == 0) {
+                // every threshold digit is 0 here: a 1 digit rejects
 #pragma unroll
-            for (int i = 0; i < PPB; ++i) {
-                const int k = bt * PPB + i;
-                const uint32_t f = p.pc[0][k] ^ (E0 & p.pc[1][k]) ^ (E1 & p.pc[2][k]) ^ (E01 & p.pc[3][k]);
-                acc |= U & f & ~pb.pl[i];
-                U &= ~(f ^ pb.pl[i]);
+                for (int i = 0; i < 4; ++i) U &= ~pb.pl[4 * qd + i];
+            } else if (mode == 1) {
+                // only T[1] has nonzero digits here
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t r = pb.pl[4 * qd + i];
+                    const uint32_t f = p.pc[0][k0 + i] & M1;
+                    acc |= U & f & ~r;
+                    U &= ~(f ^ r);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = k0 + i;
+                    const uint32_t r = pb.pl[4 * qd + i];
+                    const uint32_t f = p.pc[0][k] ^ (E0 & p.pc[1][k]) ^ (E1 & p.pc[2][k]) ^ (E01 & p.pc[3][k]);
+                    acc |= U & f & ~r;
+                    U &= ~(f ^ r);
+                }
             }
         }
         if (!U) break;
