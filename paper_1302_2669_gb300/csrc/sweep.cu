@@ -90,17 +90,16 @@ __device__ __forceinline__ uint32_t bit_of(const uint32_t cnt[kCountBits], int b
 // counter of kAccHi planes).  Each lane accumulates only its own slice of the
 // qubits; the slices of a bundle's LAM lanes are added together only when the
 // accumulator is flushed into the chains' 64-bit sums.
-constexpr int kAccHi = 16;
+constexpr int kAccHi = 10;
 constexpr uint32_t kAccCapacity = 8u * (1u << kAccHi) - 1u;
 constexpr int kFlushPlanes = 3 + kAccHi + 5;  // + butterfly growth over <= 32 lanes
 
 struct OccAcc {
-    uint32_t ones, twos, fours;
-    uint32_t* hi;  // kAccHi planes in shared memory, plane k at hi[32 k] (lane-contiguous)
+    uint32_t ones, twos, fours, hi[kAccHi];
     __device__ __forceinline__ void clear() {
         ones = twos = fours = 0;
 #pragma unroll
-        for (int k = 0; k < kAccHi; ++k) hi[32 * k] = 0;
+        for (int k = 0; k < kAccHi; ++k) hi[k] = 0;
     }
 };
 
@@ -122,10 +121,12 @@ __device__ __forceinline__ void accumulate_phase(OccAcc& a, const uint32_t* X, c
         csa(fb, a.twos, a.twos, ta, tb);
         csa(e, a.fours, a.fours, fa, fb);
         // ripple the eights into the high planes (rarely more than a few)
-        for (int k = 0; k < kAccHi && e; ++k) {
-            const uint32_t h = a.hi[32 * k];
-            a.hi[32 * k] = h ^ e;
-            e &= h;
+#pragma unroll
+        for (int k = 0; k < kAccHi; ++k) {
+            if (!e) break;
+            const uint32_t c = a.hi[k] & e;
+            a.hi[k] ^= e;
+            e = c;
         }
     }
 }
@@ -139,7 +140,7 @@ __device__ __forceinline__ void flush_acc(OccAcc& a, int sub, uint32_t valid, ui
     v[1] = a.twos;
     v[2] = a.fours;
 #pragma unroll
-    for (int k = 0; k < kAccHi; ++k) v[3 + k] = a.hi[32 * k];
+    for (int k = 0; k < kAccHi; ++k) v[3 + k] = a.hi[k];
 #pragma unroll
     for (int k = 3 + kAccHi; k < kFlushPlanes; ++k) v[k] = 0;
 #pragma unroll
@@ -280,10 +281,9 @@ constexpr int kQueueCap = 64;
 constexpr int kQueueItem = 5;  // (m | slot << 16), U, E0, E1, accepted so far
 constexpr int kMaxSlots = 8;
 
-// Per warp after the frames: queue counter and items, the bundles' ids, and
-// the high planes of the lanes' occupancy counters.
+// Per warp after the frames: queue counter and items, and the bundles' ids.
 __host__ __device__ __forceinline__ int warp_aux_words(int bundles) {
-    return 1 + kQueueCap * kQueueItem + bundles * (kMaxSlots + 1) + 32 * kAccHi;
+    return 1 + kQueueCap * kQueueItem + bundles * (kMaxSlots + 1);
 }
 
 // One unit: the bundles of group g handled by this block (warps x 32/LAM
@@ -307,7 +307,6 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
     uint32_t* q_cnt = frames + (blockDim.x >> 5) * B * bundle_stride(p.grp_nq_max) + warp * warp_aux_words(B);
     uint32_t* q_items = q_cnt + 1;
     uint32_t* binfo = q_items + kQueueCap * kQueueItem;  // per slot: w, sid[SLOTS]
-    uint32_t* acc_hi = binfo + B * (kMaxSlots + 1) + lane;  // this lane's high counter planes
 
     // Syndromes and chains of the bundle.
     long long syn[SLOTS];
@@ -401,7 +400,6 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
         if (p.chain_sum) p.chain_sum[ci] = p.init_sum ? p.init_sum[ci] : 0ull;
     }
     OccAcc occ;
-    occ.hi = acc_hi;
     occ.clear();
     const uint32_t qpl = (uint32_t)((nq + LAM - 1) / LAM);  // qubits counted per lane and phase
     const uint32_t flush_every = kAccCapacity / qpl;       // phases before the accumulator could overflow
