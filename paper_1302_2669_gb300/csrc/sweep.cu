@@ -226,7 +226,9 @@ struct PlaneBatch {
 
 // Accept mask of the undecided uphill chains U (all have Delta n = d > 0,
 // d - 1 = E0 + 2 E1 bitwise): chains whose u < T[d], deciding with the digit
-// planes of batches BT0 .. BT1-1.  U keeps the chains still undecided.
+// planes of batches BT0 .. BT1-1.  U keeps the chains still undecided.  The
+// head batches (BT0 = 0) always run in full: some lane of the warp nearly
+// always needs them, so an early exit would only add divergence.
 template <int G, int BT0, int BT1>
 __device__ __forceinline__ uint32_t bernoulli_range(const SweepParams& p, uint32_t& U, uint32_t E0, uint32_t E1,
                                                     const uint32_t* sid, uint32_t w, uint32_t t, uint32_t colm) {
@@ -267,7 +269,9 @@ __device__ __forceinline__ uint32_t bernoulli_range(const SweepParams& p, uint32
                 }
             }
         }
-        if (!U) break;
+        if constexpr (BT0 > 0) {
+            if (!U) break;
+        }
     }
     return acc;
 }
@@ -461,12 +465,10 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                             }
                         }
                     }
-                    if (acc) {
-                        own[sp.x] = o0 ^ acc;
-                        own[sp.y] = o1 ^ acc;
-                        own[sp.z] = o2 ^ acc;
-                        own[sp.w] = o3 ^ acc;
-                    }
+                    own[sp.x] = o0 ^ acc;
+                    own[sp.y] = o1 ^ acc;
+                    own[sp.z] = o2 ^ acc;
+                    own[sp.w] = o3 ^ acc;
                 }
             }
             __syncwarp();
