@@ -218,6 +218,18 @@ int surfmcmc_ragged_plan_create(surfmcmc_ctx* ctx, const int32_t* Ls, const uint
 int surfmcmc_plan_launch(surfmcmc_plan* plan, void* stream);
 void surfmcmc_plan_destroy(surfmcmc_plan* plan);
 
+/* Autotuning of the launch shape (the paper has no counterpart): times the
+ * sweep kernel on n_probe synthetic size-L syndromes for `sweeps` sweeps at
+ * rate p with every supported lanes_per_bundle (2, 4, 8, 16, 32: threads per
+ * 32-chain bundle, hence 32/lanes bundles and 32 x 32/lanes chains per warp)
+ * and records the fastest in ctx for later calls with lanes_per_bundle = 0
+ * and the same (L, chains_per_class); ragged calls use the entry of their
+ * heaviest size.  Results never depend on the choice.  *best receives it and
+ * ms[5] the timings in milliseconds (NaN where the shape does not fit); both
+ * may be NULL.  EINVAL for bad arguments. */
+int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, double p, int64_t n_probe,
+                      uint32_t sweeps, int32_t* best, double* ms);
+
 /* Thermodynamic integration (Eq. 6: log Z_E(beta) = -int_0^beta <n>_{b,E} db
  * + n_stab log 2; Sec. IV: the integral by Simpson's rule; Sec. IV.A: 21
  * equidistant temperatures).  For grid point j = 1..n_beta-1 the chains run

@@ -59,7 +59,7 @@ EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surf
            "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_start_frames", "surfmcmc_decode",
            "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time", "surfmcmc_noalloc_scratch_needed",
            "surfmcmc_decode_noalloc", "surfmcmc_decode_ti", "surfmcmc_decode_ragged", "surfmcmc_ragged_plan_create",
-           "surfmcmc_plan_launch", "surfmcmc_plan_destroy")
+           "surfmcmc_plan_launch", "surfmcmc_plan_destroy", "surfmcmc_autotune")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -94,6 +94,7 @@ def lib():
         L.surfmcmc_ragged_plan_create.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(_Opts), u64, vp, vp, u32, vp, vp, vp,
                                                   C.POINTER(vp)]
         L.surfmcmc_plan_launch.argtypes = [vp, vp]
+        L.surfmcmc_autotune.argtypes = [vp, i32, i32, dbl, i64, u32, C.POINTER(i32), C.POINTER(dbl)]
         L.surfmcmc_plan_destroy.argtypes = [vp]
         L.surfmcmc_plan_destroy.restype = None
         L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
@@ -263,6 +264,13 @@ class Context:
         self._check(lib().surfmcmc_decode_ragged(self._h, _ptr(syndromes), _ptr(Ls), _ptr(n_sweeps), n, p, C.byref(o),
                                                  seed, _ptr(ids), id0, _ptr(cls), _ptr(csum), _ptr(lr), st))
         return cls, csum, lr
+
+    def autotune(self, L, chains_per_class, p, n_probe=4096, sweeps=20):
+        """surfmcmc_autotune: returns (best lanes per bundle, {lanes: ms})."""
+        best = C.c_int32()
+        ms = (C.c_double * 5)()
+        self._check(lib().surfmcmc_autotune(self._h, L, chains_per_class, p, n_probe, sweeps, C.byref(best), ms))
+        return best.value, {lam: ms[i] for i, lam in enumerate((2, 4, 8, 16, 32))}
 
     def set_timing(self, enable: bool):
         """surfmcmc_set_timing: record CUDA events around every sweep kernel."""

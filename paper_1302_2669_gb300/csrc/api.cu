@@ -22,6 +22,7 @@ struct surfmcmc_ctx {
     size_t arena_bytes = 0;
     std::string last_error;
     bool timing = false;
+    std::map<std::pair<int, int>, int> tuned;  // (L, chains per class) -> lanes per bundle
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // recorded around sweep launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
 };
@@ -181,7 +182,7 @@ void set_temperature(SweepParams& sp, double p, double beta_scale) {
     }
 }
 
-int pick_lanes(int L, int requested, int* lam_out) {
+int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nullptr, int R = 0) {
     const int nq = n_qubits(L), nc = L * (L - 1) / 2;
     auto smem_ok = [&](int lam) { return sweep_smem_bytes(nq, nc, lam) <= 200 * 1024; };
     if (requested) {
@@ -191,6 +192,14 @@ int pick_lanes(int L, int requested, int* lam_out) {
         *lam_out = requested;
         return SURFMCMC_OK;
     }
+    if (ctx) {
+        auto it = ctx->tuned.find({L, R});
+        if (it != ctx->tuned.end()) {
+            *lam_out = it->second;
+            return SURFMCMC_OK;
+        }
+    }
+    // heuristic: the most lanes that the colour's generators fill to >= 90%
     int best = 32;
     double best_eff = -1;
     for (int lam = 32; lam >= 2; lam /= 2) {
@@ -202,7 +211,6 @@ int pick_lanes(int L, int requested, int* lam_out) {
     *lam_out = best;
     return SURFMCMC_OK;
 }
-
 
 int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
     if (!(p > 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside (0, 0.75]", p);
@@ -416,7 +424,7 @@ int ragged_layout(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* sweeps, 
     // lanes per bundle for the heaviest group, widened until the largest size fits
     int lmax = 0;
     for (auto& g : lay.groups) lmax = std::max(lmax, g.L);
-    if (pick_lanes(lay.groups.empty() ? 2 : lay.groups[0].L, o.lanes_per_bundle, &lay.lam))
+    if (pick_lanes(lay.groups.empty() ? 2 : lay.groups[0].L, o.lanes_per_bundle, &lay.lam, ctx, o.chains_per_class))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported", o.lanes_per_bundle);
     while (sweep_smem_bytes(n_qubits(lmax), lmax * (lmax - 1) / 2, lay.lam) > 200 * 1024 && lay.lam < 32) lay.lam *= 2;
     const int Cn = 4 * o.chains_per_class;
@@ -719,7 +727,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
         return fail(ctx, SURFMCMC_EINVAL, "sweep_begin > 0 needs init_frames");
     if (n > 0 && (!syndromes || !out_class)) return fail(ctx, SURFMCMC_EINVAL, "NULL syndromes or out_class");
     int lam = 0;
-    if (pick_lanes(L, o.lanes_per_bundle, &lam))
+    if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
     if (n == 0) return SURFMCMC_OK;
     ctx->last_error.clear();
@@ -1025,6 +1033,74 @@ void surfmcmc_plan_destroy(surfmcmc_plan* plan) {
     if (plan->graph) cudaGraphDestroy(plan->graph);
     if (plan->scratch) cudaFree(plan->scratch);
     delete plan;
+}
+
+
+int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, double p, int64_t n_probe,
+                      uint32_t sweeps, int32_t* best_out, double* ms_out) {
+    int rc = check_common(ctx, n_probe, L, 0);
+    if (rc) return rc;
+    if (n_probe < 1 || sweeps < 1 || chains_per_class < 1 || 4 * chains_per_class > 1024 || !(p > 0.0 && p <= 0.75))
+        return fail(ctx, SURFMCMC_EINVAL, "autotune needs n_probe, sweeps >= 1, valid R and p");
+    ctx->last_error.clear();
+    DeviceGuard g(ctx->device);
+    const int R = chains_per_class, Cn = 4 * R, nq = n_qubits(L), W = n_words(L);
+    const int cand[5] = {2, 4, 8, 16, 32};
+    SweepParams base;
+    init_chains(base, Cn, R, 0);
+    Carver cv;
+    const size_t o_syn = cv.reserve((size_t)n_probe * n_stabs(L)), o_e0 = cv.reserve((size_t)n_probe * 2 * W * 4),
+                 o_code = cv.reserve((size_t)n_probe * 4), o_cs = cv.reserve((size_t)n_probe * Cn * 8),
+                 o_ctr = cv.reserve(sizeof(unsigned int));
+    if ((rc = ensure_arena(ctx, cv.off))) return rc;
+    char* b = (char*)ctx->arena;
+    uint8_t* syn = (uint8_t*)(b + o_syn);
+    uint32_t* e0 = (uint32_t*)(b + o_e0);
+    int32_t* code = (int32_t*)(b + o_code);
+    cudaStream_t s;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e_a, e_b;
+    CK(cudaEventCreate(&e_a));
+    CK(cudaEventCreate(&e_b));
+    CK(launch_gen_syndromes(0x7475ull, 0, n_probe, L, p, syn, nullptr, s));
+    CK(launch_start_frames(syn, n_probe, L, e0, code, s));
+    int best = 0;
+    float best_ms = 0.f;
+    for (int i = 0; i < 5; ++i) {
+        if (ms_out) ms_out[i] = NAN;
+        const int lam = cand[i];
+        if (sweep_smem_bytes(nq, L * (L - 1) / 2, lam) > 200 * 1024) continue;
+        SweepParams sp = base;
+        add_group(sp, L, n_probe, 0, 0, 0, 0, lam);
+        set_temperature(sp, p, 1.0);
+        make_round_keys(0x7475u, 0u, &sp.rk);
+        sp.grp[0].t_begin = 0;
+        sp.grp[0].t_end = sweeps;
+        sp.grp[0].burn_in = 0;
+        sp.e0 = e0;
+        sp.e0code = code;
+        sp.chain_sum = (uint64_t*)(b + o_cs);
+        sp.unit_counter = (unsigned int*)(b + o_ctr);
+        CK(launch_sweep(sp, lam, s));  // warm-up
+        CK(cudaEventRecord(e_a, s));
+        CK(launch_sweep(sp, lam, s));
+        CK(cudaEventRecord(e_b, s));
+        CK(cudaEventSynchronize(e_b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e_a, e_b));
+        if (ms_out) ms_out[i] = ms;
+        if (!best || ms < best_ms) {
+            best = lam;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e_a);
+    cudaEventDestroy(e_b);
+    cudaStreamDestroy(s);
+    if (!best) return fail(ctx, SURFMCMC_EINVAL, "no lanes_per_bundle fits L=%d", L);
+    ctx->tuned[{L, R}] = best;
+    if (best_out) *best_out = best;
+    return SURFMCMC_OK;
 }
 
 int surfmcmc_decode(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L, double p,

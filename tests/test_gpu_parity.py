@@ -264,3 +264,19 @@ def test_decode_ti(ctx, pkg, L, R, nb, anneal):
         assert cls[i] == k
         assert (mean[i] == rmean).all()
         assert (lz[i] == rlz).all()
+
+
+def test_autotune_choice_keeps_results(ctx, pkg):
+    """The autotuner picks the fastest lanes-per-bundle for (L, R); decodes
+    with the tuned shape give the same results as any explicit shape."""
+    L, p, R, n = 9, 0.13, 16, 7
+    best, ms = ctx.autotune(L, R, p, n_probe=2048, sweeps=10)
+    assert best in (2, 4, 8, 16, 32)
+    assert ms[best] == min(v for v in ms.values() if v == v)
+    syn, _ = _oracle_syndromes(2222, n, L, p)
+    d = torch.from_numpy(syn).cuda()
+    tuned = ctx.decode_ex(d, L, p, pkg.Opts(chains_per_class=R, n_sweeps=15), seed=3)
+    fixed = ctx.decode_ex(d, L, p, pkg.Opts(chains_per_class=R, n_sweeps=15, lanes_per_bundle=4), seed=3)
+    torch.cuda.synchronize()
+    for k in ("cls", "class_sum", "chain_sum", "chain_frames"):
+        assert (_np(tuned[k]) == _np(fixed[k])).all()
