@@ -61,6 +61,7 @@ extern "C" {
 
 typedef struct surfmcmc_ctx surfmcmc_ctx;
 typedef struct surfmcmc_plan surfmcmc_plan;
+typedef struct surfmcmc_server surfmcmc_server;
 
 /* Decoder options.
  *   n_classes        number of equivalence classes; must be 4 (planar code,
@@ -247,6 +248,55 @@ int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, do
 int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int32_t L, double p,
                        const surfmcmc_opts* opts, int32_t n_beta, uint64_t seed, uint32_t id0, int32_t* out_class,
                        double* out_log_z, double* out_mean, void* stream);
+
+/* Request serving (the paper has no counterpart): continuous batching of
+ * single syndromes of mixed sizes.  Callers submit requests from any thread;
+ * a scheduler thread takes pending requests in arrival order into batches
+ * (at most max_batch; a partial batch waits at most max_wait_us for company),
+ * admits a batch when one of `slots` slots is free and its device scratch
+ * fits memory_budget next to the batches in flight (0 = no budget), and
+ * decodes it with surfmcmc_decode_ragged on the slot's own context and
+ * stream; slots run concurrently, so requests that arrive while others are on
+ * the GPU join the next free slot.  Each slot's scratch is sized at creation
+ * for max_batch syndromes of size max_L, so serving allocates nothing.  A
+ * request's randomness is keyed by its id (the syndrome id of
+ * surfmcmc_decode), so its result is the same alone or in any batch. */
+typedef struct {
+    int32_t max_batch;      /* >= 1 */
+    int32_t slots;          /* 1..64 batches in flight */
+    int32_t max_L;          /* largest code size accepted, 2..SURFMCMC_MAX_L */
+    int64_t memory_budget;  /* bytes of device scratch for the batches in flight; 0 = unlimited */
+    double max_wait_us;     /* longest wait of a partial batch */
+} surfmcmc_server_opts;
+
+/* Defaults: 256 per batch, 4 slots, max_L = SURFMCMC_MAX_L, no budget, 200 us. */
+void surfmcmc_server_default_opts(surfmcmc_server_opts* opts);
+
+/* Creates a server on `device` for rate p with the decoder options `opts`
+ * (opts->n_sweeps and opts->burn_in set each request's burn-in fraction as in
+ * surfmcmc_decode_ragged) and randomness key `seed`.  EINVAL, ENOMEM, ENODEV. */
+int surfmcmc_server_create(int device, double p, const surfmcmc_opts* opts, uint64_t seed,
+                           const surfmcmc_server_opts* server_opts, surfmcmc_server** server);
+
+/* Queues one request: n_stab(L) syndrome bytes (host memory, copied), L <=
+ * max_L, n_sweeps >= 1.  EINVAL for bad arguments or after shutdown began. */
+int surfmcmc_server_submit(surfmcmc_server* server, uint32_t request_id, int32_t L, uint32_t n_sweeps,
+                           const uint8_t* syndrome);
+
+/* Takes up to max_results finished requests (waiting up to wait_us for the
+ * first): ids[k], classes[k] (a negative SURFMCMC_E* code if the batch
+ * failed), class_sums[4k..4k+3] and latency_us[k] (submission to completion)
+ * (the last two may be NULL); *n_out receives the count.  Host buffers. */
+int surfmcmc_server_poll(surfmcmc_server* server, int64_t max_results, uint32_t* ids, int32_t* classes,
+                         uint64_t* class_sums, double* latency_us, int64_t* n_out, int32_t wait_us);
+
+/* Counters since creation: requests admitted to batches, batches launched,
+ * admissions deferred by the memory budget, requests waiting now. */
+int surfmcmc_server_stats(surfmcmc_server* server, int64_t* admitted, int64_t* batches, int64_t* memory_stalls,
+                          int64_t* pending);
+
+/* Finishes every submitted request, then releases the server. */
+void surfmcmc_server_destroy(surfmcmc_server* server);
 
 /* Instrumentation (the paper has no counterpart): with enable != 0 every
  * later decode call records a pair of CUDA events on its stream around its

@@ -38,6 +38,11 @@ class _Opts(C.Structure):
                 ("anneal_stages", C.c_int32), ("anneal_beta0", C.c_double)]
 
 
+class _ServerOpts(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("slots", C.c_int32), ("max_L", C.c_int32), ("memory_budget", C.c_int64),
+                ("max_wait_us", C.c_double)]
+
+
 @dataclasses.dataclass
 class Opts:
     """Mirror of ``surfmcmc_opts``."""
@@ -59,7 +64,9 @@ EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surf
            "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_start_frames", "surfmcmc_decode",
            "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time", "surfmcmc_noalloc_scratch_needed",
            "surfmcmc_decode_noalloc", "surfmcmc_decode_ti", "surfmcmc_decode_ragged", "surfmcmc_ragged_plan_create",
-           "surfmcmc_plan_launch", "surfmcmc_plan_destroy", "surfmcmc_autotune")
+           "surfmcmc_plan_launch", "surfmcmc_plan_destroy", "surfmcmc_autotune", "surfmcmc_server_default_opts",
+           "surfmcmc_server_create", "surfmcmc_server_submit", "surfmcmc_server_poll", "surfmcmc_server_stats",
+           "surfmcmc_server_destroy")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -94,6 +101,14 @@ def lib():
         L.surfmcmc_ragged_plan_create.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(_Opts), u64, vp, vp, u32, vp, vp, vp,
                                                   C.POINTER(vp)]
         L.surfmcmc_plan_launch.argtypes = [vp, vp]
+        L.surfmcmc_server_default_opts.argtypes = [C.POINTER(_ServerOpts)]
+        L.surfmcmc_server_default_opts.restype = None
+        L.surfmcmc_server_create.argtypes = [C.c_int, dbl, C.POINTER(_Opts), u64, C.POINTER(_ServerOpts), C.POINTER(vp)]
+        L.surfmcmc_server_submit.argtypes = [vp, u32, i32, u32, vp]
+        L.surfmcmc_server_poll.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(i64), i32]
+        L.surfmcmc_server_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        L.surfmcmc_server_destroy.argtypes = [vp]
+        L.surfmcmc_server_destroy.restype = None
         L.surfmcmc_autotune.argtypes = [vp, i32, i32, dbl, i64, u32, C.POINTER(i32), C.POINTER(dbl)]
         L.surfmcmc_plan_destroy.argtypes = [vp]
         L.surfmcmc_plan_destroy.restype = None
@@ -304,6 +319,55 @@ class RaggedPlan:
     def close(self):
         if self._h:
             lib().surfmcmc_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """surfmcmc_server_*: continuous batching of single-syndrome requests."""
+
+    def __init__(self, device=0, p=0.12, opts: Opts | None = None, seed=0, max_batch=256, slots=4, max_L=MAX_L,
+                 memory_budget=0, max_wait_us=200.0):
+        self._h = C.c_void_p()
+        so = _ServerOpts(max_batch, slots, max_L, memory_budget, max_wait_us)
+        o = (opts or Opts()).c()
+        rc = lib().surfmcmc_server_create(device, p, C.byref(o), seed, C.byref(so), C.byref(self._h))
+        if rc != OK:
+            raise SurfmcmcError(rc, lib().surfmcmc_strerror(rc).decode())
+
+    def submit(self, request_id: int, L: int, n_sweeps: int, syndrome: np.ndarray):
+        syn = np.ascontiguousarray(syndrome, np.uint8)
+        rc = lib().surfmcmc_server_submit(self._h, request_id, L, n_sweeps, syn.ctypes.data)
+        if rc != OK:
+            raise SurfmcmcError(rc, lib().surfmcmc_strerror(rc).decode())
+
+    def poll(self, max_results=4096, wait_us=0):
+        """Returns (ids, classes, class_sums [k][4], latency_us) of finished requests."""
+        ids = np.empty(max_results, np.uint32)
+        cls = np.empty(max_results, np.int32)
+        sums = np.empty((max_results, 4), np.uint64)
+        lat = np.empty(max_results, np.float64)
+        n = C.c_int64()
+        rc = lib().surfmcmc_server_poll(self._h, max_results, ids.ctypes.data, cls.ctypes.data, sums.ctypes.data,
+                                        lat.ctypes.data, C.byref(n), wait_us)
+        if rc != OK:
+            raise SurfmcmcError(rc, lib().surfmcmc_strerror(rc).decode())
+        k = n.value
+        return ids[:k], cls[:k], sums[:k], lat[:k]
+
+    def stats(self):
+        a, b, m, q = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        lib().surfmcmc_server_stats(self._h, C.byref(a), C.byref(b), C.byref(m), C.byref(q))
+        return {"admitted": a.value, "batches": b.value, "memory_stalls": m.value, "pending": q.value}
+
+    def close(self):
+        if self._h:
+            lib().surfmcmc_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):
