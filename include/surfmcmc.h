@@ -339,6 +339,57 @@ int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int32_t L, doub
                             uint64_t seed, uint32_t id0, int32_t* out_class, uint64_t* out_class_sum,
                             double* out_log_ratio, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Early-stop network.  The paper has no counterpart: a small convolutional
+ * network that reads a syndrome and predicts the posterior of its 4 classes,
+ * used to stop the chains of syndromes whose class is already clear.
+ *   Input: the syndrome of a size-L code as two L x L maps, channel 0 the
+ *   sigma_x generators ((L-1) x L, row i column j = syndrome entry i L + j,
+ *   last row zero), channel 1 the sigma_z generators (L x (L-1), row i column
+ *   j = entry (L-1) L + i (L-1) + j, last column zero).
+ *   Network: five 3x3 convolutions with zero padding, 2 -> 64 -> 64 -> 64 ->
+ *   64 -> 4 channels, bias, ReLU after the first four, mean over the map,
+ *   log-softmax.  Weights and activations are bfloat16 (round to nearest
+ *   even), sums float32 (tensor cores).
+ *   Parameters: surfmcmc_cnn_n_params() float32 values, layer after layer,
+ *   each layer W[co][kh][kw][ci] then b[co].
+ *   Training: mean over the batch of the cross entropy -sum_k q_k log p_k
+ *   against soft targets q, Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * A network object belongs to one context's device; it is not thread-safe.
+ * Every entry point returns EINVAL for bad arguments, ENOMEM/ECUDA for CUDA
+ * failures, and ECUDA if a tensor-core pipeline wait timed out (the device
+ * stays usable).  Pointers may be host or device memory unless stated. */
+typedef struct surfmcmc_cnn surfmcmc_cnn;
+
+int64_t surfmcmc_cnn_n_params(void);
+
+/* Allocates the parameters (all zero until set), the optimizer state and the
+ * activations of up to max_batch (1..2^20) syndromes of size L (3..31). */
+int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcmc_cnn** out);
+void surfmcmc_cnn_destroy(surfmcmc_cnn* net);
+
+/* Copies n_params floats in / out; set_params also clears the Adam state. */
+int surfmcmc_cnn_set_params(surfmcmc_cnn* net, const float* params);
+int surfmcmc_cnn_get_params(surfmcmc_cnn* net, float* params);
+
+/* Log-probabilities [n][4] of n syndromes [n][2L(L-1)] (any n >= 0; batches
+ * of max_batch internally).  Returns after the results are written. */
+int surfmcmc_cnn_forward(surfmcmc_cnn* net, const uint8_t* syndromes, int64_t n, float* out_logprob,
+                         void* stream);
+
+/* Loss (1 float) and its gradient with respect to the parameters (n_params
+ * floats; either output may be NULL) for 1 <= n <= max_batch syndromes and
+ * soft targets [n][4].  Returns after the results are written. */
+int surfmcmc_cnn_gradient(surfmcmc_cnn* net, const uint8_t* syndromes, const float* targets, int64_t n,
+                          float* out_loss, float* out_grad, void* stream);
+
+/* One Adam step with learning rate lr on the gradient of the batch.  With
+ * device inputs and out_loss NULL or device memory the call is stream-ordered
+ * and does not wait; surfmcmc_cnn_status then reports a timed-out wait. */
+int surfmcmc_cnn_train_step(surfmcmc_cnn* net, const uint8_t* syndromes, const float* targets, int64_t n,
+                            float lr, float* out_loss, void* stream);
+int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,7 +66,9 @@ EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surf
            "surfmcmc_decode_noalloc", "surfmcmc_decode_ti", "surfmcmc_decode_ragged", "surfmcmc_ragged_plan_create",
            "surfmcmc_plan_launch", "surfmcmc_plan_destroy", "surfmcmc_autotune", "surfmcmc_server_default_opts",
            "surfmcmc_server_create", "surfmcmc_server_submit", "surfmcmc_server_poll", "surfmcmc_server_stats",
-           "surfmcmc_server_destroy")
+           "surfmcmc_server_destroy", "surfmcmc_cnn_n_params", "surfmcmc_cnn_create", "surfmcmc_cnn_destroy",
+           "surfmcmc_cnn_set_params", "surfmcmc_cnn_get_params", "surfmcmc_cnn_forward", "surfmcmc_cnn_gradient",
+           "surfmcmc_cnn_train_step", "surfmcmc_cnn_status")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -112,6 +114,17 @@ def lib():
         L.surfmcmc_autotune.argtypes = [vp, i32, i32, dbl, i64, u32, C.POINTER(i32), C.POINTER(dbl)]
         L.surfmcmc_plan_destroy.argtypes = [vp]
         L.surfmcmc_plan_destroy.restype = None
+        L.surfmcmc_cnn_n_params.argtypes = []
+        L.surfmcmc_cnn_n_params.restype = i64
+        L.surfmcmc_cnn_create.argtypes = [vp, i32, i64, C.POINTER(vp)]
+        L.surfmcmc_cnn_destroy.argtypes = [vp]
+        L.surfmcmc_cnn_destroy.restype = None
+        L.surfmcmc_cnn_set_params.argtypes = [vp, vp]
+        L.surfmcmc_cnn_get_params.argtypes = [vp, vp]
+        L.surfmcmc_cnn_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.surfmcmc_cnn_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        L.surfmcmc_cnn_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
+        L.surfmcmc_cnn_status.argtypes = [vp, vp]
         L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
         L.surfmcmc_sweep_time.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         _lib = L
@@ -153,7 +166,7 @@ def _empty(like, shape, np_dtype):
     if like is not None and _is_torch(like):
         import torch
         tdt = {np.uint8: torch.uint8, np.int32: torch.int32, np.uint32: torch.uint32, np.uint64: torch.uint64,
-               np.float64: torch.float64}[np_dtype]
+               np.float64: torch.float64, np.float32: torch.float32}[np_dtype]
         return torch.empty(shape, dtype=tdt, device=like.device)
     return np.empty(shape, dtype=np_dtype)
 
@@ -368,6 +381,78 @@ class Server:
     def close(self):
         if self._h:
             lib().surfmcmc_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Network:
+    """surfmcmc_cnn_*: the early-stop network (five 3x3 convolutions on the
+    two syndrome maps, tensor-core forward and backward, Adam)."""
+
+    def __init__(self, ctx: Context, L: int, max_batch: int = 4096):
+        self._ctx = ctx
+        self._h = C.c_void_p()
+        self.L = L
+        self.max_batch = max_batch
+        ctx._check(lib().surfmcmc_cnn_create(ctx._h, L, max_batch, C.byref(self._h)))
+
+    @staticmethod
+    def n_params() -> int:
+        return int(lib().surfmcmc_cnn_n_params())
+
+    def set_params(self, params):
+        """Float32 parameters (numpy or torch, host or device)."""
+        if not _is_torch(params):
+            params = np.ascontiguousarray(params, np.float32)
+        self._ctx._check(lib().surfmcmc_cnn_set_params(self._h, _ptr(params)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params(), np.float32)
+        self._ctx._check(lib().surfmcmc_cnn_get_params(self._h, _ptr(out)))
+        return out
+
+    def forward(self, syndromes, out=None, stream=None):
+        """Log-probabilities [n][4] (float32), beside `syndromes`."""
+        n = syndromes.shape[0]
+        if out is None:
+            out = _empty(syndromes, (n, 4), np.float32)
+        st = stream if stream is not None else _stream_of(syndromes, out)
+        self._ctx._check(lib().surfmcmc_cnn_forward(self._h, _ptr(syndromes), n, _ptr(out), st))
+        return out
+
+    def gradient(self, syndromes, targets, stream=None):
+        """(loss, flat gradient float32 numpy) of the batch."""
+        n = syndromes.shape[0]
+        loss = np.zeros(1, np.float32)
+        grad = np.empty(self.n_params(), np.float32)
+        st = stream if stream is not None else _stream_of(syndromes, targets)
+        self._ctx._check(lib().surfmcmc_cnn_gradient(self._h, _ptr(syndromes), _ptr(targets), n, _ptr(loss),
+                                                     _ptr(grad), st))
+        return float(loss[0]), grad
+
+    def train_step(self, syndromes, targets, lr, loss_out=None, stream=None):
+        """One Adam step; returns the loss (float) unless `loss_out` (a device
+        tensor of 1 float) receives it without a host wait."""
+        n = syndromes.shape[0]
+        st = stream if stream is not None else _stream_of(syndromes, targets)
+        host = loss_out is None
+        if host:
+            loss_out = np.zeros(1, np.float32)
+        self._ctx._check(lib().surfmcmc_cnn_train_step(self._h, _ptr(syndromes), _ptr(targets), n, lr,
+                                                       _ptr(loss_out), st))
+        return float(loss_out[0]) if host else None
+
+    def status(self, stream=None):
+        self._ctx._check(lib().surfmcmc_cnn_status(self._h, stream))
+
+    def close(self):
+        if self._h:
+            lib().surfmcmc_cnn_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

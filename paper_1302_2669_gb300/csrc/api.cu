@@ -579,6 +579,18 @@ struct surfmcmc_plan {
     cudaGraphExec_t exec = nullptr;
 };
 
+namespace surfmcmc {
+
+void ctx_set_error(surfmcmc_ctx* ctx, const char* msg) {
+    if (ctx) ctx->last_error = msg;
+}
+
+int ctx_device(const surfmcmc_ctx* ctx) { return ctx->device; }
+
+bool device_ptr(const void* p) { return is_device_ptr(p); }
+
+}  // namespace surfmcmc
+
 extern "C" {
 
 void surfmcmc_default_opts(surfmcmc_opts* o) {

@@ -1,0 +1,1245 @@
+// The early-stop network on the GPU: five 3x3 convolutions over the two
+// syndrome maps of a size-L code (2 -> 64 -> 64 -> 64 -> 64 -> 4, ReLU after
+// the first four), global average pool and log-softmax; training by the
+// cross entropy with soft targets and Adam.
+//
+// Layouts: activations are NHWC bfloat16, [M][C] with M = n L^2 positions
+// (syndrome-major, then row, then column).  Weights live as float32 master
+// copies in the flat order W[co][kh][kw][ci] then b[co], layer after layer;
+// every step packs them into bfloat16 GEMM operands.
+//
+// Tensor-core work (tcgen05, BF16 in, FP32 accumulate in tensor memory):
+//   forward conv and input-gradient conv: an implicit GEMM, M = positions in
+//     tiles of 128, N = output channels, K = 9 C_in taken one 3x3 tap (64
+//     channels) per pipeline stage; the weight operand stays in shared memory
+//     for the whole persistent block; warps 0-3 gather the shifted activation
+//     rows, warp 8 issues the MMAs, warps 4-7 drain the two tensor-memory
+//     accumulators (bias + ReLU, or the ReLU mask of the layer below);
+//   weight gradient: D[(tap, ci)][co] = sum_p X[p + tap][ci] dZ[p][co], a
+//     GEMM over positions split across blocks, with a row of ones that yields
+//     the bias gradient; partial sums are added in a fixed order.
+// The last layer (4 outputs whose gradient is constant over a map) and the
+// pool, loss and Adam steps run on the CUDA cores.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "surfmcmc.h"
+#include "common.cuh"
+
+namespace surfmcmc {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kHid = 64;          // hidden channels
+constexpr int kCls = 4;           // classes
+constexpr int kProdWarps = 4;     // gather warps
+constexpr int kEpiWarps = 4;      // accumulator-draining warps
+constexpr int kConvThreads = (kProdWarps + kEpiWarps + 1) * 32;
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kWaitTimeout = 1;   // error codes written to the device flag
+constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
+
+// Channels of the five layers and the offsets of their weights and biases in
+// the flat parameter vector.
+__host__ __device__ constexpr int layer_cin(int l) { return l == 0 ? 2 : kHid; }
+__host__ __device__ constexpr int layer_cout(int l) { return l == 4 ? kCls : kHid; }
+__host__ __device__ constexpr long long layer_woff(int l) {
+    long long o = 0;
+    for (int i = 0; i < l; ++i) o += (long long)layer_cout(i) * 9 * layer_cin(i) + layer_cout(i);
+    return o;
+}
+__host__ __device__ constexpr long long layer_boff(int l) {
+    return layer_woff(l) + (long long)layer_cout(l) * 9 * layer_cin(l);
+}
+constexpr long long kParams = layer_woff(5);
+static_assert(kParams == 114308, "parameter count");
+
+// GEMM operand shapes of the forward conv of each layer: N rows (output
+// channels, padded to a multiple of 16) by K columns (9 C_in, padded to a
+// multiple of 16).
+__host__ __device__ constexpr int fwd_np(int l) { return l == 4 ? 16 : kHid; }
+__host__ __device__ constexpr int fwd_kp(int l) { return l == 0 ? 32 : 9 * kHid; }
+
+// ---------------------------------------------------------------------------
+// tcgen05 / mbarrier helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major: core matrices of
+// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
+// byte step between groups of 8 rows.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16 with bf16 A and B, f32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element group (row r, 16-byte group g) in a K-major
+// no-swizzle tile whose rows hold kg groups.
+__device__ __forceinline__ uint32_t core_off(int r, int g, int kg) {
+    return (uint32_t)(((r >> 3) * kg + g) * 128 + (r & 7) * 16);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the completion of the phase of the given parity.  Gives up
+// when another role of the block has given up, or after kSpinLimit polls (then
+// records the time-out in the device error flag and raises the block's abort
+// flag so that every other wait of the block returns too).
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 31) == 31 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicExch(err, kWaitTimeout);
+    return false;
+}
+
+// Bounded wait used before tensor memory is released: ignores the abort flag,
+// so that MMAs still in flight complete first.
+__device__ void mbar_drain(uint64_t* bar, uint32_t parity, int* err) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try(bar, parity)) return;
+    atomicExch(err, kWaitTimeout);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Arrives on the barrier once every tcgen05 operation issued so far by this
+// thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive f32 columns of this warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// ---------------------------------------------------------------------------
+// Implicit-GEMM 3x3 conv on tcgen05 (forward and input gradient).
+// ---------------------------------------------------------------------------
+enum Epi { kEpiRelu = 0, kEpiLogit = 1, kEpiMask = 2 };
+
+struct ConvArgs {
+    const bf16* act;     // [M][CIN] input of the conv
+    const bf16* wmat;    // [NP][KP] operand B (k = tap * CIN + ci)
+    const float* bias;   // [NP] (kEpiRelu, kEpiLogit) or NULL
+    const bf16* mask;    // [M][64] ReLU gate (kEpiMask) or NULL
+    bf16* out_bf16;      // [M][64] (kEpiRelu, kEpiMask)
+    float* out_f32;      // [M][4]  (kEpiLogit)
+    long long M;
+    int L;
+    int* err;
+};
+
+template <int CIN>
+struct ConvShape {
+    static constexpr int KP = CIN == 2 ? 32 : 9 * CIN;   // K of the GEMM, padded
+    static constexpr int KC = CIN == 2 ? 32 : CIN;       // K per pipeline stage (one tap)
+    static constexpr int NCH = KP / KC;                  // stages per tile
+    static constexpr int KGS = KC / 8;                   // 16-byte groups per stage row
+    static constexpr int KG = KP / 8;                    // 16-byte groups per B row
+    static constexpr int STAGE_BYTES = 128 * KC * 2;
+    static constexpr int S = 4;                          // pipeline depth
+};
+
+template <int CIN, int NP>
+constexpr size_t conv_smem_bytes() {
+    return (size_t)((NP * ConvShape<CIN>::KP * 2 + 1023) / 1024 * 1024) +
+           (size_t)ConvShape<CIN>::S * ConvShape<CIN>::STAGE_BYTES + 1024;
+}
+
+template <int CIN, int NP, int EPI>
+__global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
+    typedef ConvShape<CIN> Sh;
+    constexpr int S = Sh::S;
+    constexpr uint32_t NCOLS = 2 * NP < 32 ? 32 : 2 * NP;
+    constexpr uint32_t IDESC = idesc_bf16(128, NP);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sB = smem;
+    uint8_t* sA = smem + (NP * Sh::KP * 2 + 1023) / 1024 * 1024;
+    __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = a.M;
+    const int L = a.L, LL = L * L;
+    const long long n_tiles = (M + 127) / 128;
+
+    // resident weight operand
+    for (int idx = tid; idx < NP * Sh::KG; idx += kConvThreads) {
+        const int r = idx / Sh::KG, g = idx - r * Sh::KG;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.wmat + (size_t)r * Sh::KP) + g);
+        *reinterpret_cast<uint4*>(sB + core_off(r, g, Sh::KG)) = v;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], kProdWarps * 32);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], kEpiWarps * 32);
+        }
+        mbar_init(&fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();
+    if (warp == kProdWarps + kEpiWarps) tmem_alloc(&tmem_slot, NCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp < kProdWarps) {
+        // ---------------- gather: tap c of the tile's 128 positions --------
+        uint32_t q = 0;
+        bool ok = true;
+        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            constexpr int ROWS = 4;  // rows per thread
+            int ry[ROWS], rx[ROWS];
+            long long rm[ROWS];
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int r = warp * 32 + (lane & 7) + 8 * i;
+                const long long m = tile * 128 + r;
+                rm[i] = m;
+                if (m < M) {
+                    const int rem = (int)(m % LL);
+                    ry[i] = rem / L;
+                    rx[i] = rem - ry[i] * L;
+                } else {
+                    ry[i] = -1000;  // every neighbour out of range
+                    rx[i] = -1000;
+                }
+            }
+            for (int c = 0; c < Sh::NCH; ++c, ++q) {
+                const uint32_t stage = q % S, use = q / S;
+                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* st = sA + stage * Sh::STAGE_BYTES;
+                if (CIN == 2) {
+                    // K = 18 (9 taps x 2 channels) padded to 32: group g holds taps 4g..4g+3
+                    const int g = lane >> 3;
+#pragma unroll
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int r = warp * 32 + (lane & 7) + 8 * i;
+                        uint32_t w[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int t = 4 * g + j;
+                            const int dy = t / 3 - 1, dx = t % 3 - 1;
+                            const int yy = ry[i] + dy, xx = rx[i] + dx;
+                            w[j] = 0;
+                            if (t < 9 && yy >= 0 && yy < L && xx >= 0 && xx < L)
+                                w[j] = __ldg(reinterpret_cast<const uint32_t*>(a.act) + rm[i] + dy * L + dx);
+                        }
+                        *reinterpret_cast<uint4*>(st + core_off(r, g, Sh::KGS)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+                    const int dy = c / 3 - 1, dx = c % 3 - 1;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int ri = i >> 1;
+                        const int r = warp * 32 + (lane & 7) + 8 * ri;
+                        const int g = (lane >> 3) + 4 * (i & 1);
+                        const int yy = ry[ri] + dy, xx = rx[ri] + dx;
+                        uint4 v = make_uint4(0, 0, 0, 0);
+                        if (yy >= 0 && yy < L && xx >= 0 && xx < L)
+                            v = __ldg(reinterpret_cast<const uint4*>(a.act + (rm[ri] + dy * L + dx) * CIN) + g);
+                        *reinterpret_cast<uint4*>(st + core_off(r, g, Sh::KGS)) = v;
+                    }
+                }
+                fence_async_smem();
+                mbar_arrive(&full[stage]);
+            }
+        }
+    } else if (warp < kProdWarps + kEpiWarps) {
+        // ---------------- drain the accumulators ---------------------------
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        uint32_t it = 0;
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            const uint32_t b = it & 1, u = it >> 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[b], u & 1, &abort_flag, a.err));
+            if (!ok) break;
+            tc_fence_after();
+            const long long m = tile * 128 + row;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
+            if (EPI == kEpiLogit) {
+                float v[16];
+                tmem_ld16(taddr, v);
+                if (m < M) {
+                    float4 o;
+                    o.x = v[0] + __ldg(a.bias + 0);
+                    o.y = v[1] + __ldg(a.bias + 1);
+                    o.z = v[2] + __ldg(a.bias + 2);
+                    o.w = v[3] + __ldg(a.bias + 3);
+                    *reinterpret_cast<float4*>(a.out_f32 + m * 4) = o;
+                }
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < NP / 16; ++cc) {
+                    float v[16];
+                    tmem_ld16(taddr + cc * 16, v);
+                    if (m < M) {
+                        uint32_t w[8];
+                        if (EPI == kEpiRelu) {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float x0 = fmaxf(v[2 * j] + __ldg(a.bias + cc * 16 + 2 * j), 0.0f);
+                                const float x1 = fmaxf(v[2 * j + 1] + __ldg(a.bias + cc * 16 + 2 * j + 1), 0.0f);
+                                w[j] = pack_bf16(x0, x1);
+                            }
+                        } else {
+                            const uint4* mp = reinterpret_cast<const uint4*>(a.mask + m * 64 + cc * 16);
+                            const uint4 m0 = __ldg(mp), m1 = __ldg(mp + 1);
+                            const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float x0 = bf16_lo(mw[j]) > 0.0f ? v[2 * j] : 0.0f;
+                                const float x1 = bf16_hi(mw[j]) > 0.0f ? v[2 * j + 1] : 0.0f;
+                                w[j] = pack_bf16(x0, x1);
+                            }
+                        }
+                        uint4* op = reinterpret_cast<uint4*>(a.out_bf16 + m * 64 + cc * 16);
+                        op[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                        op[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[b]);
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issue ----------------------------------------
+        uint32_t q = 0, it = 0;
+        bool ok = true;
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+            const uint32_t b = it & 1, u = it >> 1;
+            if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + b * NP;
+            for (int c = 0; c < Sh::NCH; ++c, ++q) {
+                const uint32_t stage = q % S, use = q / S;
+                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int ks = 0; ks < Sh::KC / 16; ++ks) {
+                    const uint64_t ad = smem_desc(a0 + stage * Sh::STAGE_BYTES + ks * 256, 128, Sh::KGS * 128);
+                    const uint64_t bd = smem_desc(b0 + (c * Sh::KGS + ks * 2) * 128, 128, Sh::KG * 128);
+                    mma_bf16(d, ad, bd, IDESC, (c > 0 || ks > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[stage]);
+            }
+            if (ok) mma_commit(&accf[b]);
+        }
+        // every MMA of this block has completed before the memory is released
+        mma_commit(&fin);
+        mbar_drain(&fin, 0, a.err);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kProdWarps + kEpiWarps) tmem_dealloc(tmem, NCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05: D[R][co] = sum_p A[R][p] dZ[p][co] with
+// A[(tap, ci)][p] = X[p + offset(tap)][ci] (zero outside the map) and row
+// R = 9 CIN all ones (bias gradient).  Grid (slices, row tiles); each block
+// sums one slice of the positions into partial[slice][R][co].
+// ---------------------------------------------------------------------------
+struct WgradArgs {
+    const bf16* x;      // [M][CIN] input of the layer
+    const bf16* dz;     // [M][64] gradient of the layer's pre-activation
+    float* partial;     // [slices][row_tiles * 128][64]
+    long long M;
+    int L;
+    int* err;
+};
+
+constexpr int kWgS = 4;                         // pipeline depth
+constexpr int kWgAStage = 128 * 64 * 2;         // 128 rows x 64 positions
+constexpr int kWgBStage = 64 * 64 * 2;          // 64 channels x 64 positions
+constexpr size_t kWgSmem = (size_t)kWgS * (kWgAStage + kWgBStage) + 1024;
+
+template <int CIN>
+__global__ void __launch_bounds__(kConvThreads, 2) wgrad_kernel(WgradArgs a) {
+    constexpr uint32_t IDESC = idesc_bf16(128, 64);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kWgS * kWgAStage;
+    __shared__ __align__(8) uint64_t full[kWgS], empty[kWgS], accf;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int pos_yx[kProdWarps][64];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = a.M;
+    const int L = a.L, LL = L * L;
+    const long long n_chunks = (M + 63) / 64;
+    const int slice = blockIdx.x, n_slices = gridDim.x, mt = blockIdx.y;
+    const long long c_begin = n_chunks * slice / n_slices, c_end = n_chunks * (slice + 1) / n_slices;
+
+    if (tid == 0) {
+        for (int s = 0; s < kWgS; ++s) {
+            mbar_init(&full[s], kProdWarps * 32);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accf, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kProdWarps + kEpiWarps) tmem_alloc(&tmem_slot, 64);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp < kProdWarps) {
+        // row of A owned by this thread
+        const int R = mt * 128 + tid;
+        const int tap = R / CIN, ci = R - (R / CIN) * CIN;
+        const int kind = R < 9 * CIN ? 0 : (R == 9 * CIN ? 1 : 2);  // data, ones, zero
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const unsigned short* xs = reinterpret_cast<const unsigned short*>(a.x);
+        const unsigned short* zs = reinterpret_cast<const unsigned short*>(a.dz);
+        const int co = tid & 63, half = tid >> 6;
+        uint32_t q = 0;
+        for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
+            const uint32_t stage = q % kWgS, use = q / kWgS;
+            if (use > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)))
+                break;  // warp-uniform: the loop below has warp-wide syncs
+            // positions of this chunk: (y << 8) | x, or -1 past the end
+            for (int j = lane; j < 64; j += 32) {
+                const long long p = ch * 64 + j;
+                int v = -1;
+                if (p < M) {
+                    const int rem = (int)(p % LL);
+                    const int y = rem / L;
+                    v = (y << 8) | (rem - y * L);
+                }
+                pos_yx[warp][j] = v;
+            }
+            __syncwarp();
+            uint8_t* stA = sA + stage * kWgAStage;
+            uint8_t* stB = sB + stage * kWgBStage;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    unsigned short e[2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int j = g * 8 + h * 2 + k;
+                        const int yx = pos_yx[warp][j];
+                        unsigned short val = 0;
+                        if (yx >= 0) {
+                            if (kind == 0) {
+                                const int yy = (yx >> 8) + dy, xx = (yx & 255) + dx;
+                                if (yy >= 0 && yy < L && xx >= 0 && xx < L)
+                                    val = __ldg(xs + (ch * 64 + j + dy * L + dx) * CIN + ci);
+                            } else if (kind == 1) {
+                                val = 0x3F80;  // 1.0
+                            }
+                        }
+                        e[k] = val;
+                    }
+                    w[h] = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
+                }
+                *reinterpret_cast<uint4*>(stA + core_off(tid, g, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg) {
+                const int g = half * 4 + gg;
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    unsigned short e[2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int j = g * 8 + h * 2 + k;
+                        e[k] = pos_yx[warp][j] >= 0 ? __ldg(zs + (ch * 64 + j) * 64 + co) : (unsigned short)0;
+                    }
+                    w[h] = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
+                }
+                *reinterpret_cast<uint4*>(stB + core_off(co, g, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            __syncwarp();  // pos_yx is rewritten by the next chunk
+            fence_async_smem();
+            mbar_arrive(&full[stage]);
+        }
+    } else if (warp < kProdWarps + kEpiWarps) {
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        float* out = a.partial + (((long long)slice * gridDim.y + mt) * 128 + row) * 64;
+        if (c_end > c_begin) {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err));
+            if (ok) {
+                tc_fence_after();
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + cc * 16, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(out + cc * 16 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+            }
+        } else {
+            for (int j = 0; j < 64; j += 4) *reinterpret_cast<float4*>(out + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else if (lane == 0) {
+        uint32_t q = 0;
+        bool ok = true;
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
+            const uint32_t stage = q % kWgS, use = q / kWgS;
+            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t ad = smem_desc(a0 + stage * kWgAStage + ks * 256, 128, 8 * 128);
+                const uint64_t bd = smem_desc(b0 + stage * kWgBStage + ks * 256, 128, 8 * 128);
+                mma_bf16(tmem, ad, bd, IDESC, (ch > c_begin || ks > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[stage]);
+        }
+        // completes after every MMA of the block (also on the abort path)
+        mma_commit(&accf);
+        if (!ok || c_end == c_begin) mbar_drain(&accf, 0, a.err);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kProdWarps + kEpiWarps) tmem_dealloc(tmem, 64);
+}
+
+// partial[s][R][co] summed over s in order -> flat gradient of layer l.
+__global__ void wgrad_reduce_kernel(const float* partial, int n_slices, int rows_pad, int cin, float* grad_w,
+                                    float* grad_b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // R * 64 + co
+    const int R = i >> 6, co = i & 63;
+    if (R > 9 * cin) return;
+    float s = 0.0f;
+    for (int k = 0; k < n_slices; ++k) s += partial[((long long)k * rows_pad + R) * 64 + co];
+    if (R < 9 * cin) grad_w[(long long)co * 9 * cin + R] = s;
+    else grad_b[co] = s;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core kernels
+// ---------------------------------------------------------------------------
+
+// Syndromes [n][2L(L-1)] -> input maps [n L^2][2]: channel 0 the sigma_x
+// generators ((L-1) x L, last row zero), channel 1 the sigma_z generators
+// (L x (L-1), last column zero).
+__global__ void input_maps_kernel(const uint8_t* syn, long long n, int L, bf16* x0) {
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long LL = (long long)L * L;
+    if (m >= n * LL) return;
+    const long long item = m / LL;
+    const int rem = (int)(m - item * LL), y = rem / L, x = rem - (rem / L) * L;
+    const uint8_t* s = syn + item * 2 * L * (L - 1);
+    const float c0 = y < L - 1 ? (float)(s[y * L + x] & 1) : 0.0f;
+    const float c1 = x < L - 1 ? (float)(s[L * (L - 1) + y * (L - 1) + x] & 1) : 0.0f;
+    reinterpret_cast<uint32_t*>(x0)[m] = pack_bf16(c0, c1);
+}
+
+// Master weights -> bf16 GEMM operands.  Forward operand of layer l:
+// [np][kp], row co, column tap * cin + ci, zero padded.  Input-gradient
+// operand of layers 1..3: [64][576], row ci, column tap' * 64 + co holding
+// W[co][8 - tap'][ci] (the kernel flipped in both directions).
+struct PackArgs {
+    const float* theta;
+    bf16* fwd[5];
+    bf16* bwd[3];
+    long long fwd_begin[6];
+    long long total;
+};
+
+__global__ void pack_kernel(PackArgs a) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.total) return;
+    if (i < a.fwd_begin[5]) {
+        int l = 0;
+        while (i >= a.fwd_begin[l + 1]) ++l;
+        const long long j = i - a.fwd_begin[l];
+        const int kp = fwd_kp(l), cin = layer_cin(l);
+        const int co = (int)(j / kp), k = (int)(j - (long long)co * kp);
+        float v = 0.0f;
+        if (co < layer_cout(l) && k < 9 * cin) v = a.theta[layer_woff(l) + (long long)co * 9 * cin + k];
+        a.fwd[l][j] = __float2bfloat16_rn(v);
+    } else {
+        const long long j = i - a.fwd_begin[5];
+        const int l = (int)(j / (64 * 576)) + 1;
+        const int jj = (int)(j - (long long)(l - 1) * 64 * 576);
+        const int ci = jj / 576, k = jj - ci * 576, tapf = k / 64, co = k - tapf * 64;
+        const float v = a.theta[layer_woff(l) + (long long)co * 576 + (8 - tapf) * 64 + ci];
+        a.bwd[l - 1][jj] = __float2bfloat16_rn(v);
+    }
+}
+
+// One warp per syndrome: mean of the last layer over the map, log-softmax,
+// and with targets the loss and d loss / d z5 (= (softmax - q) / (n L^2),
+// the same at every position of the map).
+__global__ void pool_loss_kernel(const float* z5, long long n, int L, const float* targets, float* logprob,
+                                 float* g5, float* loss_item) {
+    const long long item = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (item >= n) return;
+    const int LL = L * L;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int p = lane; p < LL; p += 32) {
+        const float4 v = *reinterpret_cast<const float4*>(z5 + (item * LL + p) * 4);
+        s[0] += v.x;
+        s[1] += v.y;
+        s[2] += v.z;
+        s[3] += v.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if (lane != 0) return;
+    float z[4], mx = -INFINITY;
+    for (int k = 0; k < 4; ++k) {
+        z[k] = s[k] / (float)LL;
+        mx = fmaxf(mx, z[k]);
+    }
+    float se = 0.0f;
+    for (int k = 0; k < 4; ++k) se += expf(z[k] - mx);
+    const float lse = mx + logf(se);
+    float lp[4];
+    for (int k = 0; k < 4; ++k) {
+        lp[k] = z[k] - lse;
+        if (logprob) logprob[item * 4 + k] = lp[k];
+    }
+    if (targets) {
+        float loss = 0.0f;
+        for (int k = 0; k < 4; ++k) {
+            const float q = targets[item * 4 + k];
+            loss -= q * lp[k];
+            g5[item * 4 + k] = (expf(lp[k]) - q) / ((float)n * (float)LL);
+        }
+        loss_item[item] = loss;
+    }
+}
+
+// Sum of the per-item losses in a fixed order, divided by n.
+__global__ void loss_sum_kernel(const float* loss_item, long long n, float* loss) {
+    __shared__ float part[256];
+    float s = 0.0f;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += loss_item[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = part[0] / (float)n;
+}
+
+// Input gradient of the last layer, gated by the ReLU of layer 4:
+// dZ4[q][ci] = [a4[q][ci] > 0] sum over taps (kh, kw) with q - (kh-1, kw-1)
+// inside the map of sum_co W5[co][kh][kw][ci] g5[item][co].
+__global__ void conv5_dgrad_kernel(const bf16* w5, const float* g5, const bf16* a4, long long M, int L,
+                                   bf16* dz4) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // m * 8 + ci group
+    if (i >= M * 8) return;
+    const long long m = i >> 3;
+    const int cg = (int)(i & 7) * 8;
+    const int LL = L * L;
+    const long long item = m / LL;
+    const int rem = (int)(m - item * LL), y = rem / L, x = rem - (rem / L) * L;
+    float g[4];
+    for (int co = 0; co < 4; ++co) g[co] = g5[item * 4 + co];
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t < 9; ++t) {
+        const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+        if (yy < 0 || yy >= L || xx < 0 || xx >= L) continue;
+        for (int co = 0; co < 4; ++co) {
+            const uint4 wv = *reinterpret_cast<const uint4*>(w5 + (long long)co * 576 + t * 64 + cg);
+            const uint32_t ww[4] = {wv.x, wv.y, wv.z, wv.w};
+            for (int j = 0; j < 4; ++j) {
+                acc[2 * j] += bf16_lo(ww[j]) * g[co];
+                acc[2 * j + 1] += bf16_hi(ww[j]) * g[co];
+            }
+        }
+    }
+    const uint4 av = *reinterpret_cast<const uint4*>(a4 + m * 64 + cg);
+    const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
+    uint32_t o[4];
+    for (int j = 0; j < 4; ++j)
+        o[j] = pack_bf16(bf16_lo(aw[j]) > 0.0f ? acc[2 * j] : 0.0f, bf16_hi(aw[j]) > 0.0f ? acc[2 * j + 1] : 0.0f);
+    *reinterpret_cast<uint4*>(dz4 + m * 64 + cg) = make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+// Box sums of layer 4 under each tap: S[item][tap][ci] = sum over positions
+// p of the map with p + offset(tap) inside of a4[p + offset(tap)][ci].
+__global__ void conv5_boxsum_kernel(const bf16* a4, int L, float* S) {
+    const long long item = blockIdx.x;
+    const int t = threadIdx.x >> 6, ci = threadIdx.x & 63;  // blockDim 576
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    const int y0 = dy > 0 ? dy : 0, y1 = dy < 0 ? L + dy : L;
+    const int x0 = dx > 0 ? dx : 0, x1 = dx < 0 ? L + dx : L;
+    const bf16* a = a4 + item * L * L * 64;
+    float s = 0.0f;
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) s += __bfloat162float(a[(y * L + x) * 64 + ci]);
+    S[item * 576 + threadIdx.x] = s;
+}
+
+// Last-layer weight and bias gradients: dW5[co][j] = sum_item g5[item][co]
+// S[item][j]; db5[co] = L^2 sum_item g5[item][co].  Items in order.
+__global__ void conv5_wgrad_kernel(const float* S, const float* g5, long long n, int L, float* grad_w,
+                                   float* grad_b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 4 * 576) {
+        const int co = i / 576, j = i - co * 576;
+        float s = 0.0f;
+        for (long long k = 0; k < n; ++k) s += g5[k * 4 + co] * S[k * 576 + j];
+        grad_w[i] = s;
+    } else if (i < 4 * 576 + 4) {
+        const int co = i - 4 * 576;
+        float s = 0.0f;
+        for (long long k = 0; k < n; ++k) s += g5[k * 4 + co];
+        grad_b[co] = s * (float)(L * L);
+    }
+}
+
+__global__ void adam_kernel(float* theta, float* m1, float* m2, const float* grad, long long n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float a = b1 * m1[i] + (1.0f - b1) * g;
+    const float b = b2 * m2[i] + (1.0f - b2) * g * g;
+    m1[i] = a;
+    m2[i] = b;
+    theta[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Network state and its launches
+// ---------------------------------------------------------------------------
+struct CnnNet {
+    surfmcmc_ctx* ctx = nullptr;
+    int device = 0, L = 0, sms = 0;
+    long long max_batch = 0;
+    long long step = 0;
+    // parameters (float32) and Adam moments, gradient
+    float *theta = nullptr, *m1 = nullptr, *m2 = nullptr, *grad = nullptr;
+    // packed operands
+    bf16* fwd[5] = {};
+    bf16* bwd[3] = {};
+    // activations and gradients for max_batch syndromes
+    uint8_t* syn = nullptr;
+    float* targets = nullptr;
+    bf16* x0 = nullptr;
+    bf16* act[4] = {};
+    float* z5 = nullptr;
+    bf16* dz[2] = {};
+    float *logprob = nullptr, *g5 = nullptr, *loss_item = nullptr, *loss = nullptr, *S5 = nullptr;
+    float* partial = nullptr;
+    int* err = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+cudaError_t net_alloc(CnnNet* net, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) net->allocs.push_back(*p);
+    return e;
+}
+
+cudaError_t prepare_kernels() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e;
+    if ((e = set_smem(conv_kernel<2, 64, kEpiRelu>, conv_smem_bytes<2, 64>()))) return e;
+    if ((e = set_smem(conv_kernel<64, 64, kEpiRelu>, conv_smem_bytes<64, 64>()))) return e;
+    if ((e = set_smem(conv_kernel<64, 16, kEpiLogit>, conv_smem_bytes<64, 16>()))) return e;
+    if ((e = set_smem(conv_kernel<64, 64, kEpiMask>, conv_smem_bytes<64, 64>()))) return e;
+    if ((e = set_smem(wgrad_kernel<2>, kWgSmem))) return e;
+    if ((e = set_smem(wgrad_kernel<64>, kWgSmem))) return e;
+    done = true;
+    return cudaSuccess;
+}
+
+template <int CIN, int NP, int EPI>
+cudaError_t launch_conv(const CnnNet* net, const ConvArgs& a, cudaStream_t s) {
+    const long long tiles = (a.M + 127) / 128;
+    if (tiles == 0) return cudaSuccess;
+    const int grid = (int)(tiles < net->sms ? tiles : net->sms);
+    conv_kernel<CIN, NP, EPI><<<grid, kConvThreads, conv_smem_bytes<CIN, NP>(), s>>>(a);
+    return cudaGetLastError();
+}
+
+int wgrad_slices(long long M, int row_tiles, int sms) {
+    const long long chunks = (M + 63) / 64;
+    long long k = (2LL * sms + row_tiles - 1) / row_tiles;
+    if (k > kMaxSplits) k = kMaxSplits;
+    if (k > chunks) k = (int)chunks;
+    return (int)(k < 1 ? 1 : k);
+}
+
+template <int CIN>
+cudaError_t launch_wgrad(const CnnNet* net, const bf16* x, const bf16* dz, long long M, int layer,
+                         cudaStream_t s) {
+    const int row_tiles = (9 * CIN + 1 + 127) / 128;
+    const int slices = wgrad_slices(M, row_tiles, net->sms);
+    WgradArgs a;
+    a.x = x;
+    a.dz = dz;
+    a.partial = net->partial;
+    a.M = M;
+    a.L = net->L;
+    a.err = net->err;
+    wgrad_kernel<CIN><<<dim3(slices, row_tiles), kConvThreads, kWgSmem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    const int outs = (9 * CIN + 1) * 64;
+    wgrad_reduce_kernel<<<(outs + 255) / 256, 256, 0, s>>>(net->partial, slices, row_tiles * 128, CIN,
+                                                           net->grad + layer_woff(layer),
+                                                           net->grad + layer_boff(layer));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t cnn_pack(CnnNet* net, cudaStream_t s) {
+    PackArgs a;
+    a.theta = net->theta;
+    long long off = 0;
+    for (int l = 0; l < 5; ++l) {
+        a.fwd[l] = net->fwd[l];
+        a.fwd_begin[l] = off;
+        off += (long long)fwd_np(l) * fwd_kp(l);
+    }
+    a.fwd_begin[5] = off;
+    for (int l = 0; l < 3; ++l) a.bwd[l] = net->bwd[l];
+    a.total = off + 3LL * 64 * 576;
+    pack_kernel<<<(unsigned)((a.total + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Forward pass of n <= max_batch syndromes already in net->syn (or syn):
+// activations kept for a backward pass; log-probabilities to logprob.
+cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const float* targets, float* logprob,
+                            cudaStream_t s) {
+    cudaError_t e;
+    const int L = net->L;
+    const long long M = n * L * L;
+    if (n == 0) return cudaSuccess;
+    if ((e = prepare_kernels())) return e;
+    input_maps_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(syn, n, L, net->x0);
+    if ((e = cudaGetLastError())) return e;
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.M = M;
+    a.L = L;
+    a.err = net->err;
+    for (int l = 0; l < 4; ++l) {
+        a.act = l == 0 ? net->x0 : net->act[l - 1];
+        a.wmat = net->fwd[l];
+        a.bias = net->theta + layer_boff(l);
+        a.out_bf16 = net->act[l];
+        e = l == 0 ? launch_conv<2, 64, kEpiRelu>(net, a, s) : launch_conv<64, 64, kEpiRelu>(net, a, s);
+        if (e) return e;
+    }
+    a.act = net->act[3];
+    a.wmat = net->fwd[4];
+    a.bias = net->theta + layer_boff(4);
+    a.out_bf16 = nullptr;
+    a.out_f32 = net->z5;
+    if ((e = launch_conv<64, 16, kEpiLogit>(net, a, s))) return e;
+    pool_loss_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(net->z5, n, L, targets, logprob, net->g5,
+                                                             net->loss_item);
+    return cudaGetLastError();
+}
+
+// Loss and flat gradient of n syndromes with soft targets.
+cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const float* targets, cudaStream_t s) {
+    cudaError_t e;
+    const int L = net->L;
+    const long long M = n * L * L;
+    if ((e = cnn_forward_dev(net, syn, n, targets, net->logprob, s))) return e;
+    loss_sum_kernel<<<1, 256, 0, s>>>(net->loss_item, n, net->loss);
+    if ((e = cudaGetLastError())) return e;
+    // last layer (CUDA cores)
+    conv5_boxsum_kernel<<<(unsigned)n, 576, 0, s>>>(net->act[3], L, net->S5);
+    if ((e = cudaGetLastError())) return e;
+    conv5_wgrad_kernel<<<(4 * 576 + 4 + 255) / 256, 256, 0, s>>>(net->S5, net->g5, n, L,
+                                                                  net->grad + layer_woff(4),
+                                                                  net->grad + layer_boff(4));
+    if ((e = cudaGetLastError())) return e;
+    conv5_dgrad_kernel<<<(unsigned)((M * 8 + 255) / 256), 256, 0, s>>>(net->fwd[4], net->g5, net->act[3], M, L,
+                                                                        net->dz[0]);
+    if ((e = cudaGetLastError())) return e;
+    // layers 4, 3, 2: weight gradient, then input gradient gated by the layer below
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.M = M;
+    a.L = L;
+    a.err = net->err;
+    int cur = 0;
+    for (int l = 3; l >= 1; --l) {
+        if ((e = launch_wgrad<64>(net, net->act[l - 1], net->dz[cur], M, l, s))) return e;
+        a.act = net->dz[cur];
+        a.wmat = net->bwd[l - 1];
+        a.mask = net->act[l - 1];
+        a.out_bf16 = net->dz[cur ^ 1];
+        if ((e = launch_conv<64, 64, kEpiMask>(net, a, s))) return e;
+        cur ^= 1;
+    }
+    return launch_wgrad<2>(net, net->x0, net->dz[cur], M, 0, s);
+}
+
+cudaError_t cnn_adam_dev(CnnNet* net, float lr, cudaStream_t s) {
+    net->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - pow(b1, (double)net->step));
+    const float c2 = (float)(1.0 - pow(b2, (double)net->step));
+    adam_kernel<<<(unsigned)((kParams + 255) / 256), 256, 0, s>>>(net->theta, net->m1, net->m2, net->grad, kParams,
+                                                                   lr, (float)b1, (float)b2, 1e-8f, c1, c2);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    return cnn_pack(net, s);
+}
+
+}  // namespace surfmcmc
+
+using namespace surfmcmc;
+
+struct surfmcmc_cnn : public CnnNet {};
+
+namespace {
+
+int cfail(surfmcmc_cnn* net, int code, const char* msg) {
+    if (net && net->ctx) ctx_set_error(net->ctx, msg);
+    return code;
+}
+
+int cuda_fail(surfmcmc_cnn* net, cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    return cfail(net, e == cudaErrorMemoryAllocation ? SURFMCMC_ENOMEM : SURFMCMC_ECUDA, buf);
+}
+
+// Reads the device error flag of the tensor-core kernels (synchronises s).
+int check_err(surfmcmc_cnn* net, cudaStream_t s) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, net->err, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(net, e, "network kernels");
+    if (h) {
+        cudaMemsetAsync(net->err, 0, sizeof(int), s);
+        return cfail(net, SURFMCMC_ECUDA, "network kernel: a pipeline wait timed out");
+    }
+    return SURFMCMC_OK;
+}
+
+struct NetGuard {
+    int prev = -1;
+    explicit NetGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~NetGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+namespace surfmcmc {
+
+cudaError_t cnn_logprob(surfmcmc_cnn* net, const uint8_t* syn, long long n, float* logprob, cudaStream_t s) {
+    const long long ns = 2LL * net->L * (net->L - 1);
+    for (long long b0 = 0; b0 < n; b0 += net->max_batch) {
+        const long long b = n - b0 < net->max_batch ? n - b0 : net->max_batch;
+        const cudaError_t e = cnn_forward_dev(net, syn + b0 * ns, b, nullptr, logprob + b0 * 4, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int cnn_code_size(const surfmcmc_cnn* net) { return net->L; }
+
+}  // namespace surfmcmc
+
+extern "C" {
+
+int64_t surfmcmc_cnn_n_params(void) { return kParams; }
+
+int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcmc_cnn** out) {
+    if (!ctx || !out) return SURFMCMC_EINVAL;
+    *out = nullptr;
+    if (L < 3 || L > SURFMCMC_MAX_L) {
+        ctx_set_error(ctx, "network: L outside 3..31");
+        return SURFMCMC_EINVAL;
+    }
+    if (max_batch < 1 || max_batch > (1LL << 20)) {
+        ctx_set_error(ctx, "network: max_batch outside 1..2^20");
+        return SURFMCMC_EINVAL;
+    }
+    surfmcmc_cnn* net = new surfmcmc_cnn();
+    net->ctx = ctx;
+    net->device = ctx_device(ctx);
+    net->L = L;
+    net->max_batch = max_batch;
+    NetGuard g(net->device);
+    cudaError_t e = cudaDeviceGetAttribute(&net->sms, cudaDevAttrMultiProcessorCount, net->device);
+    const long long M = max_batch * L * L;
+    const size_t P = (size_t)kParams * 4;
+    auto na = [&](auto** field, size_t bytes) {
+        void* p = nullptr;
+        if (e == cudaSuccess) e = net_alloc(net, &p, bytes);
+        *field = (std::remove_pointer_t<decltype(field)>)p;
+    };
+    na(&net->theta, P);
+    na(&net->m1, P);
+    na(&net->m2, P);
+    na(&net->grad, P);
+    for (int l = 0; l < 5; ++l) na(&net->fwd[l], (size_t)fwd_np(l) * fwd_kp(l) * 2);
+    for (int l = 0; l < 3; ++l) na(&net->bwd[l], (size_t)64 * 576 * 2);
+    na(&net->syn, (size_t)max_batch * 2 * L * (L - 1));
+    na(&net->targets, (size_t)max_batch * 16);
+    na(&net->x0, (size_t)M * 4);
+    for (int l = 0; l < 4; ++l) na(&net->act[l], (size_t)M * 128);
+    na(&net->z5, (size_t)M * 16);
+    na(&net->dz[0], (size_t)M * 128);
+    na(&net->dz[1], (size_t)M * 128);
+    na(&net->logprob, (size_t)max_batch * 16);
+    na(&net->g5, (size_t)max_batch * 16);
+    na(&net->loss_item, (size_t)max_batch * 4);
+    na(&net->loss, 4);
+    na(&net->S5, (size_t)max_batch * 576 * 4);
+    na(&net->partial, (size_t)kMaxSplits * 640 * 64 * 4);
+    na(&net->err, 4);
+    if (e == cudaSuccess) e = cudaMemset(net->err, 0, 4);
+    if (e == cudaSuccess) e = cudaMemset(net->theta, 0, P);
+    if (e == cudaSuccess) e = cudaMemset(net->m1, 0, P);
+    if (e == cudaSuccess) e = cudaMemset(net->m2, 0, P);
+    if (e == cudaSuccess) e = prepare_kernels();
+    if (e == cudaSuccess) e = cnn_pack(net, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        const int rc = cuda_fail(net, e, "network create");
+        surfmcmc_cnn_destroy(net);
+        return rc;
+    }
+    *out = net;
+    return SURFMCMC_OK;
+}
+
+void surfmcmc_cnn_destroy(surfmcmc_cnn* net) {
+    if (!net) return;
+    NetGuard g(net->device);
+    cudaDeviceSynchronize();
+    for (void* p : net->allocs) cudaFree(p);
+    delete net;
+}
+
+int surfmcmc_cnn_set_params(surfmcmc_cnn* net, const float* params) {
+    if (!net || !params) return cfail(net, SURFMCMC_EINVAL, "network: NULL params");
+    NetGuard g(net->device);
+    const size_t P = (size_t)kParams * 4;
+    cudaError_t e = cudaMemcpy(net->theta, params, P, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemset(net->m1, 0, P);
+    if (e == cudaSuccess) e = cudaMemset(net->m2, 0, P);
+    if (e == cudaSuccess) e = cnn_pack(net, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(net, e, "network set_params");
+    net->step = 0;
+    return SURFMCMC_OK;
+}
+
+int surfmcmc_cnn_get_params(surfmcmc_cnn* net, float* params) {
+    if (!net || !params) return cfail(net, SURFMCMC_EINVAL, "network: NULL params");
+    NetGuard g(net->device);
+    cudaError_t e = cudaMemcpy(params, net->theta, (size_t)kParams * 4, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(net, e, "network get_params");
+    return SURFMCMC_OK;
+}
+
+int surfmcmc_cnn_forward(surfmcmc_cnn* net, const uint8_t* syndromes, int64_t n, float* out_logprob,
+                         void* stream) {
+    if (!net) return SURFMCMC_EINVAL;
+    if (n < 0 || (n > 0 && (!syndromes || !out_logprob))) return cfail(net, SURFMCMC_EINVAL, "network forward: bad args");
+    if (n == 0) return SURFMCMC_OK;
+    NetGuard g(net->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ns = (size_t)2 * net->L * (net->L - 1);
+    const bool syn_dev = device_ptr(syndromes), out_dev = device_ptr(out_logprob);
+    for (int64_t b0 = 0; b0 < n; b0 += net->max_batch) {
+        const int64_t b = n - b0 < net->max_batch ? n - b0 : net->max_batch;
+        const uint8_t* sp = syndromes + b0 * ns;
+        cudaError_t e = cudaSuccess;
+        if (!syn_dev) {
+            e = cudaMemcpyAsync(net->syn, sp, b * ns, cudaMemcpyHostToDevice, s);
+            sp = net->syn;
+        }
+        float* lp = out_dev ? out_logprob + b0 * 4 : net->logprob;
+        if (e == cudaSuccess) e = cnn_forward_dev(net, sp, b, nullptr, lp, s);
+        if (e == cudaSuccess && !out_dev)
+            e = cudaMemcpyAsync(out_logprob + b0 * 4, net->logprob, b * 16, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(net, e, "network forward");
+        if (!out_dev || !syn_dev) {
+            const int rc = check_err(net, s);
+            if (rc) return rc;
+        }
+    }
+    if (syn_dev && out_dev) return check_err(net, s);
+    return SURFMCMC_OK;
+}
+
+int surfmcmc_cnn_gradient(surfmcmc_cnn* net, const uint8_t* syndromes, const float* targets, int64_t n,
+                          float* out_loss, float* out_grad, void* stream) {
+    if (!net) return SURFMCMC_EINVAL;
+    if (n < 1 || n > net->max_batch || !syndromes || !targets)
+        return cfail(net, SURFMCMC_EINVAL, "network gradient: need 1 <= n <= max_batch and inputs");
+    NetGuard g(net->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ns = (size_t)2 * net->L * (net->L - 1);
+    cudaError_t e = cudaMemcpyAsync(net->syn, syndromes, n * ns, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(net->targets, targets, n * 16, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cnn_backward_dev(net, net->syn, n, net->targets, s);
+    if (e == cudaSuccess && out_loss) e = cudaMemcpyAsync(out_loss, net->loss, 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess && out_grad) e = cudaMemcpyAsync(out_grad, net->grad, (size_t)kParams * 4, cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return cuda_fail(net, e, "network gradient");
+    return check_err(net, s);
+}
+
+int surfmcmc_cnn_train_step(surfmcmc_cnn* net, const uint8_t* syndromes, const float* targets, int64_t n,
+                            float lr, float* out_loss, void* stream) {
+    if (!net) return SURFMCMC_EINVAL;
+    if (n < 1 || n > net->max_batch || !syndromes || !targets || !(lr > 0.0f))
+        return cfail(net, SURFMCMC_EINVAL, "network train_step: need 1 <= n <= max_batch, inputs, lr > 0");
+    NetGuard g(net->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ns = (size_t)2 * net->L * (net->L - 1);
+    const uint8_t* sp = syndromes;
+    const float* tp = targets;
+    cudaError_t e = cudaSuccess;
+    if (!device_ptr(syndromes)) {
+        e = cudaMemcpyAsync(net->syn, syndromes, n * ns, cudaMemcpyHostToDevice, s);
+        sp = net->syn;
+    }
+    if (e == cudaSuccess && !device_ptr(targets)) {
+        e = cudaMemcpyAsync(net->targets, targets, n * 16, cudaMemcpyHostToDevice, s);
+        tp = net->targets;
+    }
+    if (e == cudaSuccess) e = cnn_backward_dev(net, sp, n, tp, s);
+    if (e == cudaSuccess) e = cnn_adam_dev(net, lr, s);
+    if (e == cudaSuccess && out_loss) e = cudaMemcpyAsync(out_loss, net->loss, 4, cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return cuda_fail(net, e, "network train_step");
+    if (out_loss && !device_ptr(out_loss)) return check_err(net, s);
+    return SURFMCMC_OK;
+}
+
+int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream) {
+    if (!net) return SURFMCMC_EINVAL;
+    NetGuard g(net->device);
+    return check_err(net, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -6,6 +6,9 @@
 #include <math.h>
 #include <stdint.h>
 
+struct surfmcmc_ctx;
+struct surfmcmc_cnn;
+
 namespace surfmcmc {
 
 constexpr int kMaxL = 31;
@@ -173,5 +176,15 @@ cudaError_t launch_class_means(long long n, int K, int R, int N, int j, uint64_t
                                double* mean, cudaStream_t s);
 cudaError_t launch_ti_decide(long long n, int K, int N, double mean0, double h3, double* mean, int32_t* out_class,
                              double* out_log_z, cudaStream_t s);
+
+// Context services shared with the network code (api.cu).
+void ctx_set_error(surfmcmc_ctx* ctx, const char* msg);
+int ctx_device(const surfmcmc_ctx* ctx);
+bool device_ptr(const void* p);
+
+// Network log-probabilities [n][4] of n device syndromes into device memory,
+// stream-ordered, batched by the network's max_batch (cnn.cu).
+cudaError_t cnn_logprob(surfmcmc_cnn* net, const uint8_t* syn, long long n, float* logprob, cudaStream_t s);
+int cnn_code_size(const surfmcmc_cnn* net);
 
 }  // namespace surfmcmc
