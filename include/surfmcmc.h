@@ -348,11 +348,20 @@ int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int32_t L, doub
  *   last row zero), channel 1 the sigma_z generators (L x (L-1), row i column
  *   j = entry (L-1) L + i (L-1) + j, last column zero).
  *   Network: five 3x3 convolutions with zero padding, 2 -> 64 -> 64 -> 64 ->
- *   64 -> 4 channels, bias, ReLU after the first four, mean over the map,
- *   log-softmax.  Weights and activations are bfloat16 (round to nearest
- *   even), sums float32 (tensor cores).
- *   Parameters: surfmcmc_cnn_n_params() float32 values, layer after layer,
- *   each layer W[co][kh][kw][ci] then b[co].
+ *   64 -> 2 channels, bias, ReLU after the first four.  Weights and
+ *   activations are bfloat16 (round to nearest even), sums float32 (tensor
+ *   cores).
+ *   Readout: class k = a + 2b, a (b) the parity of an error's sigma_x
+ *   (sigma_z) part on qubit column (row) 0.  With e0 the decoder's pure error
+ *   (surfmcmc_start_frames) of class code a0 + 2 b0 and m = (L-1) div 2, the
+ *   last layer's channel 0 at map position (i, m) and channel 1 at (m, j) are
+ *   the logits s of flips of E + e0 on qubits (2i, 2m) and (2m, 2j) (E + e0
+ *   has the same parities on the middle column/row as on column/row 0);
+ *   M_x = prod_i -tanh(s_i / 2) (likewise M_z), clipped to +-(1 - 1e-6);
+ *   log p_k = log((1 + (-1)^(a xor a0) M_x) / 2) + log((1 + (-1)^(b xor b0)
+ *   M_z) / 2).
+ *   Parameters: surfmcmc_cnn_n_params() (= 113154) float32 values, layer
+ *   after layer, each layer W[co][kh][kw][ci] then b[co].
  *   Training: mean over the batch of the cross entropy -sum_k q_k log p_k
  *   against soft targets q, Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * A network object belongs to one context's device; it is not thread-safe.
@@ -389,6 +398,32 @@ int surfmcmc_cnn_gradient(surfmcmc_cnn* net, const uint8_t* syndromes, const flo
 int surfmcmc_cnn_train_step(surfmcmc_cnn* net, const uint8_t* syndromes, const float* targets, int64_t n,
                             float lr, float* out_loss, void* stream);
 int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream);
+
+/* Decoding with early stop (the paper has no counterpart).  The same chains
+ * as surfmcmc_decode with opts (same seed, ids id0 + i, same sweeps), run in
+ * chunks: checkpoints at burn_in + k chunk_sweeps (k = 1, 2, ...) below
+ * n_sweeps, and n_sweeps.  At a checkpoint the decision so far is argmin_k of
+ * the class sums; syndrome i stops there when the network (net, built for
+ * this L) is confident, log p_a - max_{k != a} log p_k > tau for its argmax
+ * a, and a equals that decision.  The others continue; at n_sweeps every
+ * syndrome stops.  A syndrome that never stops early gets exactly the
+ * results of surfmcmc_decode; tau = +infinity reproduces surfmcmc_decode.
+ *   out_class [n] int32: the decision at the syndrome's stop.
+ *   out_class_sum [n][4] uint64 (may be NULL): the class sums at the stop.
+ *   out_sweeps [n] uint32 (may be NULL): the sweeps run (the stop).
+ * Buffers may be host or device memory.  The call waits for the device at
+ * every checkpoint (to size the next chunk).  EINVAL: bad arguments, a net
+ * for another L, chunk_sweeps 0, tau NaN. */
+int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* syndromes, int64_t n, int32_t L,
+                          double p, const surfmcmc_opts* opts, uint32_t chunk_sweeps, float tau, uint64_t seed,
+                          uint32_t id0, int32_t* out_class, uint64_t* out_class_sum, uint32_t* out_sweeps,
+                          void* stream);
+
+/* Soft targets for training: targets[i][k] = softmax_k(log_ratio[i][k])
+ * (float32) from the [n][4] double log-ratios of a decode.  Both buffers are
+ * device memory of the current device; stream-ordered.  EINVAL for n < 0,
+ * NULL or host pointers. */
+int surfmcmc_cnn_soft_targets(const double* log_ratio, int64_t n, float* targets, void* stream);
 
 #ifdef __cplusplus
 }

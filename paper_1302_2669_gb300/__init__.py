@@ -68,7 +68,7 @@ EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surf
            "surfmcmc_server_create", "surfmcmc_server_submit", "surfmcmc_server_poll", "surfmcmc_server_stats",
            "surfmcmc_server_destroy", "surfmcmc_cnn_n_params", "surfmcmc_cnn_create", "surfmcmc_cnn_destroy",
            "surfmcmc_cnn_set_params", "surfmcmc_cnn_get_params", "surfmcmc_cnn_forward", "surfmcmc_cnn_gradient",
-           "surfmcmc_cnn_train_step", "surfmcmc_cnn_status")
+           "surfmcmc_cnn_train_step", "surfmcmc_cnn_status", "surfmcmc_cnn_soft_targets", "surfmcmc_decode_early")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -125,6 +125,9 @@ def lib():
         L.surfmcmc_cnn_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         L.surfmcmc_cnn_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
         L.surfmcmc_cnn_status.argtypes = [vp, vp]
+        L.surfmcmc_cnn_soft_targets.argtypes = [vp, i64, vp, vp]
+        L.surfmcmc_decode_early.argtypes = [vp, vp, vp, i64, i32, dbl, C.POINTER(_Opts), u32, C.c_float, u64, u32, vp,
+                                            vp, vp, vp]
         L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
         L.surfmcmc_sweep_time.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         _lib = L
@@ -293,6 +296,20 @@ class Context:
                                                  seed, _ptr(ids), id0, _ptr(cls), _ptr(csum), _ptr(lr), st))
         return cls, csum, lr
 
+    def decode_early(self, net, syndromes, L, p, opts: Opts | None = None, chunk_sweeps=64, tau=float("inf"), seed=0,
+                     id0=0, stream=None):
+        """surfmcmc_decode_early; returns (class [n], class_sum [n][4], sweeps [n])."""
+        opts = opts or Opts()
+        n = syndromes.shape[0]
+        cls = _empty(syndromes, (n,), np.int32)
+        csum = _empty(syndromes, (n, 4), np.uint64)
+        sw = _empty(syndromes, (n,), np.uint32)
+        st = stream if stream is not None else _stream_of(syndromes, cls)
+        o = opts.c()
+        self._check(lib().surfmcmc_decode_early(self._h, net._h, _ptr(syndromes), n, L, p, C.byref(o), chunk_sweeps,
+                                                tau, seed, id0, _ptr(cls), _ptr(csum), _ptr(sw), st))
+        return cls, csum, sw
+
     def autotune(self, L, chains_per_class, p, n_probe=4096, sweeps=20):
         """surfmcmc_autotune: returns (best lanes per bundle, {lanes: ms})."""
         best = C.c_int32()
@@ -449,6 +466,18 @@ class Network:
 
     def status(self, stream=None):
         self._ctx._check(lib().surfmcmc_cnn_status(self._h, stream))
+
+    @staticmethod
+    def soft_targets(log_ratio, out=None, stream=None):
+        """softmax of [n][4] float64 log-ratios (CUDA tensors) -> float32 targets."""
+        n = log_ratio.shape[0]
+        if out is None:
+            out = _empty(log_ratio, (n, 4), np.float32)
+        st = stream if stream is not None else _stream_of(log_ratio, out)
+        rc = lib().surfmcmc_cnn_soft_targets(_ptr(log_ratio), n, _ptr(out), st)
+        if rc != OK:
+            raise SurfmcmcError(rc, lib().surfmcmc_strerror(rc).decode())
+        return out
 
     def close(self):
         if self._h:

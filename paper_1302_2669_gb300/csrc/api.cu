@@ -18,6 +18,7 @@ using namespace surfmcmc;
 
 struct surfmcmc_ctx {
     int device = 0;
+    int sms = 0;               // multiprocessors of the device
     void* arena = nullptr;     // grow-only device scratch
     size_t arena_bytes = 0;
     std::string last_error;
@@ -210,6 +211,21 @@ int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nul
     }
     *lam_out = best;
     return SURFMCMC_OK;
+}
+
+// Small batches: a persistent block takes work units of 4 warps x 32/lam
+// bundles, so a batch of few bundles leaves most blocks idle and the run
+// time is the latency of one unit.  Unless the caller fixed the lanes, widen
+// (more lanes share a bundle's generators, shorter units) until the units
+// fill the resident blocks once.  The results do not depend on the lanes.
+int widen_lanes(const surfmcmc_ctx* ctx, int L, int requested, int lam, long long n_bundles, int G) {
+    if (requested || !ctx || ctx->sms <= 0) return lam;
+    const int nq = n_qubits(L), nc = L * (L - 1) / 2;
+    const long long capacity = (long long)ctx->sms * (G >= 16 ? 5 : 3);
+    while (lam < 32 && sweep_units(n_bundles, lam) < capacity &&
+           sweep_smem_bytes(nq, nc, 2 * lam) <= 200 * 1024)
+        lam *= 2;
+    return lam;
 }
 
 int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
@@ -631,6 +647,7 @@ int surfmcmc_create(surfmcmc_ctx** out, int device) {
     if (prop.major != 10 || prop.minor != 3) return SURFMCMC_ENODEV;
     surfmcmc_ctx* ctx = new surfmcmc_ctx;
     ctx->device = device;
+    ctx->sms = prop.multiProcessorCount;
     *out = ctx;
     return SURFMCMC_OK;
 }
@@ -753,6 +770,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
 
     SweepParams sp;
     init_chains(sp, Cn, R, id0);
+    lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
 
@@ -1112,6 +1130,154 @@ int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, do
     if (!best) return fail(ctx, SURFMCMC_EINVAL, "no lanes_per_bundle fits L=%d", L);
     ctx->tuned[{L, R}] = best;
     if (best_out) *best_out = best;
+    return SURFMCMC_OK;
+}
+
+int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* syndromes, int64_t n, int32_t L,
+                          double p, const surfmcmc_opts* opts_in, uint32_t chunk_sweeps, float tau, uint64_t seed,
+                          uint32_t id0, int32_t* out_class, uint64_t* out_class_sum, uint32_t* out_sweeps,
+                          void* stream) {
+    int rc = check_common(ctx, n, L, id0);
+    if (rc) return rc;
+    surfmcmc_opts o;
+    surfmcmc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if ((rc = check_opts(ctx, o, p))) return rc;
+    if (!net || cnn_code_size(net) != L) return fail(ctx, SURFMCMC_EINVAL, "network missing or built for another L");
+    if (chunk_sweeps == 0) return fail(ctx, SURFMCMC_EINVAL, "chunk_sweeps must be > 0");
+    if (tau != tau) return fail(ctx, SURFMCMC_EINVAL, "tau is NaN");
+    if (n > 0 && (!syndromes || !out_class)) return fail(ctx, SURFMCMC_EINVAL, "NULL syndromes or out_class");
+    int lam = 0;
+    if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class))
+        return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
+    if (n == 0) return SURFMCMC_OK;
+    ctx->last_error.clear();
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    const int K = 4, R = o.chains_per_class, Cn = K * R;
+    const int nq = n_qubits(L), W = n_words(L), ns = n_stabs(L);
+    const int fw = Cn * 2 * W;  // frame words per item
+
+    // checkpoints: burn_in + k chunk_sweeps (k >= 1) below n_sweeps, then n_sweeps
+    std::vector<uint32_t> marks;
+    for (uint64_t t = (uint64_t)o.burn_in + chunk_sweeps; t < o.n_sweeps; t += chunk_sweeps)
+        marks.push_back((uint32_t)t);
+    marks.push_back(o.n_sweeps);
+
+    SweepParams sp0;
+    init_chains(sp0, Cn, R, id0);
+    add_group(sp0, L, n, 0, 0, 0, 0, lam);
+    const long long nb_max = sp0.grp[0].n_bundles;
+
+    Carver cv;
+    Buf b_syn, b_cls, b_csum, b_sw;
+    plan(b_syn, (void*)syndromes, (size_t)n * ns, cv);
+    plan(b_cls, out_class, (size_t)n * 4, cv);
+    plan(b_csum, out_class_sum, out_class_sum ? (size_t)n * K * 8 : 0, cv);
+    plan(b_sw, out_sweeps, out_sweeps ? (size_t)n * 4 : 0, cv);
+    const size_t off_lp = cv.reserve((size_t)n * 16);
+    const size_t off_perm[2] = {cv.reserve((size_t)n * 8), cv.reserve((size_t)n * 8)};
+    const size_t off_ids[2] = {cv.reserve((size_t)n * 4), cv.reserve((size_t)n * 4)};
+    const size_t off_fin = cv.reserve((size_t)n * fw * 4), off_fout = cv.reserve((size_t)n * fw * 4);
+    const size_t off_sin = cv.reserve((size_t)n * Cn * 8), off_sout = cv.reserve((size_t)n * Cn * 8);
+    const size_t off_keep = cv.reserve((size_t)n * 4);
+    const size_t off_pos = cv.reserve((size_t)n * 8);
+    const size_t off_cnt = cv.reserve(8);
+    const size_t off_tcls = cv.reserve((size_t)n * 4);
+    const size_t off_tsum = cv.reserve((size_t)n * K * 8);
+    const size_t off_e0 = cv.reserve((size_t)n * 2 * W * 4);
+    const size_t off_code = cv.reserve((size_t)n * 4);
+    const size_t off_state = cv.reserve((size_t)nb_max * 2 * nq * 4);
+    const size_t off_ctr = cv.reserve(sizeof(unsigned int));
+    if ((rc = ensure_arena(ctx, cv.off))) return rc;
+    Buf* all[] = {&b_syn, &b_cls, &b_csum, &b_sw};
+    for (Buf* b : all) bind(*b, ctx);
+    char* base = (char*)ctx->arena;
+    auto at = [&](size_t off) { return (void*)(base + off); };
+    float* logprob = (float*)at(off_lp);
+    uint32_t* f_in = (uint32_t*)at(off_fin);
+    uint32_t* f_out = (uint32_t*)at(off_fout);
+    uint64_t* s_in = (uint64_t*)at(off_sin);
+    uint64_t* s_out = (uint64_t*)at(off_sout);
+    int32_t* keep = (int32_t*)at(off_keep);
+    long long* cnt = (long long*)at(off_cnt);
+    int32_t* tcls = (int32_t*)at(off_tcls);
+    uint64_t* tsum = (uint64_t*)at(off_tsum);
+
+    if ((rc = copy_in(ctx, b_syn, s))) return rc;
+    CK(cnn_logprob(net, (const uint8_t*)b_syn.dev, n, logprob, s));
+    CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, (uint32_t*)at(off_e0), (int32_t*)at(off_code), s));
+    CK(launch_iota(n, (long long*)at(off_perm[0]), s));
+
+    uint64_t T[5];
+    double beta_bar;
+    acceptance_table(p, 1.0, T, &beta_bar);
+    long long n_act = n;
+    uint32_t t = 0;
+    int cur = 0;  // pair holding the active items' caller indices and ids
+    for (size_t k = 0; k < marks.size() && n_act > 0; ++k) {
+        const uint32_t tk = marks[k];
+        const bool final_chunk = k + 1 == marks.size();
+        // sweeps [t, tk) of the active items, resumed from their state at t
+        SweepParams sp;
+        init_chains(sp, Cn, R, id0);
+        sp.ids = t == 0 ? nullptr : (const uint32_t*)at(off_ids[cur]);
+        const int lam_k = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n_act), sp.G);
+        add_group(sp, L, n_act, 0, 0, 0, 0, lam_k);
+        make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
+        // the chunk's non-empty segments (annealing stages already passed are skipped)
+        std::vector<Segment> segs;
+        for (const Segment& sg : plan_segments(tk, o.burn_in, o.anneal_stages, o.anneal_beta0, o.beta_scale, t))
+            if (sg.t1 > sg.t0) segs.push_back(sg);
+        if (segs.empty()) segs.push_back({t, tk, o.beta_scale, false});
+        SweepIO io;
+        if (t == 0) {
+            io.e0 = (uint32_t*)at(off_e0);
+            io.e0code = (int32_t*)at(off_code);
+        } else {
+            io.init_frames = f_in;
+            io.init_sum = s_in;
+        }
+        io.chain_sum = s_out;
+        io.chain_frames = final_chunk ? nullptr : f_out;
+        io.state = segs.size() > 1 ? (uint32_t*)at(off_state) : nullptr;
+        io.unit_counter = (unsigned int*)at(off_ctr);
+        if ((rc = run_segments(ctx, sp, segs, o.burn_in, p, lam_k, io, s))) return rc;
+
+        // decision so far, then retire the items that may stop here
+        DecideParams dp;
+        memset(&dp, 0, sizeof dp);
+        dp.n = n_act;
+        dp.K = K;
+        dp.R = R;
+        dp.samples = tk > o.burn_in ? (uint64_t)4 * R * (tk - o.burn_in) : 0;
+        dp.beta_bar = beta_bar;
+        dp.chain_sum = s_out;
+        dp.out_class = tcls;
+        dp.out_class_sum = tsum;
+        CK(launch_decide(dp, s));
+        CK(launch_retire(n_act, (const long long*)at(off_perm[cur]), logprob, tcls, tsum, tau, tk,
+                         final_chunk ? 1 : 0, (int32_t*)b_cls.dev, (uint64_t*)b_csum.dev, (uint32_t*)b_sw.dev, keep,
+                         s));
+        t = tk;
+        if (final_chunk) break;
+        // survivors, in order: caller indices and ids to the other pair, frames and sums to the inputs
+        CK(launch_compact(n_act, keep, (long long*)at(off_pos), cnt, (const long long*)at(off_perm[cur]), id0, fw,
+                          Cn, f_out, s_out, (long long*)at(off_perm[cur ^ 1]), (uint32_t*)at(off_ids[cur ^ 1]),
+                          f_in, s_in, s));
+        long long h_cnt = 0;
+        CK(cudaMemcpyAsync(&h_cnt, cnt, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        n_act = h_cnt;
+        cur ^= 1;
+    }
+    bool any_host = false;
+    for (Buf* b : {&b_cls, &b_csum, &b_sw}) {
+        if ((rc = copy_out(ctx, *b, s))) return rc;
+        any_host |= b->staged;
+    }
+    if (!stream || any_host) CK(cudaStreamSynchronize(s));
     return SURFMCMC_OK;
 }
 

@@ -184,6 +184,112 @@ __global__ void gather_rows_kernel(long long n, const uint8_t* src, const long l
     ids_out[i] = ids ? ids[perm[i]] : id0 + (uint32_t)perm[i];
 }
 
+// Early stop, after a chunk of sweeps: item i of the active set (caller's
+// index perm[i]) retires when this is the last checkpoint, or when the
+// network is confident (log p of its argmax exceeds every other class's by
+// more than tau) and its argmax equals the chains' current decision.  A
+// retiring item writes its decision, class sums and sweep count.
+__global__ void retire_kernel(long long n, const long long* perm, const float* logprob, const int32_t* cls,
+                              const uint64_t* class_sum, float tau, uint32_t sweeps, int final_chunk,
+                              int32_t* out_class, uint64_t* out_class_sum, uint32_t* out_sweeps, int32_t* keep) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long o = perm[i];
+    int am = 0;
+    float lp[4];
+    for (int k = 0; k < 4; ++k) {
+        lp[k] = logprob[o * 4 + k];
+        if (lp[k] > lp[am]) am = k;
+    }
+    float second = -INFINITY;
+    for (int k = 0; k < 4; ++k)
+        if (k != am && lp[k] > second) second = lp[k];
+    const bool retire = final_chunk || (lp[am] - second > tau && am == cls[i]);
+    keep[i] = retire ? 0 : 1;
+    if (!retire) return;
+    out_class[o] = cls[i];
+    if (out_class_sum)
+        for (int k = 0; k < 4; ++k) out_class_sum[o * 4 + k] = class_sum[i * 4 + k];
+    if (out_sweeps) out_sweeps[o] = sweeps;
+}
+
+// Exclusive prefix sum of keep[0..n) into pos, total into *count (one block
+// of 1024 threads: each thread scans a contiguous run, then the run totals
+// are scanned in shared memory).
+__global__ void scan_keep_kernel(long long n, const int32_t* keep, long long* pos, long long* count) {
+    __shared__ long long tot[1024];
+    const int t = threadIdx.x;
+    const long long per = (n + 1023) / 1024;
+    const long long a = t * per, b = a + per < n ? a + per : n;
+    long long s = 0;
+    for (long long i = a; i < b; ++i) s += keep[i];
+    tot[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const long long v = t >= off ? tot[t - off] : 0;
+        __syncthreads();
+        tot[t] += v;
+        __syncthreads();
+    }
+    long long run = tot[t] - s;  // exclusive start of this thread's run
+    for (long long i = a; i < b; ++i) {
+        pos[i] = run;
+        run += keep[i];
+    }
+    if (t == 1023) *count = tot[1023];
+}
+
+// Moves the kept items' per-item rows to their compacted positions: the
+// caller's index, the chain ids, the per-chain frames and sums.
+__global__ void compact_kernel(long long n, const int32_t* keep, const long long* pos, const long long* perm,
+                               uint32_t id0, int frame_words, int chains, const uint32_t* frames,
+                               const uint64_t* sums, long long* perm_out, uint32_t* ids_out, uint32_t* frames_out,
+                               uint64_t* sums_out) {
+    const long long i = blockIdx.x;
+    if (i >= n || !keep[i]) return;
+    const long long j = pos[i];
+    if (threadIdx.x == 0) {
+        perm_out[j] = perm[i];
+        ids_out[j] = id0 + (uint32_t)perm[i];
+    }
+    for (int w = threadIdx.x; w < frame_words; w += blockDim.x)
+        frames_out[j * frame_words + w] = frames[i * frame_words + w];
+    for (int c = threadIdx.x; c < chains; c += blockDim.x) sums_out[j * chains + c] = sums[i * chains + c];
+}
+
+__global__ void iota_kernel(long long n, long long* perm) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[i] = i;
+}
+
+cudaError_t launch_iota(long long n, long long* perm, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    iota_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_retire(long long n, const long long* perm, const float* logprob, const int32_t* cls,
+                          const uint64_t* class_sum, float tau, uint32_t sweeps, int final_chunk, int32_t* out_class,
+                          uint64_t* out_class_sum, uint32_t* out_sweeps, int32_t* keep, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    retire_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, perm, logprob, cls, class_sum, tau, sweeps,
+                                                              final_chunk, out_class, out_class_sum, out_sweeps, keep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(long long n, const int32_t* keep, long long* pos, long long* count, const long long* perm,
+                           uint32_t id0, int frame_words, int chains, const uint32_t* frames, const uint64_t* sums,
+                           long long* perm_out, uint32_t* ids_out, uint32_t* frames_out, uint64_t* sums_out,
+                           cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    scan_keep_kernel<<<1, 1024, 0, s>>>(n, keep, pos, count);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    compact_kernel<<<(unsigned)n, 128, 0, s>>>(n, keep, pos, perm, id0, frame_words, chains, frames, sums, perm_out,
+                                               ids_out, frames_out, sums_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_rows(long long n, const uint8_t* src, const long long* src_off, const long long* dst_off,
                                const int32_t* len, const long long* perm, const uint32_t* ids, uint32_t id0,
                                uint8_t* dst, uint32_t* ids_out, cudaStream_t s) {

@@ -1,7 +1,16 @@
 // The early-stop network on the GPU: five 3x3 convolutions over the two
-// syndrome maps of a size-L code (2 -> 64 -> 64 -> 64 -> 64 -> 4, ReLU after
-// the first four), global average pool and log-softmax; training by the
-// cross entropy with soft targets and Adam.
+// syndrome maps of a size-L code (2 -> 64 -> 64 -> 64 -> 64 -> 2, ReLU after
+// the first four) and a parity readout giving the log-probabilities of the 4
+// classes; training by the cross entropy with soft targets and Adam.
+//
+// Readout: class bit a (b) is the parity of an error's sigma_x (sigma_z)
+// part on qubit column (row) 0.  With e0 the decoder's pure error of class
+// code c0 = a0 + 2 b0, E + e0 has a trivial syndrome, so its parities are
+// the same on the middle qubit column / row 2m, m = (L-1) div 2.  The last
+// layer gives at map position (i, m) (channel 0) and (m, j) (channel 1) the
+// logit s of a flip of (E + e0) on qubit (2i, 2m) / (2m, 2j); with
+// independent flips P(odd) = (1 - M)/2, M = prod(-tanh(s/2)) clipped to
+// +-(1 - 1e-6), and log p_{a + 2b} = log P_x(a xor a0) + log P_z(b xor b0).
 //
 // Layouts: activations are NHWC bfloat16, [M][C] with M = n L^2 positions
 // (syndrome-major, then row, then column).  Weights live as float32 master
@@ -18,8 +27,8 @@
 //   weight gradient: D[(tap, ci)][co] = sum_p X[p + tap][ci] dZ[p][co], a
 //     GEMM over positions split across blocks, with a row of ones that yields
 //     the bias gradient; partial sums are added in a fixed order.
-// The last layer (4 outputs whose gradient is constant over a map) and the
-// pool, loss and Adam steps run on the CUDA cores.
+// The last layer's backward (2 outputs, gradient nonzero on the middle lines
+// only), the readout, loss and Adam steps run on the CUDA cores.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -39,6 +48,8 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kHid = 64;          // hidden channels
 constexpr int kCls = 4;           // classes
+constexpr int kOut = 2;           // flip logits per position (last layer)
+constexpr float kClip = 1e-6f;    // |M| <= 1 - kClip
 constexpr int kProdWarps = 4;     // gather warps
 constexpr int kEpiWarps = 4;      // accumulator-draining warps
 constexpr int kConvThreads = (kProdWarps + kEpiWarps + 1) * 32;
@@ -49,7 +60,7 @@ constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
 // Channels of the five layers and the offsets of their weights and biases in
 // the flat parameter vector.
 __host__ __device__ constexpr int layer_cin(int l) { return l == 0 ? 2 : kHid; }
-__host__ __device__ constexpr int layer_cout(int l) { return l == 4 ? kCls : kHid; }
+__host__ __device__ constexpr int layer_cout(int l) { return l == 4 ? kOut : kHid; }
 __host__ __device__ constexpr long long layer_woff(int l) {
     long long o = 0;
     for (int i = 0; i < l; ++i) o += (long long)layer_cout(i) * 9 * layer_cin(i) + layer_cout(i);
@@ -59,7 +70,7 @@ __host__ __device__ constexpr long long layer_boff(int l) {
     return layer_woff(l) + (long long)layer_cout(l) * 9 * layer_cin(l);
 }
 constexpr long long kParams = layer_woff(5);
-static_assert(kParams == 114308, "parameter count");
+static_assert(kParams == 113154, "parameter count");
 
 // GEMM operand shapes of the forward conv of each layer: N rows (output
 // channels, padded to a multiple of 16) by K columns (9 C_in, padded to a
@@ -200,7 +211,7 @@ struct ConvArgs {
     const float* bias;   // [NP] (kEpiRelu, kEpiLogit) or NULL
     const bf16* mask;    // [M][64] ReLU gate (kEpiMask) or NULL
     bf16* out_bf16;      // [M][64] (kEpiRelu, kEpiMask)
-    float* out_f32;      // [M][4]  (kEpiLogit)
+    float* out_f32;      // [M][2]  (kEpiLogit)
     long long M;
     int L;
     int* err;
@@ -348,14 +359,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
             if (EPI == kEpiLogit) {
                 float v[16];
                 tmem_ld16(taddr, v);
-                if (m < M) {
-                    float4 o;
-                    o.x = v[0] + __ldg(a.bias + 0);
-                    o.y = v[1] + __ldg(a.bias + 1);
-                    o.z = v[2] + __ldg(a.bias + 2);
-                    o.w = v[3] + __ldg(a.bias + 3);
-                    *reinterpret_cast<float4*>(a.out_f32 + m * 4) = o;
-                }
+                if (m < M)
+                    *reinterpret_cast<float2*>(a.out_f32 + m * 2) =
+                        make_float2(v[0] + __ldg(a.bias + 0), v[1] + __ldg(a.bias + 1));
             } else {
 #pragma unroll
                 for (int cc = 0; cc < NP / 16; ++cc) {
@@ -669,48 +675,80 @@ __global__ void pack_kernel(PackArgs a) {
     }
 }
 
-// One warp per syndrome: mean of the last layer over the map, log-softmax,
-// and with targets the loss and d loss / d z5 (= (softmax - q) / (n L^2),
-// the same at every position of the map).
-__global__ void pool_loss_kernel(const float* z5, long long n, int L, const float* targets, float* logprob,
-                                 float* g5, float* loss_item) {
+// One warp per syndrome: the parity readout.  Lane i < L holds the flip
+// logits on the middle column (row i) and middle row (column j = i); the
+// products are taken in lane order 0..31 by every lane.  With targets, also
+// the loss and d loss / d z5 at the middle-line positions (dz5 must be zero
+// elsewhere).
+__device__ __forceinline__ float warp_prod_except(float t, int skip) {
+    float r = 1.0f;
+    for (int j = 0; j < 32; ++j) {
+        const float v = __shfl_sync(0xffffffffu, t, j);
+        if (j != skip) r *= v;
+    }
+    return r;
+}
+
+__global__ void readout_kernel(const float* z5, const uint8_t* syn, long long n, int L, const float* targets,
+                               float* logprob, float* dz5, float* loss_item) {
     const long long item = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (item >= n) return;
-    const int LL = L * L;
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int p = lane; p < LL; p += 32) {
-        const float4 v = *reinterpret_cast<const float4*>(z5 + (item * LL + p) * 4);
-        s[0] += v.x;
-        s[1] += v.y;
-        s[2] += v.z;
-        s[3] += v.w;
+    const int m = (L - 1) / 2;
+    const long long base = item * L * L;
+    float sa = 0.0f, sb = 0.0f, ta = 1.0f, tb = 1.0f;
+    if (lane < L) {
+        sa = z5[(base + (long long)lane * L + m) * 2 + 0];
+        sb = z5[(base + (long long)m * L + lane) * 2 + 1];
+        ta = -tanhf(0.5f * sa);
+        tb = -tanhf(0.5f * sb);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-    if (lane != 0) return;
-    float z[4], mx = -INFINITY;
-    for (int k = 0; k < 4; ++k) {
-        z[k] = s[k] / (float)LL;
-        mx = fmaxf(mx, z[k]);
-    }
-    float se = 0.0f;
-    for (int k = 0; k < 4; ++k) se += expf(z[k] - mx);
-    const float lse = mx + logf(se);
-    float lp[4];
-    for (int k = 0; k < 4; ++k) {
-        lp[k] = z[k] - lse;
-        if (logprob) logprob[item * 4 + k] = lp[k];
-    }
-    if (targets) {
-        float loss = 0.0f;
-        for (int k = 0; k < 4; ++k) {
-            const float q = targets[item * 4 + k];
-            loss -= q * lp[k];
-            g5[item * 4 + k] = (expf(lp[k]) - q) / ((float)n * (float)LL);
+    const float Ma = warp_prod_except(ta, -1), Mb = warp_prod_except(tb, -1);
+    // class code of the pure error: sigma_x strings of the sigma_z defects
+    // that go left cross column 0, sigma_z strings of the sigma_x defects
+    // that go up cross row 0
+    const uint8_t* s = syn + item * 2 * L * (L - 1);
+    int pa = 0, pb = 0;
+    for (int g = lane; g < 2 * L * (L - 1); g += 32) {
+        if (!(s[g] & 1)) continue;
+        if (g < L * (L - 1)) {
+            const int i = g / L;                       // sigma_x generator row (2i+1, 2j)
+            pb ^= 2 * (i + 1) <= L;
+        } else {
+            const int j = (g - L * (L - 1)) % (L - 1);  // sigma_z generator (2i, 2j+1)
+            pa ^= 2 * (j + 1) <= L;
         }
-        loss_item[item] = loss;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pa ^= __shfl_xor_sync(0xffffffffu, pa, o);
+        pb ^= __shfl_xor_sync(0xffffffffu, pb, o);
+    }
+    const float Mac = fminf(fmaxf(Ma, -1.0f + kClip), 1.0f - kClip);
+    const float Mbc = fminf(fmaxf(Mb, -1.0f + kClip), 1.0f - kClip);
+    const float ln2 = 0.69314718f;
+    const float la[2] = {log1pf(Mac) - ln2, log1pf(-Mac) - ln2};
+    const float lb[2] = {log1pf(Mbc) - ln2, log1pf(-Mbc) - ln2};
+    float lp[4];
+    for (int k = 0; k < 4; ++k) lp[k] = la[(k & 1) ^ pa] + lb[(k >> 1) ^ pb];
+    if (lane == 0 && logprob)
+        for (int k = 0; k < 4; ++k) logprob[item * 4 + k] = lp[k];
+    if (!targets) return;
+    float q[4], ga[2] = {0.f, 0.f}, gb[2] = {0.f, 0.f}, loss = 0.0f;
+    for (int k = 0; k < 4; ++k) {
+        q[k] = targets[item * 4 + k];
+        loss -= q[k] * lp[k];
+        ga[(k & 1) ^ pa] -= q[k] / (float)n;
+        gb[(k >> 1) ^ pb] -= q[k] / (float)n;
+    }
+    if (lane == 0) loss_item[item] = loss;
+    const bool ina = Ma > -1.0f + kClip && Ma < 1.0f - kClip;
+    const bool inb = Mb > -1.0f + kClip && Mb < 1.0f - kClip;
+    const float dMa = ina ? ga[0] / (1.0f + Ma) - ga[1] / (1.0f - Ma) : 0.0f;
+    const float dMb = inb ? gb[0] / (1.0f + Mb) - gb[1] / (1.0f - Mb) : 0.0f;
+    const float oa = warp_prod_except(ta, lane), ob = warp_prod_except(tb, lane);
+    if (lane < L) {
+        dz5[(base + (long long)lane * L + m) * 2 + 0] = dMa * oa * (-0.5f * (1.0f - ta * ta));
+        dz5[(base + (long long)m * L + lane) * 2 + 1] = dMb * ob * (-0.5f * (1.0f - tb * tb));
     }
 }
 
@@ -729,9 +767,9 @@ __global__ void loss_sum_kernel(const float* loss_item, long long n, float* loss
 }
 
 // Input gradient of the last layer, gated by the ReLU of layer 4:
-// dZ4[q][ci] = [a4[q][ci] > 0] sum over taps (kh, kw) with q - (kh-1, kw-1)
-// inside the map of sum_co W5[co][kh][kw][ci] g5[item][co].
-__global__ void conv5_dgrad_kernel(const bf16* w5, const float* g5, const bf16* a4, long long M, int L,
+// dZ4[q][ci] = [a4[q][ci] > 0] sum over taps (kh, kw) with p = q - (kh-1,
+// kw-1) inside the map of sum_co W5[co][kh][kw][ci] dz5[p][co].
+__global__ void conv5_dgrad_kernel(const bf16* w5, const float* dz5, const bf16* a4, long long M, int L,
                                    bf16* dz4) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // m * 8 + ci group
     if (i >= M * 8) return;
@@ -740,13 +778,15 @@ __global__ void conv5_dgrad_kernel(const bf16* w5, const float* g5, const bf16* 
     const int LL = L * L;
     const long long item = m / LL;
     const int rem = (int)(m - item * LL), y = rem / L, x = rem - (rem / L) * L;
-    float g[4];
-    for (int co = 0; co < 4; ++co) g[co] = g5[item * 4 + co];
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int t = 0; t < 9; ++t) {
-        const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+        const int dy = t / 3 - 1, dx = t % 3 - 1;
+        const int yy = y - dy, xx = x - dx;
         if (yy < 0 || yy >= L || xx < 0 || xx >= L) continue;
-        for (int co = 0; co < 4; ++co) {
+        const float2 d = *reinterpret_cast<const float2*>(dz5 + (m - dy * L - dx) * 2);
+        if (d.x == 0.0f && d.y == 0.0f) continue;
+        const float g[2] = {d.x, d.y};
+        for (int co = 0; co < kOut; ++co) {
             const uint4 wv = *reinterpret_cast<const uint4*>(w5 + (long long)co * 576 + t * 64 + cg);
             const uint32_t ww[4] = {wv.x, wv.y, wv.z, wv.w};
             for (int j = 0; j < 4; ++j) {
@@ -763,36 +803,51 @@ __global__ void conv5_dgrad_kernel(const bf16* w5, const float* g5, const bf16* 
     *reinterpret_cast<uint4*>(dz4 + m * 64 + cg) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
-// Box sums of layer 4 under each tap: S[item][tap][ci] = sum over positions
-// p of the map with p + offset(tap) inside of a4[p + offset(tap)][ci].
-__global__ void conv5_boxsum_kernel(const bf16* a4, int L, float* S) {
+// Last-layer weight and bias gradients of one syndrome (block per item, 576
+// threads = (tap, ci)): S[item][co][tap * 64 + ci] = sum_p dz5[p][co]
+// a4[p + offset(tap)][ci] over positions p of the map with p + offset inside;
+// Sb[item][co] = sum_p dz5[p][co].  Positions in order.
+__global__ void conv5_wgrad_item_kernel(const float* dz5, const bf16* a4, int L, float* S, float* Sb) {
     const long long item = blockIdx.x;
-    const int t = threadIdx.x >> 6, ci = threadIdx.x & 63;  // blockDim 576
+    const int t = threadIdx.x >> 6, ci = threadIdx.x & 63;
     const int dy = t / 3 - 1, dx = t % 3 - 1;
-    const int y0 = dy > 0 ? dy : 0, y1 = dy < 0 ? L + dy : L;
-    const int x0 = dx > 0 ? dx : 0, x1 = dx < 0 ? L + dx : L;
-    const bf16* a = a4 + item * L * L * 64;
-    float s = 0.0f;
-    for (int y = y0; y < y1; ++y)
-        for (int x = x0; x < x1; ++x) s += __bfloat162float(a[(y * L + x) * 64 + ci]);
-    S[item * 576 + threadIdx.x] = s;
+    const int LL = L * L;
+    const float* d = dz5 + item * LL * 2;
+    const bf16* a = a4 + item * LL * 64;
+    float acc0 = 0.0f, acc1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+    for (int p = 0; p < LL; ++p) {
+        const float d0 = d[2 * p], d1 = d[2 * p + 1];
+        if (d0 == 0.0f && d1 == 0.0f) continue;
+        b0 += d0;
+        b1 += d1;
+        const int y = p / L + dy, x = p % L + dx;
+        if (y < 0 || y >= L || x < 0 || x >= L) continue;
+        const float v = __bfloat162float(a[(y * L + x) * 64 + ci]);
+        acc0 += d0 * v;
+        acc1 += d1 * v;
+    }
+    S[(item * 2 + 0) * 576 + threadIdx.x] = acc0;
+    S[(item * 2 + 1) * 576 + threadIdx.x] = acc1;
+    if (threadIdx.x == 0) {
+        Sb[item * 2 + 0] = b0;
+        Sb[item * 2 + 1] = b1;
+    }
 }
 
-// Last-layer weight and bias gradients: dW5[co][j] = sum_item g5[item][co]
-// S[item][j]; db5[co] = L^2 sum_item g5[item][co].  Items in order.
-__global__ void conv5_wgrad_kernel(const float* S, const float* g5, long long n, int L, float* grad_w,
-                                   float* grad_b) {
+// Sum over the items in order: dW5[co][j] = sum_item S[item][co][j],
+// db5[co] = sum_item Sb[item][co].
+__global__ void conv5_wgrad_kernel(const float* S, const float* Sb, long long n, float* grad_w, float* grad_b) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 4 * 576) {
+    if (i < kOut * 576) {
         const int co = i / 576, j = i - co * 576;
         float s = 0.0f;
-        for (long long k = 0; k < n; ++k) s += g5[k * 4 + co] * S[k * 576 + j];
+        for (long long k = 0; k < n; ++k) s += S[(k * 2 + co) * 576 + j];
         grad_w[i] = s;
-    } else if (i < 4 * 576 + 4) {
-        const int co = i - 4 * 576;
+    } else if (i < kOut * 576 + kOut) {
+        const int co = i - kOut * 576;
         float s = 0.0f;
-        for (long long k = 0; k < n; ++k) s += g5[k * 4 + co];
-        grad_b[co] = s * (float)(L * L);
+        for (long long k = 0; k < n; ++k) s += Sb[k * 2 + co];
+        grad_b[co] = s;
     }
 }
 
@@ -806,6 +861,19 @@ __global__ void adam_kernel(float* theta, float* m1, float* m2, const float* gra
     m1[i] = a;
     m2[i] = b;
     theta[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+__global__ void soft_targets_kernel(const double* lr, long long n, float* q) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double m = lr[i * 4];
+    for (int k = 1; k < 4; ++k) m = fmax(m, lr[i * 4 + k]);
+    double e[4], s = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        e[k] = exp(lr[i * 4 + k] - m);
+        s += e[k];
+    }
+    for (int k = 0; k < 4; ++k) q[i * 4 + k] = (float)(e[k] / s);
 }
 
 template <typename K>
@@ -835,7 +903,7 @@ struct CnnNet {
     bf16* act[4] = {};
     float* z5 = nullptr;
     bf16* dz[2] = {};
-    float *logprob = nullptr, *g5 = nullptr, *loss_item = nullptr, *loss = nullptr, *S5 = nullptr;
+    float *logprob = nullptr, *dz5 = nullptr, *loss_item = nullptr, *loss = nullptr, *S5 = nullptr, *Sb5 = nullptr;
     float* partial = nullptr;
     int* err = nullptr;
     std::vector<void*> allocs;
@@ -950,8 +1018,9 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
     a.out_bf16 = nullptr;
     a.out_f32 = net->z5;
     if ((e = launch_conv<64, 16, kEpiLogit>(net, a, s))) return e;
-    pool_loss_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(net->z5, n, L, targets, logprob, net->g5,
-                                                             net->loss_item);
+    if (targets && (e = cudaMemsetAsync(net->dz5, 0, (size_t)M * 8, s))) return e;
+    readout_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(net->z5, syn, n, L, targets, logprob, net->dz5,
+                                                           net->loss_item);
     return cudaGetLastError();
 }
 
@@ -964,13 +1033,13 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
     loss_sum_kernel<<<1, 256, 0, s>>>(net->loss_item, n, net->loss);
     if ((e = cudaGetLastError())) return e;
     // last layer (CUDA cores)
-    conv5_boxsum_kernel<<<(unsigned)n, 576, 0, s>>>(net->act[3], L, net->S5);
+    conv5_wgrad_item_kernel<<<(unsigned)n, 576, 0, s>>>(net->dz5, net->act[3], L, net->S5, net->Sb5);
     if ((e = cudaGetLastError())) return e;
-    conv5_wgrad_kernel<<<(4 * 576 + 4 + 255) / 256, 256, 0, s>>>(net->S5, net->g5, n, L,
-                                                                  net->grad + layer_woff(4),
-                                                                  net->grad + layer_boff(4));
+    conv5_wgrad_kernel<<<(kOut * 576 + kOut + 255) / 256, 256, 0, s>>>(net->S5, net->Sb5, n,
+                                                                        net->grad + layer_woff(4),
+                                                                        net->grad + layer_boff(4));
     if ((e = cudaGetLastError())) return e;
-    conv5_dgrad_kernel<<<(unsigned)((M * 8 + 255) / 256), 256, 0, s>>>(net->fwd[4], net->g5, net->act[3], M, L,
+    conv5_dgrad_kernel<<<(unsigned)((M * 8 + 255) / 256), 256, 0, s>>>(net->fwd[4], net->dz5, net->act[3], M, L,
                                                                         net->dz[0]);
     if ((e = cudaGetLastError())) return e;
     // layers 4, 3, 2: weight gradient, then input gradient gated by the layer below
@@ -1105,14 +1174,15 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     na(&net->targets, (size_t)max_batch * 16);
     na(&net->x0, (size_t)M * 4);
     for (int l = 0; l < 4; ++l) na(&net->act[l], (size_t)M * 128);
-    na(&net->z5, (size_t)M * 16);
+    na(&net->z5, (size_t)M * 8);
+    na(&net->dz5, (size_t)M * 8);
     na(&net->dz[0], (size_t)M * 128);
     na(&net->dz[1], (size_t)M * 128);
     na(&net->logprob, (size_t)max_batch * 16);
-    na(&net->g5, (size_t)max_batch * 16);
     na(&net->loss_item, (size_t)max_batch * 4);
     na(&net->loss, 4);
-    na(&net->S5, (size_t)max_batch * 576 * 4);
+    na(&net->S5, (size_t)max_batch * 2 * 576 * 4);
+    na(&net->Sb5, (size_t)max_batch * 2 * 4);
     na(&net->partial, (size_t)kMaxSplits * 640 * 64 * 4);
     na(&net->err, 4);
     if (e == cudaSuccess) e = cudaMemset(net->err, 0, 4);
@@ -1234,6 +1304,14 @@ int surfmcmc_cnn_train_step(surfmcmc_cnn* net, const uint8_t* syndromes, const f
     if (e != cudaSuccess) return cuda_fail(net, e, "network train_step");
     if (out_loss && !device_ptr(out_loss)) return check_err(net, s);
     return SURFMCMC_OK;
+}
+
+int surfmcmc_cnn_soft_targets(const double* log_ratio, int64_t n, float* targets, void* stream) {
+    if (n < 0) return SURFMCMC_EINVAL;
+    if (n == 0) return SURFMCMC_OK;
+    if (!device_ptr(log_ratio) || !device_ptr(targets)) return SURFMCMC_EINVAL;
+    soft_targets_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(log_ratio, n, targets);
+    return cudaGetLastError() == cudaSuccess ? SURFMCMC_OK : SURFMCMC_ECUDA;
 }
 
 int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream) {

@@ -177,6 +177,15 @@ cudaError_t launch_class_means(long long n, int K, int R, int N, int j, uint64_t
 cudaError_t launch_ti_decide(long long n, int K, int N, double mean0, double h3, double* mean, int32_t* out_class,
                              double* out_log_z, cudaStream_t s);
 
+cudaError_t launch_retire(long long n, const long long* perm, const float* logprob, const int32_t* cls,
+                          const uint64_t* class_sum, float tau, uint32_t sweeps, int final_chunk, int32_t* out_class,
+                          uint64_t* out_class_sum, uint32_t* out_sweeps, int32_t* keep, cudaStream_t s);
+cudaError_t launch_compact(long long n, const int32_t* keep, long long* pos, long long* count, const long long* perm,
+                           uint32_t id0, int frame_words, int chains, const uint32_t* frames, const uint64_t* sums,
+                           long long* perm_out, uint32_t* ids_out, uint32_t* frames_out, uint64_t* sums_out,
+                           cudaStream_t s);
+cudaError_t launch_iota(long long n, long long* perm, cudaStream_t s);
+
 // Context services shared with the network code (api.cu).
 void ctx_set_error(surfmcmc_ctx* ctx, const char* msg);
 int ctx_device(const surfmcmc_ctx* ctx);

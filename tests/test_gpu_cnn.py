@@ -69,7 +69,7 @@ def test_forward_parity_small(pkg, ctx, L, n, seed):
     net = pkg.Network(ctx, L, max_batch=64)
     net.set_params(p.astype(np.float32))
     lp = net.forward(syn)
-    ref = cnn.forward(p.astype(np.float32).astype(np.float64), cnn.syndrome_maps(syn, L), bf16=True)
+    ref = cnn.forward(p.astype(np.float32).astype(np.float64), syn, L, bf16=True)
     _forward_check(lp, ref)
     net.close()
 
@@ -86,7 +86,7 @@ def test_forward_parity_many_tiles(pkg, ctx):
     dev = torch.from_numpy(syn).cuda()
     lp = net.forward(dev).cpu().numpy()
     idx = np.array(sorted(set(np.linspace(0, n - 1, 20).astype(int).tolist())))
-    ref = cnn.forward(p.astype(np.float32).astype(np.float64), cnn.syndrome_maps(syn[idx], L), bf16=True)
+    ref = cnn.forward(p.astype(np.float32).astype(np.float64), syn[idx], L, bf16=True)
     _forward_check(lp[idx], ref)
     net.close()
 
@@ -121,7 +121,7 @@ def test_gradient_parity(pkg, ctx, L, n, seed):
     net = pkg.Network(ctx, L, max_batch=n)
     net.set_params(p)
     loss, g = net.gradient(syn, q.astype(np.float32))
-    rl, rg = cnn.loss_and_grad(p.astype(np.float64), cnn.syndrome_maps(syn, L), q, bf16=True)
+    rl, rg = cnn.loss_and_grad(p.astype(np.float64), syn, L, q, bf16=True)
     assert abs(loss - rl) < 1e-3 * max(1.0, abs(rl)), (loss, rl)
     for name, sl in _layer_slices():
         a, b = g[sl].astype(np.float64), rg[sl]
