@@ -64,17 +64,17 @@ def lib():
         L.orc_chain_uniform_less.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, C.c_int,
                                              C.c_int, C.c_uint64]
         L.orc_run_chains.argtypes = [C.c_void_p, u8p, C.c_int, u8p, u8p, u64p, C.c_void_p, C.c_void_p, C.c_void_p]
-        L.orc_decide.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double, u64p, u64p, f64p]
+        L.orc_decide.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, u64p, u64p, f64p]
         L.orc_decode_one.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double,
                                      C.c_int, C.c_double, C.c_uint64, C.c_uint32, u8p, u64p, f64p, u64p, i32p, u8p,
-                                     u8p, C.c_void_p]
+                                     u8p, C.c_void_p, C.c_int]
         L.orc_anneal_scale.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
         L.orc_anneal_scale.restype = C.c_double
         L.orc_anneal_stage.argtypes = [C.c_uint32, C.c_uint32, C.c_int]
         L.orc_exact_histogram.argtypes = [C.c_int, u8p, u64p]
         L.orc_simpson_integral.argtypes = [C.c_int, C.c_int, f64p, C.c_double, f64p]
         L.orc_decode_ti.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double,
-                                    C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32, u8p, f64p, f64p]
+                                    C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32, u8p, f64p, f64p, C.c_int]
         _lib = L
     return _lib
 
@@ -83,7 +83,7 @@ class _Run(C.Structure):
     _fields_ = [("L", C.c_int32), ("K", C.c_int32), ("R", C.c_int32), ("t_begin", C.c_uint32),
                 ("t_end", C.c_uint32), ("burn_in", C.c_uint32), ("p", C.c_double), ("beta_scale", C.c_double),
                 ("seed", C.c_uint64), ("id", C.c_uint32), ("anneal_stages", C.c_int32),
-                ("anneal_beta0", C.c_double)]
+                ("anneal_beta0", C.c_double), ("scan", C.c_int32)]
 
 
 def nq(L: int) -> int:
@@ -206,7 +206,7 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
 
 
 def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_scale=1.0,
-               frames=None, chain_sum=None, trace=False, accepts=False, anneal_stages=0, anneal_beta0=1.0):
+               frames=None, chain_sum=None, trace=False, accepts=False, anneal_stages=0, anneal_beta0=1.0, scan=0):
     """Run all K*R chains of one syndrome from sweep t_begin to t_end.  With
     frames=None the chains start from the start frames of `syn`; otherwise
     frames = (fx, fz) [C][nq] uint8 is the state at t_begin.  Returns a dict
@@ -220,7 +220,7 @@ def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_sca
     cn = np.zeros(Cn, np.int32)
     acc = np.zeros(Cn, np.uint64) if accepts else None
     tr = np.zeros(4 * (t_end - t_begin), np.int32) if trace else None
-    a = _Run(L, K, R, t_begin, t_end, burn_in, p, beta_scale, seed, ident, anneal_stages, anneal_beta0)
+    a = _Run(L, K, R, t_begin, t_end, burn_in, p, beta_scale, seed, ident, anneal_stages, anneal_beta0, scan)
     lib().orc_run_chains(C.addressof(a), np.ascontiguousarray(syn, np.uint8), 1 if frames is None else 0,
                          fx, fz, cs, cn.ctypes.data, None if acc is None else acc.ctypes.data,
                          None if tr is None else tr.ctypes.data)
@@ -232,16 +232,16 @@ def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_sca
     return out
 
 
-def decide(K, R, n_sweeps, burn_in, beta_bar, chain_sum):
+def decide(K, R, n_sweeps, burn_in, beta_bar, chain_sum, samples_per_sweep=4):
     cs = np.ascontiguousarray(chain_sum, np.uint64)
     S = np.zeros(K, np.uint64)
     lr = np.zeros(K, np.float64)
-    k = lib().orc_decide(K, R, n_sweeps, burn_in, beta_bar, cs, S, lr)
+    k = lib().orc_decide(K, R, n_sweeps, burn_in, samples_per_sweep, beta_bar, cs, S, lr)
     return k, S, lr
 
 
 def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0, accepts=False,
-               anneal_stages=0, anneal_beta0=1.0):
+               anneal_stages=0, anneal_beta0=1.0, scan=0):
     """Decode one syndrome; returns a dict with the chosen class, per-class
     sums and log-ratios, per-chain sums, final n and final frames."""
     Cn = K * R
@@ -255,7 +255,7 @@ def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0
     acc = np.zeros(Cn, np.uint64) if accepts else None
     k = lib().orc_decode_one(L, p, K, R, n_sweeps, burn_in, beta_scale, anneal_stages, anneal_beta0, seed, ident,
                              np.ascontiguousarray(syn, np.uint8), S, lr, cs, cn, fx, fz,
-                             None if acc is None else acc.ctypes.data)
+                             None if acc is None else acc.ctypes.data, scan)
     out = {"cls": k, "class_sum": S, "log_ratio": lr, "chain_sum": cs, "chain_n": cn,
            "frames_x": fx, "frames_z": fz}
     if accepts:
@@ -285,9 +285,9 @@ def exact_class_stats(L: int, syn: np.ndarray, beta: float):
 
 
 def _decode_worker(args):
-    (L, p, K, R, n_sweeps, seed, ident, syn, burn_in, beta_scale, anneal_stages, anneal_beta0) = args
+    (L, p, K, R, n_sweeps, seed, ident, syn, burn_in, beta_scale, anneal_stages, anneal_beta0, scan) = args
     d = decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=burn_in, beta_scale=beta_scale,
-                   anneal_stages=anneal_stages, anneal_beta0=anneal_beta0)
+                   anneal_stages=anneal_stages, anneal_beta0=anneal_beta0, scan=scan)
     return d
 
 
@@ -300,13 +300,13 @@ def anneal_stage(t, B, S):
 
 
 def decode_batch(L, p, K, R, n_sweeps, seed, ids, syns, burn_in=0, beta_scale=1.0, processes=None,
-                 anneal_stages=0, anneal_beta0=1.0):
+                 anneal_stages=0, anneal_beta0=1.0, scan=0):
     """decode_one over many syndromes, one process per syndrome block
     (multiprocessing with the spawn start method, safe after CUDA use).
     Returns the list of per-syndrome result dicts in input order."""
     import multiprocessing as mp
     jobs = [(L, p, K, R, n_sweeps, seed, int(i), np.ascontiguousarray(s, np.uint8), burn_in, beta_scale,
-             anneal_stages, anneal_beta0) for i, s in zip(ids, syns)]
+             anneal_stages, anneal_beta0, scan) for i, s in zip(ids, syns)]
     if processes == 1 or len(jobs) <= 1:
         return [_decode_worker(j) for j in jobs]
     with mp.get_context("spawn").Pool(processes or os.cpu_count()) as pool:
@@ -325,13 +325,13 @@ def simpson_integral(mean, beta_bar):
 
 
 def decode_ti(L, p, K, R, n_sweeps, seed, ident, syn, n_beta=21, burn_in=0, beta_scale=1.0, anneal_stages=0,
-              anneal_beta0=1.0):
+              anneal_beta0=1.0, scan=0):
     """Thermodynamic-integration decode (Eq. 6, Simpson over n_beta points):
     returns (class, log Z_k - max log Z, means [K][n_beta])."""
     mean = np.zeros((K, n_beta), np.float64)
     lz = np.zeros(K, np.float64)
     k = lib().orc_decode_ti(L, p, K, R, n_sweeps, burn_in, beta_scale, anneal_stages, anneal_beta0, n_beta, seed,
-                            ident, np.ascontiguousarray(syn, np.uint8), mean, lz)
+                            ident, np.ascontiguousarray(syn, np.uint8), mean, lz, scan)
     if k < 0:
         raise ValueError("bad TI arguments")
     return k, lz, mean

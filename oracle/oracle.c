@@ -390,6 +390,7 @@ typedef struct {
     uint32_t id;
     int32_t anneal_stages;
     double anneal_beta0;
+    int32_t scan;          /* 0: colour sweeps (Sec. V); 1: one random generator per step (Sec. IV) */
 } orc_run_t;
 
 /* Start preparation (reading of Sec. IV: the chains should start near the
@@ -442,6 +443,36 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
         for (uint32_t t = a->t_begin; t < a->t_end; ++t) {
             int stage = a->anneal_stages > 0 ? orc_anneal_stage(t, a->burn_in, a->anneal_stages) : -1;
             const uint64_t* T = stage >= 0 ? Tst[stage] : Tmain;
+            if (a->scan) {
+                /* Sec. IV as written: each step picks one generator at
+                 * random, g = floor(w0 n_stab / 2^32), and applies it when
+                 * Delta n <= 0 or w1 < T[Delta n]; f(n) = n is summed after
+                 * every step.  A sweep is n_stab steps; Philox counter
+                 * (id, chain, t, step), words w0, w1. */
+                int ns = orc_nstab(L);
+                for (int step = 0; step < ns; ++step) {
+                    uint32_t ctr[4] = {a->id, (uint32_t)c, t, (uint32_t)step}, key[2], blk[4];
+                    key[0] = (uint32_t)a->seed;
+                    key[1] = (uint32_t)(a->seed >> 32);
+                    orc_philox4x32_10(ctr, key, blk);
+                    int g = (int)(((uint64_t)blk[0] * (uint64_t)ns) >> 32);
+                    int r, cc;
+                    int type = orc_stab_pos(L, g, &r, &cc);
+                    int32_t q[4];
+                    int w = orc_stab_support(L, g, q);
+                    int dn = delta_n(type, w, q, ex, ez);
+                    if (dn <= 0 || (uint64_t)blk[1] < T[dn]) {
+                        for (int k = 0; k < w; ++k) {
+                            if (type == 0) ex[q[k]] ^= 1; else ez[q[k]] ^= 1;
+                        }
+                        n += dn;
+                        if (accepts) accepts[c] += 1;
+                    }
+                    if (t >= a->burn_in) chain_sum[c] += (uint64_t)n;
+                }
+                if (trace && c == 0) trace[t - a->t_begin] = n;
+                continue;
+            }
             for (int col = 0; col < 4; ++col) {
                 int type = col / 2;
                 for (int m = 0; m < ncol[col]; ++m) {
@@ -473,7 +504,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
  * class with the smallest S_k (the smallest <n>, all classes having the same
  * number of samples), lowest k on ties.  Also reports the log-ratio proxy
  * -beta_bar (<n>_k - min_k <n>_k). */
-int orc_decide(int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_bar,
+int orc_decide(int K, int R, uint32_t n_sweeps, uint32_t burn_in, uint32_t samples_per_sweep, double beta_bar,
                const uint64_t* chain_sum, uint64_t* class_sum, double* log_ratio)
 {
     uint64_t S[64];
@@ -485,7 +516,8 @@ int orc_decide(int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_ba
         if (class_sum) class_sum[k] = S[k];
     }
     if (log_ratio) {
-        uint64_t samples = n_sweeps > burn_in ? (uint64_t)4 * (uint64_t)R * (n_sweeps - burn_in) : 0;
+        uint64_t samples =
+            n_sweeps > burn_in ? (uint64_t)samples_per_sweep * (uint64_t)R * (n_sweeps - burn_in) : 0;
         for (int k = 0; k < K; ++k) {
             if (samples == 0) { log_ratio[k] = 0.0; continue; }
             double mean_k = (double)S[k] / (double)samples;
@@ -500,10 +532,10 @@ int orc_decide(int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_ba
 int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in,
                    double beta_scale, int anneal_stages, double anneal_beta0, uint64_t seed, uint32_t id,
                    const uint8_t* syn, uint64_t* class_sum, double* log_ratio, uint64_t* chain_sum,
-                   int32_t* chain_n, uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts)
+                   int32_t* chain_n, uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts, int scan)
 {
     int nq = orc_nq(L), C = K * R;
-    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0};
+    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0, scan};
     uint8_t* fx = frames_x ? frames_x : malloc((size_t)C * nq);
     uint8_t* fz = frames_z ? frames_z : malloc((size_t)C * nq);
     uint64_t* cs = chain_sum ? chain_sum : malloc(sizeof(uint64_t) * C);
@@ -513,7 +545,8 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
     double beta_bar;
     uint64_t T[5];
     orc_thresholds(p, 1.0, T, &beta_bar);
-    int k = orc_decide(K, R, n_sweeps, burn_in, beta_bar, cs, class_sum, log_ratio);
+    int k = orc_decide(K, R, n_sweeps, burn_in, scan ? (uint32_t)orc_nstab(L) : 4u, beta_bar, cs, class_sum,
+                       log_ratio);
     if (!frames_x) free(fx);
     if (!frames_z) free(fz);
     if (!chain_sum) free(cs);
@@ -586,11 +619,12 @@ int orc_simpson_integral(int K, int N, const double* mean, double beta_bar, doub
  * log_z[k] = -(I_k - min_k I_k).  mean_out[k*N + j] receives the means. */
 int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_scale,
                   int anneal_stages, double anneal_beta0, int N, uint64_t seed, uint32_t id,
-                  const uint8_t* syn, double* mean_out, double* log_z)
+                  const uint8_t* syn, double* mean_out, double* log_z, int scan)
 {
     int nq = orc_nq(L), C = K * R;
     if (N < 3 || N % 2 == 0 || N > 129 || K > 64) return -1;
-    uint64_t samples = n_sweeps > burn_in ? (uint64_t)4 * (uint64_t)R * (n_sweeps - burn_in) : 0;
+    uint64_t per_sweep = scan ? (uint64_t)orc_nstab(L) : 4u;
+    uint64_t samples = n_sweeps > burn_in ? per_sweep * (uint64_t)R * (n_sweeps - burn_in) : 0;
     if (samples == 0) return -1;
     uint8_t* fx = malloc((size_t)C * nq);
     uint8_t* fz = malloc((size_t)C * nq);
@@ -599,7 +633,8 @@ int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bur
     for (int k = 0; k < K; ++k) mean[k * N] = 0.75 * (double)nq;
     for (int j = 1; j < N; ++j) {
         double bs = beta_scale * (double)j / (double)(N - 1);
-        orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, bs, seed + (uint64_t)j, id, anneal_stages, anneal_beta0};
+        orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, bs, seed + (uint64_t)j, id, anneal_stages, anneal_beta0,
+                       scan};
         memset(cs, 0, sizeof(uint64_t) * C);
         orc_run_chains(&a, syn, 1, fx, fz, cs, NULL, NULL, NULL);
         for (int k = 0; k < K; ++k) {
