@@ -84,7 +84,16 @@ typedef struct surfmcmc_server surfmcmc_server;
  *                    floor(jB/S) .. floor((j+1)B/S)-1 (B = burn_in) run at
  *                    beta* (a0 + (1 - a0) j / S), j = 0..S-1; needs
  *                    S <= burn_in and S <= 64.
- *   anneal_beta0     a0 in (0, 1], the first stage's fraction of beta*. */
+ *   anneal_beta0     a0 in (0, 1], the first stage's fraction of beta*.
+ *   scan             0: sweeps as above.  1: Sec. IV as written, one
+ *                    generator picked at random per step, g = floor(w0
+ *                    n_stab / 2^32), applied when Delta n <= 0 or w1 <
+ *                    T[Delta n], with Philox4x32-10 words (w0, w1) of
+ *                    counter (syndrome id, chain k R + r, sweep t, step)
+ *                    and key (seed_lo, seed_hi); a sweep is n_stab steps and
+ *                    n is summed after every step, so the sample count is
+ *                    n_stab R (n_sweeps - burn_in) per class.  Needs
+ *                    lanes_per_bundle 0 or 32. */
 typedef struct {
     int32_t n_classes;
     int32_t chains_per_class;
@@ -94,6 +103,7 @@ typedef struct {
     int32_t lanes_per_bundle;
     int32_t anneal_stages;
     double anneal_beta0;
+    int32_t scan;
 } surfmcmc_opts;
 
 /* Fills opts with K = 4, R = 4, 2000 sweeps, no burn-in, beta* = beta_bar,
@@ -318,8 +328,8 @@ int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches);
  * every GPU that loads the library holds until the process exits.
  *   Buffers: syndromes, out_class and (if not NULL) out_class_sum and
  *   out_log_ratio must be device memory of the current device; the layouts
- *   and results are those of surfmcmc_decode.  opts->lanes_per_bundle and
- *   opts->anneal_stages must be 0.  With stream == NULL the call returns after the results are
+ *   and results are those of surfmcmc_decode.  opts->lanes_per_bundle,
+ *   opts->anneal_stages and opts->scan must be 0.  With stream == NULL the call returns after the results are
  *   written; otherwise it is stream-ordered.
  *   Scratch: the call needs surfmcmc_noalloc_scratch_needed(n, L, R) bytes;
  *   a batch needing more than SURFMCMC_NOALLOC_SCRATCH_BYTES is rejected with

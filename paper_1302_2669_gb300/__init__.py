@@ -35,7 +35,7 @@ class SurfmcmcError(RuntimeError):
 class _Opts(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("chains_per_class", C.c_int32), ("n_sweeps", C.c_uint32),
                 ("burn_in", C.c_uint32), ("beta_scale", C.c_double), ("lanes_per_bundle", C.c_int32),
-                ("anneal_stages", C.c_int32), ("anneal_beta0", C.c_double)]
+                ("anneal_stages", C.c_int32), ("anneal_beta0", C.c_double), ("scan", C.c_int32)]
 
 
 class _ServerOpts(C.Structure):
@@ -54,10 +54,11 @@ class Opts:
     lanes_per_bundle: int = 0
     anneal_stages: int = 0
     anneal_beta0: float = 1.0
+    scan: int = 0
 
     def c(self) -> _Opts:
         return _Opts(self.n_classes, self.chains_per_class, self.n_sweeps, self.burn_in, self.beta_scale,
-                     self.lanes_per_bundle, self.anneal_stages, self.anneal_beta0)
+                     self.lanes_per_bundle, self.anneal_stages, self.anneal_beta0, self.scan)
 
 
 EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surfmcmc_strerror",

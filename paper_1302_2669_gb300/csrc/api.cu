@@ -161,6 +161,7 @@ void set_temperature(SweepParams& sp, double p, double beta_scale) {
     uint64_t T[5];
     double beta_bar;
     acceptance_table(p, beta_scale, T, &beta_bar);
+    for (int d = 0; d < 5; ++d) sp.T[d] = T[d];
     sp.accept_all = T[1] >= 4294967296ull;
     sp.reject_all = T[1] == 0;
     sp.qmodes = 0;
@@ -241,8 +242,15 @@ int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
         return fail(ctx, SURFMCMC_EINVAL, "anneal_stages=%d outside 0..64", o.anneal_stages);
     if (o.anneal_stages > 0 && ((uint32_t)o.anneal_stages > o.burn_in || !(o.anneal_beta0 > 0.0 && o.anneal_beta0 <= 1.0)))
         return fail(ctx, SURFMCMC_EINVAL, "annealing needs anneal_stages <= burn_in and 0 < anneal_beta0 <= 1");
+    if (o.scan != 0 && o.scan != 1) return fail(ctx, SURFMCMC_EINVAL, "scan=%d must be 0 or 1", o.scan);
+    if (o.scan == 1 && o.lanes_per_bundle != 0 && o.lanes_per_bundle != 32)
+        return fail(ctx, SURFMCMC_EINVAL, "random scan runs 32 lanes per bundle");
     return SURFMCMC_OK;
 }
+
+// Samples of n per chain and sweep: one per colour phase (sweeps), one per
+// step (random scan: n_stab steps per sweep).
+uint64_t samples_per_sweep(const surfmcmc_opts& o, int L) { return o.scan ? (uint64_t)n_stabs(L) : 4u; }
 
 // Chain layout of a run: C chains per syndrome, plane width G, bundles of 32
 // chains (G = 32: C/32 bundles per syndrome; G < 32: 32/G syndromes per
@@ -442,9 +450,11 @@ int ragged_layout(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* sweeps, 
     for (auto& g : lay.groups) lmax = std::max(lmax, g.L);
     if (pick_lanes(lay.groups.empty() ? 2 : lay.groups[0].L, o.lanes_per_bundle, &lay.lam, ctx, o.chains_per_class))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported", o.lanes_per_bundle);
+    if (o.scan) lay.lam = 32;
     while (sweep_smem_bytes(n_qubits(lmax), lmax * (lmax - 1) / 2, lay.lam) > 200 * 1024 && lay.lam < 32) lay.lam *= 2;
     const int Cn = 4 * o.chains_per_class;
     init_chains(lay.sp, Cn, o.chains_per_class, 0);
+    lay.sp.scan = o.scan;
     long long dst = 0, item = 0, e0w = 0, stw = 0;
     for (auto& g : lay.groups) {
         add_group(lay.sp, g.L, (long long)g.items.size(), item, e0w, 0, stw, lay.lam);
@@ -452,7 +462,8 @@ int ragged_layout(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* sweeps, 
             lay.perm.push_back(i);
             lay.dst_off.push_back(dst);
             lay.len.push_back(n_stabs(g.L));
-            lay.samples.push_back(g.sweeps > g.burn ? (uint64_t)4 * o.chains_per_class * (g.sweeps - g.burn) : 0);
+            lay.samples.push_back(g.sweeps > g.burn ? samples_per_sweep(o, g.L) * o.chains_per_class * (g.sweeps - g.burn)
+                                                    : 0);
             dst += n_stabs(g.L);
         }
         item += (long long)g.items.size();
@@ -619,6 +630,7 @@ void surfmcmc_default_opts(surfmcmc_opts* o) {
     o->lanes_per_bundle = 0;
     o->anneal_stages = 0;
     o->anneal_beta0 = 1.0;
+    o->scan = 0;
 }
 
 const char* surfmcmc_strerror(int code) {
@@ -758,6 +770,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     int lam = 0;
     if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
+    if (o.scan) lam = 32;
     if (n == 0) return SURFMCMC_OK;
     ctx->last_error.clear();
     DeviceGuard g(ctx->device);
@@ -770,6 +783,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
 
     SweepParams sp;
     init_chains(sp, Cn, R, id0);
+    sp.scan = o.scan;
     lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
@@ -825,7 +839,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     dp.n = n;
     dp.K = K;
     dp.R = R;
-    dp.samples = o.n_sweeps > o.burn_in ? (uint64_t)4 * R * (o.n_sweeps - o.burn_in) : 0;
+    dp.samples = o.n_sweeps > o.burn_in ? samples_per_sweep(o, L) * R * (o.n_sweeps - o.burn_in) : 0;
     dp.beta_bar = beta_bar;
     dp.chain_sum = chain_sum;
     dp.out_class = (int32_t*)b_cls.dev;
@@ -864,6 +878,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     int lam = 0;
     if (pick_lanes(L, o.lanes_per_bundle, &lam))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
+    if (o.scan) lam = 32;
     if (n == 0) return SURFMCMC_OK;
     ctx->last_error.clear();
     DeviceGuard g(ctx->device);
@@ -871,6 +886,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     const int K = 4, R = o.chains_per_class, Cn = K * R, N = n_beta;
     SweepParams sp;
     init_chains(sp, Cn, R, id0);
+    sp.scan = o.scan;
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
     const int W = n_words(L), nq = n_qubits(L);
@@ -899,7 +915,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
 
     if ((rc = copy_in(ctx, b_syn, s))) return rc;
     CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
-    const uint64_t samples = (uint64_t)4 * R * (o.n_sweeps - o.burn_in);
+    const uint64_t samples = samples_per_sweep(o, L) * R * (o.n_sweeps - o.burn_in);
     for (int j = 1; j < N; ++j) {
         // grid point j: beta_j = beta* j/(N-1), randomness keyed by seed + j
         const double bs = o.beta_scale * (double)j / (double)(N - 1);
@@ -1150,6 +1166,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
     int lam = 0;
     if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
+    if (o.scan) lam = 32;
     if (n == 0) return SURFMCMC_OK;
     ctx->last_error.clear();
     DeviceGuard g(ctx->device);
@@ -1222,6 +1239,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
         // sweeps [t, tk) of the active items, resumed from their state at t
         SweepParams sp;
         init_chains(sp, Cn, R, id0);
+        sp.scan = o.scan;
         sp.ids = t == 0 ? nullptr : (const uint32_t*)at(off_ids[cur]);
         const int lam_k = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n_act), sp.G);
         add_group(sp, L, n_act, 0, 0, 0, 0, lam_k);
@@ -1251,7 +1269,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
         dp.n = n_act;
         dp.K = K;
         dp.R = R;
-        dp.samples = tk > o.burn_in ? (uint64_t)4 * R * (tk - o.burn_in) : 0;
+        dp.samples = tk > o.burn_in ? samples_per_sweep(o, L) * R * (tk - o.burn_in) : 0;
         dp.beta_bar = beta_bar;
         dp.chain_sum = s_out;
         dp.out_class = tcls;

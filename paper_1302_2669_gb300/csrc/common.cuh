@@ -122,6 +122,8 @@ struct SweepParams {
     int bps, spb;              // bundles per syndrome (G == 32), syndromes per bundle (G < 32)
     uint32_t id0;
     const uint32_t* ids;       // per-syndrome ids (NULL: id0 + global index)
+    int scan;                  // 0: colour sweeps; 1: random scan (one random generator per step)
+    uint64_t T[5];             // acceptance thresholds T[d] = floor(r*^d 2^32) (random scan)
     int accept_all;            // r* == 1: every proposal accepted
     int reject_all;            // T[1] == 0: no uphill proposal accepted
     uint32_t qmodes;           // per quad of planes 4q..4q+3, 2 bits: 0 every threshold digit is 0,

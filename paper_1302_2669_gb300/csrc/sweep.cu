@@ -290,9 +290,38 @@ __host__ __device__ __forceinline__ int warp_aux_words(int bundles) {
     return 1 + kQueueCap * kQueueItem + bundles * (kMaxSlots + 1);
 }
 
+// Support of generator g in the syndrome order (sigma_x block row-major over
+// (i, j) at grid point (2i+1, 2j), then the sigma_z block at (2i, 2j+1)):
+// up, down, left, right neighbours, a missing one replaced by the dummy slot
+// (nq for sigma_x generators, nq + 1 for sigma_z).  Returns 0 for sigma_x
+// (flips the X plane), 1 for sigma_z.
+__device__ __forceinline__ int generator_support(int L, int g, int q[4]) {
+    const int nx = L * (L - 1), n = 2 * L - 1, nq = n_qubits(L);
+    int r, c, type;
+    if (g < nx) {
+        const int i = g / L;
+        r = 2 * i + 1;
+        c = 2 * (g - i * L);
+        type = 0;
+    } else {
+        const int h = g - nx, i = h / (L - 1);
+        r = 2 * i;
+        c = 2 * (h - i * (L - 1)) + 1;
+        type = 1;
+    }
+    const int dummy = nq + type, base = r * n + c;
+    q[0] = r > 0 ? (base - n) / 2 : dummy;
+    q[1] = r < n - 1 ? (base + n) / 2 : dummy;
+    q[2] = c > 0 ? (base - 1) / 2 : dummy;
+    q[3] = c < n - 1 ? (base + 1) / 2 : dummy;
+    return type;
+}
+
 // One unit: the bundles of group g handled by this block (warps x 32/LAM
 // bundles); every warp runs its bundles' chains from gd.t_begin to gd.t_end.
-template <int G, int LAM>
+// SCAN (with LAM = 32, one chain per lane): random-scan steps instead of
+// colour sweeps, on the same bit-sliced frames.
+template <int G, int LAM, bool SCAN>
 __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& gd, long long unit,
                                          uint32_t* smem, const ushort4* tab) {
     constexpr int B = 32 / LAM;                       // bundles per warp
@@ -410,6 +439,45 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
     uint32_t since_flush = 0;
     __syncwarp();
 
+    if constexpr (SCAN) {
+        static_assert(LAM == 32, "random scan runs one chain per lane");
+        // Sec. IV as written: each step draws one generator g = floor(w0
+        // n_stab / 2^32) and applies it when Delta n <= 0 or w1 < T[Delta n]
+        // (Philox counter (id, chain, t, step)); n is summed after every
+        // step.  Lane b owns bit b of the bundle's words and flips only it.
+        const int b = lane;
+        const bool mine = (valid >> b) & 1u;
+        const uint32_t bit = 1u << b;
+        const uint32_t my_sid = sid[G == 32 ? 0 : b / G];
+        const uint32_t chain = (uint32_t)chain_of(b);
+        const int ns = 2 * L * (L - 1);
+        int n = 0;
+        for (int q = 0; q < nq; ++q) n += (int)(((X[q] | Z[q]) >> b) & 1u);
+        uint64_t sum = 0;
+        for (uint32_t t = gd.t_begin; t < gd.t_end; ++t) {
+            const bool sample = t >= gd.burn_in;
+            for (int step = 0; step < ns; ++step) {
+                const uint4 r = philox10(make_uint4(my_sid, chain, t, (uint32_t)step), p.rk);
+                const int g = (int)__umulhi(r.x, (uint32_t)ns);
+                int q[4];
+                const int type = generator_support(L, g, q);
+                uint32_t* own = type == 0 ? X : Z;
+                const uint32_t* oth = type == 0 ? Z : X;
+                int dn = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (!((oth[q[k]] >> b) & 1u)) dn += ((own[q[k]] >> b) & 1u) ? -1 : 1;
+                if (mine && (dn <= 0 || (uint64_t)r.y < p.T[dn])) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) atomicXor(&own[q[k]], bit);
+                    n += dn;
+                }
+                if (sample) sum += (uint64_t)n;
+            }
+        }
+        if (mine && p.chain_sum) p.chain_sum[ci_of(b)] += sum;
+        __syncwarp();
+    } else
     for (uint32_t t = gd.t_begin; t < gd.t_end; ++t) {
 #pragma unroll 1
         for (int col = 0; col < 4; ++col) {
@@ -547,7 +615,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
 // fill its warps) first by its index, then from a queue counter, in the order
 // the host arranged (largest work first), and rebuilds the support table in
 // shared memory when the group's code size changes.
-template <int G, int LAM>
+template <int G, int LAM, bool SCAN>
 __global__ void __launch_bounds__(128, (G >= 16 ? 5 : 3)) sweep_kernel(const __grid_constant__ SweepParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ long long s_unit;
@@ -574,7 +642,7 @@ __global__ void __launch_bounds__(128, (G >= 16 ? 5 : 3)) sweep_kernel(const __g
             cur = g;
             __syncthreads();
         }
-        run_unit<G, LAM>(p, gd, u - gd.unit_base, smem, tab);
+        run_unit<G, LAM, SCAN>(p, gd, u - gd.unit_base, smem, tab);
         __syncthreads();
         if (!p.unit_counter) break;
     }
@@ -590,12 +658,12 @@ size_t sweep_smem_bytes(int nq, int nc, int lam) {
 long long sweep_units(long long n_bundles, int lam) { return (n_bundles + (long long)kWarps * (32 / lam) - 1) /
                                                                ((long long)kWarps * (32 / lam)); }
 
-template <int G, int LAM>
+template <int G, int LAM, bool SCAN = false>
 static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
     const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM);
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM, SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
@@ -608,25 +676,27 @@ static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM>, 32 * kWarps, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM, SCAN>, 32 * kWarps,
+                                                              smem);
         if (e != cudaSuccess) return e;
         const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
         if (blocks > resident) blocks = resident;
         e = cudaMemsetAsync(p.unit_counter, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return e;
     }
-    sweep_kernel<G, LAM><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
+    sweep_kernel<G, LAM, SCAN><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int G, int LAM>
+template <int G, int LAM, bool SCAN = false>
 static cudaError_t prepare_t(const SweepParams& p) {
     const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM);
-    return cudaFuncSetAttribute(sweep_kernel<G, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(sweep_kernel<G, LAM, SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <int G>
 static cudaError_t prepare_g(const SweepParams& p, int lam) {
+    if (p.scan) return lam == 32 ? prepare_t<G, 32, true>(p) : cudaErrorInvalidValue;
     switch (lam) {
         case 2: return prepare_t<G, 2>(p);
         case 4: return prepare_t<G, 4>(p);
@@ -650,6 +720,7 @@ cudaError_t prepare_sweep(const SweepParams& p, int lam) {
 
 template <int G>
 static cudaError_t launch_g(const SweepParams& p, int lam, cudaStream_t s) {
+    if (p.scan) return lam == 32 ? launch_t<G, 32, true>(p, s) : cudaErrorInvalidValue;
     switch (lam) {
         case 2: return launch_t<G, 2>(p, s);
         case 4: return launch_t<G, 4>(p, s);
