@@ -55,6 +55,11 @@ def lib():
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_gen_error.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_double, u8p, u8p]
         L.orc_gen_syndromes.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_double, u8p, i32p]
+        L.orc_gen_syndromes_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_double, C.c_int, u8p,
+                                              i32p]
+        L.orc_gen_error_flips.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_double, u8p, u8p]
+        L.orc_thresholds_noise.argtypes = [C.c_double, C.c_int, C.c_double, u64p, C.POINTER(C.c_double)]
+        L.orc_exact_histogram_noise.argtypes = [C.c_int, u8p, C.c_int, u64p]
         L.orc_pure_error.argtypes = [C.c_int, u8p, u8p, u8p]
         L.orc_start_frame.argtypes = [C.c_int, u8p, C.c_int, u8p, u8p]
         L.orc_thresholds.argtypes = [C.c_double, C.c_double, u64p, C.POINTER(C.c_double)]
@@ -67,14 +72,15 @@ def lib():
         L.orc_decide.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, u64p, u64p, f64p]
         L.orc_decode_one.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double,
                                      C.c_int, C.c_double, C.c_uint64, C.c_uint32, u8p, u64p, f64p, u64p, i32p, u8p,
-                                     u8p, C.c_void_p, C.c_int]
+                                     u8p, C.c_void_p, C.c_int, C.c_int]
         L.orc_anneal_scale.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
         L.orc_anneal_scale.restype = C.c_double
         L.orc_anneal_stage.argtypes = [C.c_uint32, C.c_uint32, C.c_int]
         L.orc_exact_histogram.argtypes = [C.c_int, u8p, u64p]
         L.orc_simpson_integral.argtypes = [C.c_int, C.c_int, f64p, C.c_double, f64p]
         L.orc_decode_ti.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double,
-                                    C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32, u8p, f64p, f64p, C.c_int]
+                                    C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32, u8p, f64p, f64p, C.c_int,
+                                    C.c_int]
         _lib = L
     return _lib
 
@@ -83,7 +89,7 @@ class _Run(C.Structure):
     _fields_ = [("L", C.c_int32), ("K", C.c_int32), ("R", C.c_int32), ("t_begin", C.c_uint32),
                 ("t_end", C.c_uint32), ("burn_in", C.c_uint32), ("p", C.c_double), ("beta_scale", C.c_double),
                 ("seed", C.c_uint64), ("id", C.c_uint32), ("anneal_stages", C.c_int32),
-                ("anneal_beta0", C.c_double), ("scan", C.c_int32)]
+                ("anneal_beta0", C.c_double), ("scan", C.c_int32), ("noise", C.c_int32)]
 
 
 def nq(L: int) -> int:
@@ -152,12 +158,19 @@ def gen_error(seed: int, ident: int, L: int, p: float):
     return ex, ez
 
 
-def gen_syndromes(seed: int, id0: int, n: int, L: int, p: float):
+def gen_syndromes(seed: int, id0: int, n: int, L: int, p: float, noise: int = 0):
     syn = np.zeros((n, nstab(L)), np.uint8)
     tc = np.zeros(n, np.int32)
     if n:
-        lib().orc_gen_syndromes(seed, id0, n, L, p, syn, tc)
+        lib().orc_gen_syndromes_noise(seed, id0, n, L, p, noise, syn, tc)
     return syn, tc
+
+
+def gen_error_flips(seed: int, ident: int, L: int, p: float):
+    ex = np.zeros(nq(L), np.uint8)
+    ez = np.zeros(nq(L), np.uint8)
+    lib().orc_gen_error_flips(seed, ident, L, p, ex, ez)
+    return ex, ez
 
 
 def pure_error(L: int, syn: np.ndarray):
@@ -174,10 +187,10 @@ def start_frame(L: int, syn: np.ndarray, k: int):
     return ex, ez, code0
 
 
-def thresholds(p: float, beta_scale: float = 1.0):
+def thresholds(p: float, beta_scale: float = 1.0, noise: int = 0):
     T = np.zeros(5, np.uint64)
     bb = C.c_double()
-    lib().orc_thresholds(p, beta_scale, T, C.byref(bb))
+    lib().orc_thresholds_noise(p, noise, beta_scale, T, C.byref(bb))
     return T, bb.value
 
 
@@ -206,7 +219,8 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
 
 
 def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_scale=1.0,
-               frames=None, chain_sum=None, trace=False, accepts=False, anneal_stages=0, anneal_beta0=1.0, scan=0):
+               frames=None, chain_sum=None, trace=False, accepts=False, anneal_stages=0, anneal_beta0=1.0, scan=0,
+               noise=0):
     """Run all K*R chains of one syndrome from sweep t_begin to t_end.  With
     frames=None the chains start from the start frames of `syn`; otherwise
     frames = (fx, fz) [C][nq] uint8 is the state at t_begin.  Returns a dict
@@ -220,7 +234,7 @@ def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_sca
     cn = np.zeros(Cn, np.int32)
     acc = np.zeros(Cn, np.uint64) if accepts else None
     tr = np.zeros(4 * (t_end - t_begin), np.int32) if trace else None
-    a = _Run(L, K, R, t_begin, t_end, burn_in, p, beta_scale, seed, ident, anneal_stages, anneal_beta0, scan)
+    a = _Run(L, K, R, t_begin, t_end, burn_in, p, beta_scale, seed, ident, anneal_stages, anneal_beta0, scan, noise)
     lib().orc_run_chains(C.addressof(a), np.ascontiguousarray(syn, np.uint8), 1 if frames is None else 0,
                          fx, fz, cs, cn.ctypes.data, None if acc is None else acc.ctypes.data,
                          None if tr is None else tr.ctypes.data)
@@ -241,7 +255,7 @@ def decide(K, R, n_sweeps, burn_in, beta_bar, chain_sum, samples_per_sweep=4):
 
 
 def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0, accepts=False,
-               anneal_stages=0, anneal_beta0=1.0, scan=0):
+               anneal_stages=0, anneal_beta0=1.0, scan=0, noise=0):
     """Decode one syndrome; returns a dict with the chosen class, per-class
     sums and log-ratios, per-chain sums, final n and final frames."""
     Cn = K * R
@@ -255,7 +269,7 @@ def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0
     acc = np.zeros(Cn, np.uint64) if accepts else None
     k = lib().orc_decode_one(L, p, K, R, n_sweeps, burn_in, beta_scale, anneal_stages, anneal_beta0, seed, ident,
                              np.ascontiguousarray(syn, np.uint8), S, lr, cs, cn, fx, fz,
-                             None if acc is None else acc.ctypes.data, scan)
+                             None if acc is None else acc.ctypes.data, scan, noise)
     out = {"cls": k, "class_sum": S, "log_ratio": lr, "chain_sum": cs, "chain_n": cn,
            "frames_x": fx, "frames_z": fz}
     if accepts:
@@ -263,19 +277,21 @@ def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0
     return out
 
 
-def exact_histogram(L: int, syn: np.ndarray) -> np.ndarray:
-    """[4][nq+1] counts of frames of weight n in each class (L <= 4)."""
-    h = np.zeros((4, nq(L) + 1), np.uint64)
-    rc = lib().orc_exact_histogram(L, np.ascontiguousarray(syn, np.uint8), h)
+def exact_histogram(L: int, syn: np.ndarray, noise: int = 0) -> np.ndarray:
+    """[4][nmax+1] counts of frames with n = w in each class (L <= 4); n is
+    the number of qubits in error (noise 0) or of bit plus phase flips
+    (noise 1, nmax = 2 nq)."""
+    h = np.zeros((4, (2 if noise else 1) * nq(L) + 1), np.uint64)
+    rc = lib().orc_exact_histogram_noise(L, np.ascontiguousarray(syn, np.uint8), noise, h)
     if rc != 0:
         raise ValueError("exact enumeration needs n_stab <= 30")
     return h
 
 
-def exact_class_stats(L: int, syn: np.ndarray, beta: float):
+def exact_class_stats(L: int, syn: np.ndarray, beta: float, noise: int = 0):
     """log Z_k(beta) (Eq. 3, up to the common factor) and <n>_{beta,k} (Eq. 4)
     from the exact histogram."""
-    h = exact_histogram(L, syn).astype(np.float64)
+    h = exact_histogram(L, syn, noise).astype(np.float64)
     n = np.arange(h.shape[1], dtype=np.float64)
     logw = -beta * n
     m = logw.max()
@@ -285,9 +301,9 @@ def exact_class_stats(L: int, syn: np.ndarray, beta: float):
 
 
 def _decode_worker(args):
-    (L, p, K, R, n_sweeps, seed, ident, syn, burn_in, beta_scale, anneal_stages, anneal_beta0, scan) = args
+    (L, p, K, R, n_sweeps, seed, ident, syn, burn_in, beta_scale, anneal_stages, anneal_beta0, scan, noise) = args
     d = decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=burn_in, beta_scale=beta_scale,
-                   anneal_stages=anneal_stages, anneal_beta0=anneal_beta0, scan=scan)
+                   anneal_stages=anneal_stages, anneal_beta0=anneal_beta0, scan=scan, noise=noise)
     return d
 
 
@@ -300,13 +316,13 @@ def anneal_stage(t, B, S):
 
 
 def decode_batch(L, p, K, R, n_sweeps, seed, ids, syns, burn_in=0, beta_scale=1.0, processes=None,
-                 anneal_stages=0, anneal_beta0=1.0, scan=0):
+                 anneal_stages=0, anneal_beta0=1.0, scan=0, noise=0):
     """decode_one over many syndromes, one process per syndrome block
     (multiprocessing with the spawn start method, safe after CUDA use).
     Returns the list of per-syndrome result dicts in input order."""
     import multiprocessing as mp
     jobs = [(L, p, K, R, n_sweeps, seed, int(i), np.ascontiguousarray(s, np.uint8), burn_in, beta_scale,
-             anneal_stages, anneal_beta0, scan) for i, s in zip(ids, syns)]
+             anneal_stages, anneal_beta0, scan, noise) for i, s in zip(ids, syns)]
     if processes == 1 or len(jobs) <= 1:
         return [_decode_worker(j) for j in jobs]
     with mp.get_context("spawn").Pool(processes or os.cpu_count()) as pool:
@@ -325,13 +341,13 @@ def simpson_integral(mean, beta_bar):
 
 
 def decode_ti(L, p, K, R, n_sweeps, seed, ident, syn, n_beta=21, burn_in=0, beta_scale=1.0, anneal_stages=0,
-              anneal_beta0=1.0, scan=0):
+              anneal_beta0=1.0, scan=0, noise=0):
     """Thermodynamic-integration decode (Eq. 6, Simpson over n_beta points):
     returns (class, log Z_k - max log Z, means [K][n_beta])."""
     mean = np.zeros((K, n_beta), np.float64)
     lz = np.zeros(K, np.float64)
     k = lib().orc_decode_ti(L, p, K, R, n_sweeps, burn_in, beta_scale, anneal_stages, anneal_beta0, n_beta, seed,
-                            ident, np.ascontiguousarray(syn, np.uint8), mean, lz, scan)
+                            ident, np.ascontiguousarray(syn, np.uint8), mean, lz, scan, noise)
     if k < 0:
         raise ValueError("bad TI arguments")
     return k, lz, mean

@@ -207,21 +207,46 @@ void orc_gen_error(uint64_t seed, uint32_t id, int L, double p, uint8_t* ex, uin
     }
 }
 
+/* Independent bit and phase flips (Sec. IV.B): sigma_x on each qubit with
+ * probability p and, independently, sigma_z with probability p.  tau =
+ * floor(p 2^32); qubit q uses words 2 (q mod 2) (bit flip) and 2 (q mod 2) + 1
+ * (phase flip) of the block with counter (id, q div 2, 1, 0). */
+void orc_gen_error_flips(uint64_t seed, uint32_t id, int L, double p, uint8_t* ex, uint8_t* ez)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u};
+    uint64_t tau = (uint64_t)floor(p * 4294967296.0);
+    uint32_t blk[4];
+    for (int q = 0; q < orc_nq(L); ++q) {
+        uint32_t ctr[4] = {id, (uint32_t)(q / 2), 1, 0};
+        orc_philox4x32_10(ctr, key, blk);
+        ex[q] = (uint8_t)((uint64_t)blk[2 * (q % 2)] < tau);
+        ez[q] = (uint8_t)((uint64_t)blk[2 * (q % 2) + 1] < tau);
+    }
+}
+
 /* n syndromes with ids id0 .. id0+n-1; true_class gets the class code of the
- * sampled error (the class a perfect decoder must return). */
-void orc_gen_syndromes(uint64_t seed, uint32_t id0, int64_t n, int L, double p,
-                       uint8_t* syn, int32_t* true_class)
+ * sampled error (the class a perfect decoder must return).  noise 0:
+ * depolarizing, 1: independent bit and phase flips. */
+void orc_gen_syndromes_noise(uint64_t seed, uint32_t id0, int64_t n, int L, double p, int noise,
+                             uint8_t* syn, int32_t* true_class)
 {
     int nq = orc_nq(L), ns = orc_nstab(L);
     uint8_t* ex = malloc(nq);
     uint8_t* ez = malloc(nq);
     for (int64_t i = 0; i < n; ++i) {
-        orc_gen_error(seed, id0 + (uint32_t)i, L, p, ex, ez);
+        if (noise) orc_gen_error_flips(seed, id0 + (uint32_t)i, L, p, ex, ez);
+        else orc_gen_error(seed, id0 + (uint32_t)i, L, p, ex, ez);
         orc_syndrome(L, ex, ez, syn + i * ns);
         if (true_class) true_class[i] = orc_class_code(L, ex, ez);
     }
     free(ex);
     free(ez);
+}
+
+void orc_gen_syndromes(uint64_t seed, uint32_t id0, int64_t n, int L, double p,
+                       uint8_t* syn, int32_t* true_class)
+{
+    orc_gen_syndromes_noise(seed, id0, n, L, p, 0, syn, true_class);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -273,9 +298,11 @@ int orc_start_frame(int L, const uint8_t* syn, int k, uint8_t* ex, uint8_t* ez)
 /* scaled temperature beta* = s beta_bar, r* = e^{-beta*}.                   */
 /* T[d] = floor(r*^d 2^32) for d = 1..4, r*^d by repeated multiplication.   */
 /* ------------------------------------------------------------------------ */
-void orc_thresholds(double p, double beta_scale, uint64_t* T, double* beta_bar)
+void orc_thresholds_noise(double p, int noise, double beta_scale, uint64_t* T, double* beta_bar)
 {
-    double r = (p / 3.0) / (1.0 - p);
+    /* depolarizing: r = (p/3)/(1-p) (Eq. 2); independent flips: each flip
+     * costs p/(1-p) (Sec. IV.B) */
+    double r = noise ? p / (1.0 - p) : (p / 3.0) / (1.0 - p);
     double rs = beta_scale == 1.0 ? r : exp(-beta_scale * -log(r));
     double rd = rs;
     T[0] = 0;
@@ -284,6 +311,11 @@ void orc_thresholds(double p, double beta_scale, uint64_t* T, double* beta_bar)
         rd = rd * rs;
     }
     if (beta_bar) *beta_bar = -log(r);
+}
+
+void orc_thresholds(double p, double beta_scale, uint64_t* T, double* beta_bar)
+{
+    orc_thresholds_noise(p, 0, beta_scale, T, beta_bar);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -359,10 +391,12 @@ int orc_chain_uniform_less(uint64_t seed, uint32_t s, uint32_t t, int col, int m
 /* The single-temperature algorithm (Sec. IV.A) for one syndrome.           */
 /* ------------------------------------------------------------------------ */
 
-static int weight(int nq, const uint8_t* ex, const uint8_t* ez)
+/* n of a frame: qubits carrying an error (depolarizing, Sec. IV), or bit
+ * flips plus phase flips (independent flips, Sec. IV.B). */
+static int weight(int nq, const uint8_t* ex, const uint8_t* ez, int noise)
 {
     int n = 0;
-    for (int q = 0; q < nq; ++q) n += ex[q] | ez[q];
+    for (int q = 0; q < nq; ++q) n += noise ? ex[q] + ez[q] : (ex[q] | ez[q]);
     return n;
 }
 
@@ -370,14 +404,14 @@ static int weight(int nq, const uint8_t* ex, const uint8_t* ez)
  * total number of errors n in the code would change if that stabilizer were
  * applied"); a sigma_x generator flips x on its support, a sigma_z generator
  * flips z.  Plain before/after count over the support. */
-static int delta_n(int type, int w, const int32_t* q, const uint8_t* ex, const uint8_t* ez)
+static int delta_n(int type, int w, const int32_t* q, const uint8_t* ex, const uint8_t* ez, int noise)
 {
     int before = 0, after = 0;
     for (int k = 0; k < w; ++k) {
         int x = ex[q[k]], z = ez[q[k]];
-        before += x | z;
+        before += noise ? x + z : (x | z);
         if (type == 0) x ^= 1; else z ^= 1;
-        after += x | z;
+        after += noise ? x + z : (x | z);
     }
     return after - before;
 }
@@ -391,6 +425,7 @@ typedef struct {
     int32_t anneal_stages;
     double anneal_beta0;
     int32_t scan;          /* 0: colour sweeps (Sec. V); 1: one random generator per step (Sec. IV) */
+    int32_t noise;         /* 0: depolarizing; 1: independent bit and phase flips */
 } orc_run_t;
 
 /* Start preparation (reading of Sec. IV: the chains should start near the
@@ -427,9 +462,10 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
 {
     int L = a->L, nq = orc_nq(L), C = a->K * a->R;
     uint64_t Tmain[5], Tst[64][5];
-    orc_thresholds(a->p, a->beta_scale, Tmain, NULL);
+    orc_thresholds_noise(a->p, a->noise, a->beta_scale, Tmain, NULL);
     for (int j = 0; j < a->anneal_stages && j < 64; ++j)
-        orc_thresholds(a->p, orc_anneal_scale(a->beta_scale, a->anneal_beta0, j, a->anneal_stages), Tst[j], NULL);
+        orc_thresholds_noise(a->p, a->noise, orc_anneal_scale(a->beta_scale, a->anneal_beta0, j, a->anneal_stages),
+                             Tst[j], NULL);
     int ncol[4], members[4][ORC_MAX_L * ORC_MAX_L];
     for (int col = 0; col < 4; ++col) {
         ncol[col] = orc_colour_count(L, col);
@@ -439,7 +475,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
         uint8_t* ex = frames_x + (size_t)c * nq;
         uint8_t* ez = frames_z + (size_t)c * nq;
         if (start_from_syndrome) orc_start_frame(L, syn, c / a->R, ex, ez);
-        int n = weight(nq, ex, ez);
+        int n = weight(nq, ex, ez, a->noise);
         for (uint32_t t = a->t_begin; t < a->t_end; ++t) {
             int stage = a->anneal_stages > 0 ? orc_anneal_stage(t, a->burn_in, a->anneal_stages) : -1;
             const uint64_t* T = stage >= 0 ? Tst[stage] : Tmain;
@@ -460,7 +496,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                     int type = orc_stab_pos(L, g, &r, &cc);
                     int32_t q[4];
                     int w = orc_stab_support(L, g, q);
-                    int dn = delta_n(type, w, q, ex, ez);
+                    int dn = delta_n(type, w, q, ex, ez, a->noise);
                     if (dn <= 0 || (uint64_t)blk[1] < T[dn]) {
                         for (int k = 0; k < w; ++k) {
                             if (type == 0) ex[q[k]] ^= 1; else ez[q[k]] ^= 1;
@@ -478,7 +514,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                 for (int m = 0; m < ncol[col]; ++m) {
                     int32_t q[4];
                     int w = orc_stab_support(L, members[col][m], q);
-                    int dn = delta_n(type, w, q, ex, ez);
+                    int dn = delta_n(type, w, q, ex, ez, a->noise);
                     /* Metropolis (Sec. IV): apply if Delta n <= 0, otherwise
                      * with probability e^{-beta* Delta n} = T[Delta n] / 2^32. */
                     int accept = dn <= 0 ||
@@ -532,10 +568,11 @@ int orc_decide(int K, int R, uint32_t n_sweeps, uint32_t burn_in, uint32_t sampl
 int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in,
                    double beta_scale, int anneal_stages, double anneal_beta0, uint64_t seed, uint32_t id,
                    const uint8_t* syn, uint64_t* class_sum, double* log_ratio, uint64_t* chain_sum,
-                   int32_t* chain_n, uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts, int scan)
+                   int32_t* chain_n, uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts, int scan,
+                   int noise)
 {
     int nq = orc_nq(L), C = K * R;
-    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0, scan};
+    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0, scan, noise};
     uint8_t* fx = frames_x ? frames_x : malloc((size_t)C * nq);
     uint8_t* fz = frames_z ? frames_z : malloc((size_t)C * nq);
     uint64_t* cs = chain_sum ? chain_sum : malloc(sizeof(uint64_t) * C);
@@ -544,7 +581,7 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
     orc_run_chains(&a, syn, 1, fx, fz, cs, chain_n, accepts, NULL);
     double beta_bar;
     uint64_t T[5];
-    orc_thresholds(p, 1.0, T, &beta_bar);
+    orc_thresholds_noise(p, noise, 1.0, T, &beta_bar);
     int k = orc_decide(K, R, n_sweeps, burn_in, scan ? (uint32_t)orc_nstab(L) : 4u, beta_bar, cs, class_sum,
                        log_ratio);
     if (!frames_x) free(fx);
@@ -560,7 +597,7 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
 /* Z_k(beta) = sum_n hist[k][n] e^{-beta n} and <n>_{beta,k} follows         */
 /* (Eq. 4).  Gray-code order: one generator is toggled per step.  L <= 4.   */
 /* ------------------------------------------------------------------------ */
-int orc_exact_histogram(int L, const uint8_t* syn, uint64_t* hist /* [4][nq+1] */)
+int orc_exact_histogram_noise(int L, const uint8_t* syn, int noise, uint64_t* hist /* [4][2 nq + 1] */)
 {
     int nq = orc_nq(L), ns = orc_nstab(L);
     if (ns > 30) return -1;
@@ -572,20 +609,26 @@ int orc_exact_histogram(int L, const uint8_t* syn, uint64_t* hist /* [4][nq+1] *
         wt[g] = orc_stab_support(L, g, sup + 4 * g);
     }
     uint8_t ex[64], ez[64];
+    int width = noise ? 2 * nq + 1 : nq + 1;
     for (int k = 0; k < 4; ++k) {
-        uint64_t* h = hist + (size_t)k * (nq + 1);
-        memset(h, 0, sizeof(uint64_t) * (nq + 1));
+        uint64_t* h = hist + (size_t)k * width;
+        memset(h, 0, sizeof(uint64_t) * width);
         orc_start_frame(L, syn, k, ex, ez);
-        h[weight(nq, ex, ez)] += 1;
+        h[weight(nq, ex, ez, noise)] += 1;
         for (uint64_t i = 1; i < ((uint64_t)1 << ns); ++i) {
             int g = __builtin_ctzll(i); /* generator toggled between Gray codes i-1 and i */
             for (int e = 0; e < wt[g]; ++e) {
                 if (type[g] == 0) ex[sup[4 * g + e]] ^= 1; else ez[sup[4 * g + e]] ^= 1;
             }
-            h[weight(nq, ex, ez)] += 1;
+            h[weight(nq, ex, ez, noise)] += 1;
         }
     }
     return 0;
+}
+
+int orc_exact_histogram(int L, const uint8_t* syn, uint64_t* hist /* [4][nq+1] */)
+{
+    return orc_exact_histogram_noise(L, syn, 0, hist);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -619,7 +662,7 @@ int orc_simpson_integral(int K, int N, const double* mean, double beta_bar, doub
  * log_z[k] = -(I_k - min_k I_k).  mean_out[k*N + j] receives the means. */
 int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_scale,
                   int anneal_stages, double anneal_beta0, int N, uint64_t seed, uint32_t id,
-                  const uint8_t* syn, double* mean_out, double* log_z, int scan)
+                  const uint8_t* syn, double* mean_out, double* log_z, int scan, int noise)
 {
     int nq = orc_nq(L), C = K * R;
     if (N < 3 || N % 2 == 0 || N > 129 || K > 64) return -1;
@@ -630,11 +673,13 @@ int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bur
     uint8_t* fz = malloc((size_t)C * nq);
     uint64_t* cs = malloc(sizeof(uint64_t) * C);
     double* mean = malloc(sizeof(double) * K * N);
-    for (int k = 0; k < K; ++k) mean[k * N] = 0.75 * (double)nq;
+    /* beta = 0: every frame of the class equally likely, so each qubit's x
+     * and z are uniform: <n> = 3/4 n_q (depolarizing), n_q (flips) */
+    for (int k = 0; k < K; ++k) mean[k * N] = noise ? (double)nq : 0.75 * (double)nq;
     for (int j = 1; j < N; ++j) {
         double bs = beta_scale * (double)j / (double)(N - 1);
         orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, bs, seed + (uint64_t)j, id, anneal_stages, anneal_beta0,
-                       scan};
+                       scan, noise};
         memset(cs, 0, sizeof(uint64_t) * C);
         orc_run_chains(&a, syn, 1, fx, fz, cs, NULL, NULL, NULL);
         for (int k = 0; k < K; ++k) {
@@ -645,7 +690,7 @@ int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bur
     }
     double beta_bar;
     uint64_t T[5];
-    orc_thresholds(p, 1.0, T, &beta_bar);
+    orc_thresholds_noise(p, noise, 1.0, T, &beta_bar);
     double I[64];
     orc_simpson_integral(K, N, mean, beta_scale * beta_bar, I);
     int best = 0;
