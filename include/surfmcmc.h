@@ -93,7 +93,13 @@ typedef struct surfmcmc_server surfmcmc_server;
  *                    and key (seed_lo, seed_hi); a sweep is n_stab steps and
  *                    n is summed after every step, so the sample count is
  *                    n_stab R (n_sweeps - burn_in) per class.  Needs
- *                    lanes_per_bundle 0 or 32. */
+ *                    lanes_per_bundle 0 or 32.
+ *   noise            0: depolarizing (Sec. IV), p in (0, 3/4]: n = number of
+ *                    qubits with an error, e^{-beta_bar} = (p/3)/(1-p).
+ *                    1: independent bit and phase flips (Sec. IV.B), p in
+ *                    (0, 1/2] the probability of each: n = bit flips + phase
+ *                    flips, e^{-beta_bar} = p/(1-p) (the paper finds beta* =
+ *                    0.85 beta_bar best, beta_scale = 0.85). */
 typedef struct {
     int32_t n_classes;
     int32_t chains_per_class;
@@ -104,6 +110,7 @@ typedef struct {
     int32_t anneal_stages;
     double anneal_beta0;
     int32_t scan;
+    int32_t noise;
 } surfmcmc_opts;
 
 /* Fills opts with K = 4, R = 4, 2000 sweeps, no burn-in, beta* = beta_bar,
@@ -136,6 +143,13 @@ const char* surfmcmc_last_error(const surfmcmc_ctx* ctx);
  * id0 + n > 2^32, NULL syndromes with n > 0. */
 int surfmcmc_gen_syndromes(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L,
                            double p, uint8_t* syndromes, int32_t* true_class, void* stream);
+/* As surfmcmc_gen_syndromes for the error model noise (0: depolarizing, p in
+ * [0, 3/4]; 1: independent bit and phase flips with probability p in [0, 1]
+ * each: sigma_x on qubit q iff word 2 (q mod 2) < floor(p 2^32), sigma_z iff
+ * word 2 (q mod 2) + 1 < floor(p 2^32), of the Philox block with counter
+ * (id, q div 2, 1, 0) and the same key). */
+int surfmcmc_gen_syndromes_noise(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
+                                 int32_t noise, uint8_t* syndromes, int32_t* true_class, void* stream);
 
 /* Start state (Sec. IV: one syndrome-compatible error per class, Sec. III's
  * boundary rule): the pure error joins every anyon to its nearer absorbing
@@ -329,7 +343,7 @@ int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches);
  *   Buffers: syndromes, out_class and (if not NULL) out_class_sum and
  *   out_log_ratio must be device memory of the current device; the layouts
  *   and results are those of surfmcmc_decode.  opts->lanes_per_bundle,
- *   opts->anneal_stages and opts->scan must be 0.  With stream == NULL the call returns after the results are
+ *   opts->anneal_stages, opts->scan and opts->noise must be 0.  With stream == NULL the call returns after the results are
  *   written; otherwise it is stream-ordered.
  *   Scratch: the call needs surfmcmc_noalloc_scratch_needed(n, L, R) bytes;
  *   a batch needing more than SURFMCMC_NOALLOC_SCRATCH_BYTES is rejected with

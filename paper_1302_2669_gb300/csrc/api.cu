@@ -135,10 +135,11 @@ int check_common(surfmcmc_ctx* ctx, int64_t n, int32_t L, uint32_t id0) {
     return SURFMCMC_OK;
 }
 
-// Eq. 2: r = (p/3)/(1-p) = e^{-beta_bar}; r* = e^{-beta_scale beta_bar};
-// T[d] = floor(r*^d 2^32), r*^d by repeated multiplication.
-void acceptance_table(double p, double beta_scale, uint64_t T[5], double* beta_bar) {
-    const double r = (p / 3.0) / (1.0 - p);
+// Eq. 2: r = (p/3)/(1-p) = e^{-beta_bar} (depolarizing), r = p/(1-p)
+// (independent bit and phase flips, Sec. IV.B); r* = e^{-beta_scale
+// beta_bar}; T[d] = floor(r*^d 2^32), r*^d by repeated multiplication.
+void acceptance_table(double p, int noise, double beta_scale, uint64_t T[5], double* beta_bar) {
+    const double r = noise ? p / (1.0 - p) : (p / 3.0) / (1.0 - p);
     const double rs = beta_scale == 1.0 ? r : exp(-beta_scale * -log(r));
     double rd = rs;
     T[0] = 0;
@@ -160,7 +161,7 @@ double anneal_scale(double beta_scale, double a0, int j, int S) {
 void set_temperature(SweepParams& sp, double p, double beta_scale) {
     uint64_t T[5];
     double beta_bar;
-    acceptance_table(p, beta_scale, T, &beta_bar);
+    acceptance_table(p, sp.noise, beta_scale, T, &beta_bar);
     for (int d = 0; d < 5; ++d) sp.T[d] = T[d];
     sp.accept_all = T[1] >= 4294967296ull;
     sp.reject_all = T[1] == 0;
@@ -230,14 +231,16 @@ int widen_lanes(const surfmcmc_ctx* ctx, int L, int requested, int lam, long lon
 }
 
 int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
-    if (!(p > 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside (0, 0.75]", p);
+    if (o.noise != 0 && o.noise != 1) return fail(ctx, SURFMCMC_EINVAL, "noise=%d must be 0 or 1", o.noise);
+    if (o.noise == 0 && !(p > 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside (0, 0.75]", p);
+    if (o.noise == 1 && !(p > 0.0 && p <= 0.5)) return fail(ctx, SURFMCMC_EINVAL, "flip p=%g outside (0, 0.5]", p);
     if (o.n_classes != 4) return fail(ctx, SURFMCMC_EINVAL, "n_classes must be 4 (planar code)");
     if (o.chains_per_class < 1 || 4 * o.chains_per_class > 1024)
         return fail(ctx, SURFMCMC_EINVAL, "chains_per_class=%d outside 1..256", o.chains_per_class);
     if (o.burn_in > o.n_sweeps) return fail(ctx, SURFMCMC_EINVAL, "burn_in > n_sweeps");
     if (!(o.beta_scale >= 0.0)) return fail(ctx, SURFMCMC_EINVAL, "beta_scale must be >= 0");
-    if (std::isinf(o.beta_scale) && p == 0.75)
-        return fail(ctx, SURFMCMC_EINVAL, "infinite beta_scale needs p < 0.75 (beta_bar = 0)");
+    if (std::isinf(o.beta_scale) && p == (o.noise ? 0.5 : 0.75))
+        return fail(ctx, SURFMCMC_EINVAL, "infinite beta_scale needs beta_bar > 0");
     if (o.anneal_stages < 0 || o.anneal_stages > 64)
         return fail(ctx, SURFMCMC_EINVAL, "anneal_stages=%d outside 0..64", o.anneal_stages);
     if (o.anneal_stages > 0 && ((uint32_t)o.anneal_stages > o.burn_in || !(o.anneal_beta0 > 0.0 && o.anneal_beta0 <= 1.0)))
@@ -455,6 +458,7 @@ int ragged_layout(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* sweeps, 
     const int Cn = 4 * o.chains_per_class;
     init_chains(lay.sp, Cn, o.chains_per_class, 0);
     lay.sp.scan = o.scan;
+    lay.sp.noise = o.noise;
     long long dst = 0, item = 0, e0w = 0, stw = 0;
     for (auto& g : lay.groups) {
         add_group(lay.sp, g.L, (long long)g.items.size(), item, e0w, 0, stw, lay.lam);
@@ -558,7 +562,7 @@ int ragged_enqueue(surfmcmc_ctx* ctx, const RaggedLayout& lay, long long n, cons
     if ((rc = run_segments(ctx, sp, plans, burn, p, lay.lam, io, s))) return rc;
     uint64_t T[5];
     double beta_bar;
-    acceptance_table(p, 1.0, T, &beta_bar);
+    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
     DecideParams dp;
     memset(&dp, 0, sizeof dp);
     dp.n = n;
@@ -631,6 +635,7 @@ void surfmcmc_default_opts(surfmcmc_opts* o) {
     o->anneal_stages = 0;
     o->anneal_beta0 = 1.0;
     o->scan = 0;
+    o->noise = 0;
 }
 
 const char* surfmcmc_strerror(int code) {
@@ -706,9 +711,16 @@ int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches) {
 
 int surfmcmc_gen_syndromes(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
                            uint8_t* syndromes, int32_t* true_class, void* stream) {
+    return surfmcmc_gen_syndromes_noise(ctx, seed, id0, n, L, p, 0, syndromes, true_class, stream);
+}
+
+int surfmcmc_gen_syndromes_noise(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
+                                 int32_t noise, uint8_t* syndromes, int32_t* true_class, void* stream) {
     int rc = check_common(ctx, n, L, id0);
     if (rc) return rc;
-    if (!(p >= 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside [0, 0.75]", p);
+    if (noise != 0 && noise != 1) return fail(ctx, SURFMCMC_EINVAL, "noise=%d must be 0 or 1", noise);
+    if (!(p >= 0.0 && p <= (noise ? 1.0 : 0.75)))
+        return fail(ctx, SURFMCMC_EINVAL, "p=%g outside [0, %g]", p, noise ? 1.0 : 0.75);
     if (n > 0 && !syndromes) return fail(ctx, SURFMCMC_EINVAL, "syndromes is NULL");
     if (n == 0) return SURFMCMC_OK;
     ctx->last_error.clear();
@@ -721,7 +733,7 @@ int surfmcmc_gen_syndromes(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64
     if ((rc = ensure_arena(ctx, cv.off))) return rc;
     bind(bs, ctx);
     bind(bt, ctx);
-    CK(launch_gen_syndromes(seed, id0, n, L, p, (uint8_t*)bs.dev, (int32_t*)bt.dev, s));
+    CK(launch_gen_syndromes(seed, id0, n, L, p, (uint8_t*)bs.dev, (int32_t*)bt.dev, s, noise));
     if ((rc = copy_out(ctx, bs, s)) || (rc = copy_out(ctx, bt, s))) return rc;
     if (!stream || bs.staged || bt.staged) CK(cudaStreamSynchronize(s));
     return SURFMCMC_OK;
@@ -784,6 +796,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     SweepParams sp;
     init_chains(sp, Cn, R, id0);
     sp.scan = o.scan;
+    sp.noise = o.noise;
     lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
@@ -833,7 +846,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
 
     uint64_t T[5];
     double beta_bar;
-    acceptance_table(p, 1.0, T, &beta_bar);
+    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
     DecideParams dp;
     memset(&dp, 0, sizeof dp);
     dp.n = n;
@@ -887,6 +900,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     SweepParams sp;
     init_chains(sp, Cn, R, id0);
     sp.scan = o.scan;
+    sp.noise = o.noise;
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
     const int W = n_words(L), nq = n_qubits(L);
@@ -932,9 +946,11 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     }
     uint64_t T[5];
     double beta_bar;
-    acceptance_table(p, 1.0, T, &beta_bar);
+    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
     const double h = (o.beta_scale * beta_bar) / (double)(N - 1);
-    CK(launch_ti_decide(n, K, N, 0.75 * (double)nq, h / 3.0, mean, (int32_t*)b_cls.dev, (double*)b_lz.dev, s));
+    // <n> at beta = 0: 3/4 n_q (depolarizing), n_q (independent flips)
+    const double mean0 = (o.noise ? 1.0 : 0.75) * (double)nq;
+    CK(launch_ti_decide(n, K, N, mean0, h / 3.0, mean, (int32_t*)b_cls.dev, (double*)b_lz.dev, s));
 
     bool any_host = false;
     for (Buf* b : {&b_cls, &b_lz}) {
@@ -1229,7 +1245,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
 
     uint64_t T[5];
     double beta_bar;
-    acceptance_table(p, 1.0, T, &beta_bar);
+    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
     long long n_act = n;
     uint32_t t = 0;
     int cur = 0;  // pair holding the active items' caller indices and ids
@@ -1240,6 +1256,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
         SweepParams sp;
         init_chains(sp, Cn, R, id0);
         sp.scan = o.scan;
+        sp.noise = o.noise;
         sp.ids = t == 0 ? nullptr : (const uint32_t*)at(off_ids[cur]);
         const int lam_k = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n_act), sp.G);
         add_group(sp, L, n_act, 0, 0, 0, 0, lam_k);

@@ -41,7 +41,7 @@ __device__ int class_code(int L, const uint32_t* ex, const uint32_t* ez) {
     return a + 2 * b;
 }
 
-__global__ void gen_syndromes_kernel(RoundKeys rk, uint32_t id0, long long n, int L, uint32_t tau1,
+__global__ void gen_syndromes_kernel(RoundKeys rk, uint32_t id0, long long n, int L, int noise, uint32_t tau1,
                                      uint32_t tau2, uint32_t tau3, uint8_t* syn, int32_t* true_class) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -49,6 +49,21 @@ __global__ void gen_syndromes_kernel(RoundKeys rk, uint32_t id0, long long n, in
     uint32_t ex[kMaxWords], ez[kMaxWords];
     for (int w = 0; w < W; ++w) ex[w] = ez[w] = 0;
     const uint32_t id = id0 + (uint32_t)i;
+    if (noise) {
+        // independent flips: qubit q uses words 2 (q mod 2) (bit flip) and
+        // 2 (q mod 2) + 1 (phase flip) of block (id, q div 2, 1, 0); tau1 =
+        // floor(p 2^32)
+        for (int q0 = 0; q0 < nq; q0 += 2) {
+            const uint4 b = philox10(make_uint4(id, (uint32_t)(q0 / 2), 1u, 0u), rk);
+            if (b.x < tau1) flipb(ex, q0);
+            if (b.y < tau1) flipb(ez, q0);
+            if (q0 + 1 < nq && b.z < tau1) flipb(ex, q0 + 1);
+            if (q0 + 1 < nq && b.w < tau1) flipb(ez, q0 + 1);
+        }
+        write_syndrome(L, ex, ez, syn + i * n_stabs(L));
+        if (true_class) true_class[i] = class_code(L, ex, ez);
+        return;
+    }
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const uint4 b = philox10(make_uint4(id, (uint32_t)(q0 / 4), 0u, 0u), rk);
         const uint32_t u[4] = {b.x, b.y, b.z, b.w};
@@ -314,13 +329,13 @@ cudaError_t launch_ti_decide(long long n, int K, int N, double mean0, double h3,
 }
 
 cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p, uint8_t* syn,
-                                 int32_t* true_class, cudaStream_t s) {
+                                 int32_t* true_class, cudaStream_t s, int noise) {
     if (n == 0) return cudaSuccess;
     RoundKeys rk;
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u, &rk);
-    const uint64_t tau = (uint64_t)floor((p / 3.0) * 4294967296.0);
+    const uint64_t tau = noise ? (uint64_t)floor(p * 4294967296.0) : (uint64_t)floor((p / 3.0) * 4294967296.0);
     const int bs = 128;
-    gen_syndromes_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rk, id0, n, L, (uint32_t)tau,
+    gen_syndromes_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rk, id0, n, L, noise, (uint32_t)tau,
                                                                       (uint32_t)(2 * tau), (uint32_t)(3 * tau),
                                                                       syn, true_class);
     return cudaGetLastError();

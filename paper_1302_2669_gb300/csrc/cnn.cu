@@ -47,7 +47,6 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kHid = 64;          // hidden channels
-constexpr int kCls = 4;           // classes
 constexpr int kOut = 2;           // flip logits per position (last layer)
 constexpr float kClip = 1e-6f;    // |M| <= 1 - kClip
 constexpr int kProdWarps = 4;     // gather warps

@@ -13,7 +13,7 @@ namespace surfmcmc {
 
 constexpr int kMaxL = 31;
 constexpr int kMaxWords = (2 * kMaxL * kMaxL - 2 * kMaxL + 1 + 31) / 32;  // 59
-constexpr int kCountBits = 11;  // n_q(31) = 1861 < 2^11
+constexpr int kCountBits = 12;  // n <= 2 n_q(31) = 3722 < 2^12 (independent flips)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The ten round keys are
@@ -123,6 +123,7 @@ struct SweepParams {
     uint32_t id0;
     const uint32_t* ids;       // per-syndrome ids (NULL: id0 + global index)
     int scan;                  // 0: colour sweeps; 1: random scan (one random generator per step)
+    int noise;                 // 0: depolarizing; 1: independent bit and phase flips
     uint64_t T[5];             // acceptance thresholds T[d] = floor(r*^d 2^32) (random scan)
     int accept_all;            // r* == 1: every proposal accepted
     int reject_all;            // T[1] == 0: no uphill proposal accepted
@@ -163,11 +164,13 @@ struct DecideParams {
 
 // Launchers (return cudaGetLastError() after the launch).
 cudaError_t launch_sweep(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
+cudaError_t launch_sweep_flips(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
+cudaError_t prepare_sweep_flips(const SweepParams& p, int lanes_per_bundle);
 cudaError_t prepare_sweep(const SweepParams& p, int lanes_per_bundle);
 size_t sweep_smem_bytes(int nq, int nc, int lanes_per_bundle);  // dynamic shared memory of a block
 long long sweep_units(long long n_bundles, int lanes_per_bundle);  // work units of a group
 cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p,
-                                 uint8_t* syn, int32_t* true_class, cudaStream_t s);
+                                 uint8_t* syn, int32_t* true_class, cudaStream_t s, int noise = 0);
 cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
                                 cudaStream_t s);
 cudaError_t launch_decide(const DecideParams& p, cudaStream_t s);

@@ -71,7 +71,7 @@ extern "C" int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int3
         return SURFMCMC_EINVAL;
     if (!(p > 0.0 && p <= 0.75) || o.n_classes != 4 || o.chains_per_class < 1 || 4 * o.chains_per_class > 1024 ||
         o.burn_in > o.n_sweeps || !(o.beta_scale >= 0.0) || (std::isinf(o.beta_scale) && p == 0.75) ||
-        o.anneal_stages != 0 || o.lanes_per_bundle != 0 || o.scan != 0)
+        o.anneal_stages != 0 || o.lanes_per_bundle != 0 || o.scan != 0 || o.noise != 0)
         return SURFMCMC_EINVAL;
     if (n == 0) return SURFMCMC_OK;
     // Device buffers only: staging host buffers would need memory of its own.
