@@ -49,9 +49,11 @@ typedef __nv_bfloat16 bf16;
 constexpr int kHid = 64;          // hidden channels
 constexpr int kOut = 2;           // flip logits per position (last layer)
 constexpr float kClip = 1e-6f;    // |M| <= 1 - kClip
-constexpr int kProdWarps = 4;     // gather warps
+constexpr int kConvProd = 8;      // gather warps of the conv kernel
+constexpr int kWgProd = 8;        // gather warps of the weight-gradient kernel
 constexpr int kEpiWarps = 4;      // accumulator-draining warps
-constexpr int kConvThreads = (kProdWarps + kEpiWarps + 1) * 32;
+constexpr int kConvThreads = (kConvProd + kEpiWarps + 1) * 32;
+constexpr int kWgThreads = (kWgProd + kEpiWarps + 1) * 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWaitTimeout = 1;   // error codes written to the device flag
 constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], kProdWarps * 32);
+            mbar_init(&full[s], kConvProd * 32);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -272,14 +274,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_async_smem();
-    if (warp == kProdWarps + kEpiWarps) tmem_alloc(&tmem_slot, NCOLS);
+    if (warp == kConvProd + kEpiWarps) tmem_alloc(&tmem_slot, NCOLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp < kProdWarps) {
+    if (warp < kConvProd) {
         // ---------------- gather: tap c of the tile's 128 positions --------
+        // warp w covers rows 32 (w mod 4) .. +31; the two halves of the
+        // producers split the 16-byte groups of a row.  All loads of a stage
+        // are issued before its slot is awaited and written.
+        const int rowblock = warp & 3, half = warp >> 2;
         uint32_t q = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
             long long rm[ROWS];
 #pragma unroll
             for (int i = 0; i < ROWS; ++i) {
-                const int r = warp * 32 + (lane & 7) + 8 * i;
+                const int r = rowblock * 32 + (lane & 7) + 8 * i;
                 const long long m = tile * 128 + r;
                 rm[i] = m;
                 if (m < M) {
@@ -302,48 +308,61 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
             }
             for (int c = 0; c < Sh::NCH; ++c, ++q) {
                 const uint32_t stage = q % S, use = q / S;
+                uint4 v[4];
+                if (CIN == 2) {
+                    // K = 18 (9 taps x 2 channels) padded to 32: group g
+                    // holds taps 4g..4g+3; this thread: rows 2 half, 2 half + 1
+                    const int g = lane >> 3;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int yk = half ? ry[2 + k] : ry[k], xk = half ? rx[2 + k] : rx[k];
+                        const long long mk = half ? rm[2 + k] : rm[k];
+                        uint32_t w[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int t = 4 * g + j;
+                            const int dy = t / 3 - 1, dx = t % 3 - 1;
+                            const int yy = yk + dy, xx = xk + dx;
+                            w[j] = 0;
+                            if (t < 9 && yy >= 0 && yy < L && xx >= 0 && xx < L)
+                                w[j] = __ldg(reinterpret_cast<const uint32_t*>(a.act) + mk + dy * L + dx);
+                        }
+                        v[k] = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+                    const int dy = c / 3 - 1, dx = c % 3 - 1;
+                    const int g = half * 4 + (lane >> 3);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int yy = ry[i] + dy, xx = rx[i] + dx;
+                        v[i] = make_uint4(0, 0, 0, 0);
+                        if (yy >= 0 && yy < L && xx >= 0 && xx < L)
+                            v[i] = __ldg(reinterpret_cast<const uint4*>(a.act + (rm[i] + dy * L + dx) * CIN) + g);
+                    }
+                }
                 if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) {
                     ok = false;
                     break;
                 }
                 uint8_t* st = sA + stage * Sh::STAGE_BYTES;
                 if (CIN == 2) {
-                    // K = 18 (9 taps x 2 channels) padded to 32: group g holds taps 4g..4g+3
-                    const int g = lane >> 3;
 #pragma unroll
-                    for (int i = 0; i < ROWS; ++i) {
-                        const int r = warp * 32 + (lane & 7) + 8 * i;
-                        uint32_t w[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int t = 4 * g + j;
-                            const int dy = t / 3 - 1, dx = t % 3 - 1;
-                            const int yy = ry[i] + dy, xx = rx[i] + dx;
-                            w[j] = 0;
-                            if (t < 9 && yy >= 0 && yy < L && xx >= 0 && xx < L)
-                                w[j] = __ldg(reinterpret_cast<const uint32_t*>(a.act) + rm[i] + dy * L + dx);
-                        }
-                        *reinterpret_cast<uint4*>(st + core_off(r, g, Sh::KGS)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    for (int k = 0; k < 2; ++k) {
+                        const int r = rowblock * 32 + (lane & 7) + 8 * (2 * half + k);
+                        *reinterpret_cast<uint4*>(st + core_off(r, lane >> 3, Sh::KGS)) = v[k];
                     }
                 } else {
-                    const int dy = c / 3 - 1, dx = c % 3 - 1;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int ri = i >> 1;
-                        const int r = warp * 32 + (lane & 7) + 8 * ri;
-                        const int g = (lane >> 3) + 4 * (i & 1);
-                        const int yy = ry[ri] + dy, xx = rx[ri] + dx;
-                        uint4 v = make_uint4(0, 0, 0, 0);
-                        if (yy >= 0 && yy < L && xx >= 0 && xx < L)
-                            v = __ldg(reinterpret_cast<const uint4*>(a.act + (rm[ri] + dy * L + dx) * CIN) + g);
-                        *reinterpret_cast<uint4*>(st + core_off(r, g, Sh::KGS)) = v;
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = rowblock * 32 + (lane & 7) + 8 * i;
+                        *reinterpret_cast<uint4*>(st + core_off(r, half * 4 + (lane >> 3), Sh::KGS)) = v[i];
                     }
                 }
                 fence_async_smem();
                 mbar_arrive(&full[stage]);
             }
         }
-    } else if (warp < kProdWarps + kEpiWarps) {
+    } else if (warp < kConvProd + kEpiWarps) {
         // ---------------- drain the accumulators ---------------------------
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
@@ -429,7 +448,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kProdWarps + kEpiWarps) tmem_dealloc(tmem, NCOLS);
+    if (warp == kConvProd + kEpiWarps) tmem_dealloc(tmem, NCOLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -452,8 +471,49 @@ constexpr int kWgAStage = 128 * 64 * 2;         // 128 rows x 64 positions
 constexpr int kWgBStage = 64 * 64 * 2;          // 64 channels x 64 positions
 constexpr size_t kWgSmem = (size_t)kWgS * (kWgAStage + kWgBStage) + 1024;
 
+// 8 x 8 transpose of 16-bit elements across each group of 8 lanes: lane i
+// holds row i (8 elements in 4 words, element j at half j%2 of word j/2) and
+// receives column i.  Three xor-butterfly stages (4, 2, 1 lanes apart) swap
+// the off-diagonal blocks of 4, 2 and 1 columns.
+__device__ __forceinline__ uint4 transpose8(uint4 v, int l8) {
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    {
+        const bool up = l8 & 4;
+        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, up ? w[0] : w[2], 4);
+        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, up ? w[1] : w[3], 4);
+        if (up) {
+            w[0] = r0;
+            w[1] = r1;
+        } else {
+            w[2] = r0;
+            w[3] = r1;
+        }
+    }
+    {
+        const bool up = l8 & 2;
+        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, up ? w[0] : w[1], 2);
+        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, up ? w[2] : w[3], 2);
+        if (up) {
+            w[0] = r0;
+            w[2] = r1;
+        } else {
+            w[1] = r0;
+            w[3] = r1;
+        }
+    }
+    {
+        const bool up = l8 & 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t r = __shfl_xor_sync(0xffffffffu, w[k], 1);
+            w[k] = up ? __byte_perm(r, w[k], 0x7632) : __byte_perm(w[k], r, 0x5410);
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 template <int CIN>
-__global__ void __launch_bounds__(kConvThreads, 2) wgrad_kernel(WgradArgs a) {
+__global__ void __launch_bounds__(kWgThreads, 2) wgrad_kernel(WgradArgs a) {
     constexpr uint32_t IDESC = idesc_bf16(128, 64);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -462,7 +522,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) wgrad_kernel(WgradArgs a) {
     __shared__ __align__(8) uint64_t full[kWgS], empty[kWgS], accf;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ int pos_yx[kProdWarps][64];
+    __shared__ int pos_yx[kWgProd][64];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
@@ -473,33 +533,31 @@ __global__ void __launch_bounds__(kConvThreads, 2) wgrad_kernel(WgradArgs a) {
 
     if (tid == 0) {
         for (int s = 0; s < kWgS; ++s) {
-            mbar_init(&full[s], kProdWarps * 32);
+            mbar_init(&full[s], kWgProd * 32);
             mbar_init(&empty[s], 1);
         }
         mbar_init(&accf, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kProdWarps + kEpiWarps) tmem_alloc(&tmem_slot, 64);
+    if (warp == kWgProd + kEpiWarps) tmem_alloc(&tmem_slot, 64);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp < kProdWarps) {
-        // row of A owned by this thread
-        const int R = mt * 128 + tid;
-        const int tap = R / CIN, ci = R - (R / CIN) * CIN;
-        const int kind = R < 9 * CIN ? 0 : (R == 9 * CIN ? 1 : 2);  // data, ones, zero
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const unsigned short* xs = reinterpret_cast<const unsigned short*>(a.x);
-        const unsigned short* zs = reinterpret_cast<const unsigned short*>(a.dz);
-        const int co = tid & 63, half = tid >> 6;
+    if (warp < kWgProd) {
+        // Blocks of 8 rows x 8 positions (one core matrix) per group of 8
+        // lanes: lane l8 loads position 8 pg + l8 (8 channels, 16 bytes), the
+        // group transposes, lane l8 stores row 8 rg + l8.
+        constexpr int kGroups = kWgProd * 4;
+        const int grp = tid >> 3, l8 = tid & 7;
+        const uint16_t* xs = reinterpret_cast<const uint16_t*>(a.x);
         uint32_t q = 0;
         for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
             const uint32_t stage = q % kWgS, use = q / kWgS;
             if (use > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)))
-                break;  // warp-uniform: the loop below has warp-wide syncs
+                break;  // warp-uniform: the loop below has warp-wide shuffles
             // positions of this chunk: (y << 8) | x, or -1 past the end
             for (int j = lane; j < 64; j += 32) {
                 const long long p = ch * 64 + j;
@@ -514,53 +572,73 @@ __global__ void __launch_bounds__(kConvThreads, 2) wgrad_kernel(WgradArgs a) {
             __syncwarp();
             uint8_t* stA = sA + stage * kWgAStage;
             uint8_t* stB = sB + stage * kWgBStage;
+            if constexpr (CIN == 64) {
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                uint32_t w[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    unsigned short e[2];
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const int j = g * 8 + h * 2 + k;
-                        const int yx = pos_yx[warp][j];
-                        unsigned short val = 0;
-                        if (yx >= 0) {
-                            if (kind == 0) {
-                                const int yy = (yx >> 8) + dy, xx = (yx & 255) + dx;
-                                if (yy >= 0 && yy < L && xx >= 0 && xx < L)
-                                    val = __ldg(xs + (ch * 64 + j + dy * L + dx) * CIN + ci);
-                            } else if (kind == 1) {
-                                val = 0x3F80;  // 1.0
-                            }
-                        }
-                        e[k] = val;
+                for (int pass = 0; pass < 128 / kGroups; ++pass) {
+                    const int b = grp + kGroups * pass, rg = b >> 3, pg = b & 7;
+                    const int R0 = mt * 128 + rg * 8, j = pg * 8 + l8;
+                    const int yx = pos_yx[warp][j];
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    if (R0 < 9 * CIN) {
+                        const int tap = R0 / CIN, ci0 = R0 % CIN;
+                        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                        const int yy = (yx >> 8) + dy, xx = (yx & 255) + dx;
+                        if (yx >= 0 && yy >= 0 && yy < L && xx >= 0 && xx < L)
+                            v = __ldg(reinterpret_cast<const uint4*>(a.x + (ch * 64 + j + dy * L + dx) * CIN + ci0));
+                    } else if (R0 == 9 * CIN && yx >= 0) {
+                        v.x = 0x3F80u;  // row 9 CIN: 1.0 (bias gradient)
                     }
-                    w[h] = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
+                    v = transpose8(v, l8);
+                    *reinterpret_cast<uint4*>(stA + core_off(rg * 8 + l8, pg, 8)) = v;
                 }
-                *reinterpret_cast<uint4*>(stA + core_off(tid, g, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                // 2 input channels: row R = tid holds tap R/2, channel R%2;
+                // row 18 is the row of ones, rows above are zero
+                const int R = tid;
+                for (int g = 0; g < 8 && tid < 128; ++g) {
+                    uint32_t w[4] = {0u, 0u, 0u, 0u};
+                    if (R <= 9 * CIN) {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            uint32_t e[2];
+#pragma unroll
+                            for (int k = 0; k < 2; ++k) {
+                                const int j = g * 8 + h * 2 + k;
+                                const int yx = pos_yx[warp][j];
+                                uint32_t val = 0;
+                                if (yx >= 0) {
+                                    if (R < 9 * CIN) {
+                                        const int tap = R / CIN, ci = R % CIN;
+                                        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                                        const int yy = (yx >> 8) + dy, xx = (yx & 255) + dx;
+                                        if (yy >= 0 && yy < L && xx >= 0 && xx < L)
+                                            val = __ldg(xs + (ch * 64 + j + dy * L + dx) * CIN + ci);
+                                    } else {
+                                        val = 0x3F80u;
+                                    }
+                                }
+                                e[k] = val;
+                            }
+                            w[h] = e[0] | (e[1] << 16);
+                        }
+                    }
+                    *reinterpret_cast<uint4*>(stA + core_off(R, g, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
             }
 #pragma unroll
-            for (int gg = 0; gg < 4; ++gg) {
-                const int g = half * 4 + gg;
-                uint32_t w[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    unsigned short e[2];
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const int j = g * 8 + h * 2 + k;
-                        e[k] = pos_yx[warp][j] >= 0 ? __ldg(zs + (ch * 64 + j) * 64 + co) : (unsigned short)0;
-                    }
-                    w[h] = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
-                }
-                *reinterpret_cast<uint4*>(stB + core_off(co, g, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            for (int pass = 0; pass < 64 / kGroups; ++pass) {
+                const int b = grp + kGroups * pass, cg = b >> 3, pg = b & 7;
+                const int j = pg * 8 + l8;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (pos_yx[warp][j] >= 0) v = __ldg(reinterpret_cast<const uint4*>(a.dz + (ch * 64 + j) * 64 + cg * 8));
+                v = transpose8(v, l8);
+                *reinterpret_cast<uint4*>(stB + core_off(cg * 8 + l8, pg, 8)) = v;
             }
             __syncwarp();  // pos_yx is rewritten by the next chunk
             fence_async_smem();
             mbar_arrive(&full[stage]);
         }
-    } else if (warp < kProdWarps + kEpiWarps) {
+    } else if (warp < kWgProd + kEpiWarps) {
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
         float* out = a.partial + (((long long)slice * gridDim.y + mt) * 128 + row) * 64;
@@ -606,7 +684,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) wgrad_kernel(WgradArgs a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kProdWarps + kEpiWarps) tmem_dealloc(tmem, 64);
+    if (warp == kWgProd + kEpiWarps) tmem_dealloc(tmem, 64);
 }
 
 // partial[s][R][co] summed over s in order -> flat gradient of layer l.
@@ -959,7 +1037,7 @@ cudaError_t launch_wgrad(const CnnNet* net, const bf16* x, const bf16* dz, long 
     a.M = M;
     a.L = net->L;
     a.err = net->err;
-    wgrad_kernel<CIN><<<dim3(slices, row_tiles), kConvThreads, kWgSmem, s>>>(a);
+    wgrad_kernel<CIN><<<dim3(slices, row_tiles), kWgThreads, kWgSmem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
     const int outs = (9 * CIN + 1) * 64;
