@@ -60,6 +60,12 @@ def lib():
         L.orc_gen_error_flips.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_double, u8p, u8p]
         L.orc_thresholds_noise.argtypes = [C.c_double, C.c_int, C.c_double, u64p, C.POINTER(C.c_double)]
         L.orc_exact_histogram_noise.argtypes = [C.c_int, u8p, C.c_int, u64p]
+        L.orc_exact_histogram_energy.argtypes = [C.c_int, u8p, C.c_int, C.c_void_p, C.c_int, u64p]
+        L.orc_rate_general.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int]
+        L.orc_rate_general.restype = C.c_double
+        L.orc_thresholds_r.argtypes = [C.c_double, C.c_double, C.c_int, u64p, C.POINTER(C.c_double)]
+        L.orc_gen_syndromes_pauli.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_double, C.c_double,
+                                              C.c_double, u8p, i32p]
         L.orc_pure_error.argtypes = [C.c_int, u8p, u8p, u8p]
         L.orc_start_frame.argtypes = [C.c_int, u8p, C.c_int, u8p, u8p]
         L.orc_thresholds.argtypes = [C.c_double, C.c_double, u64p, C.POINTER(C.c_double)]
@@ -72,7 +78,7 @@ def lib():
         L.orc_decide.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, u64p, u64p, f64p]
         L.orc_decode_one.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double,
                                      C.c_int, C.c_double, C.c_uint64, C.c_uint32, u8p, u64p, f64p, u64p, i32p, u8p,
-                                     u8p, C.c_void_p, C.c_int, C.c_int]
+                                     u8p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
         L.orc_anneal_scale.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
         L.orc_anneal_scale.restype = C.c_double
         L.orc_anneal_stage.argtypes = [C.c_uint32, C.c_uint32, C.c_int]
@@ -80,7 +86,7 @@ def lib():
         L.orc_simpson_integral.argtypes = [C.c_int, C.c_int, f64p, C.c_double, f64p]
         L.orc_decode_ti.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_double,
                                     C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32, u8p, f64p, f64p, C.c_int,
-                                    C.c_int]
+                                    C.c_int, C.c_void_p]
         _lib = L
     return _lib
 
@@ -89,7 +95,15 @@ class _Run(C.Structure):
     _fields_ = [("L", C.c_int32), ("K", C.c_int32), ("R", C.c_int32), ("t_begin", C.c_uint32),
                 ("t_end", C.c_uint32), ("burn_in", C.c_uint32), ("p", C.c_double), ("beta_scale", C.c_double),
                 ("seed", C.c_uint64), ("id", C.c_uint32), ("anneal_stages", C.c_int32),
-                ("anneal_beta0", C.c_double), ("scan", C.c_int32), ("noise", C.c_int32)]
+                ("anneal_beta0", C.c_double), ("scan", C.c_int32), ("noise", C.c_int32),
+                ("energy", C.c_int32 * 3)]
+
+
+def _energy(noise, energy):
+    """int32[3] array (eX, eY, eZ) for the general channel, else None."""
+    if noise != 2:
+        return None
+    return np.ascontiguousarray(energy if energy is not None else (1, 1, 1), np.int32)
 
 
 def nq(L: int) -> int:
@@ -187,6 +201,32 @@ def start_frame(L: int, syn: np.ndarray, k: int):
     return ex, ez, code0
 
 
+def rate_general(p: float, energy) -> float:
+    """r = e^{-beta_bar} of the general channel with energies (eX, eY, eZ)."""
+    return lib().orc_rate_general(p, int(energy[0]), int(energy[1]), int(energy[2]))
+
+
+def thresholds_r(r: float, beta_scale: float = 1.0, dmax: int = 32):
+    T = np.zeros(dmax + 1, np.uint64)
+    bb = C.c_double()
+    lib().orc_thresholds_r(r, beta_scale, dmax, T, C.byref(bb))
+    return T, bb.value
+
+
+def gen_syndromes_pauli(seed: int, id0: int, n: int, L: int, px: float, py: float, pz: float):
+    syn = np.zeros((n, nstab(L)), np.uint8)
+    tc = np.zeros(n, np.int32)
+    if n:
+        lib().orc_gen_syndromes_pauli(seed, id0, n, L, px, py, pz, syn, tc)
+    return syn, tc
+
+
+def pauli_probs(p: float, energy):
+    """(pX, pY, pZ) of the general channel of total error probability p."""
+    r = rate_general(p, energy)
+    return tuple((1.0 - p) * r ** int(e) for e in energy)
+
+
 def thresholds(p: float, beta_scale: float = 1.0, noise: int = 0):
     T = np.zeros(5, np.uint64)
     bb = C.c_double()
@@ -220,7 +260,7 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
 
 def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_scale=1.0,
                frames=None, chain_sum=None, trace=False, accepts=False, anneal_stages=0, anneal_beta0=1.0, scan=0,
-               noise=0):
+               noise=0, energy=None):
     """Run all K*R chains of one syndrome from sweep t_begin to t_end.  With
     frames=None the chains start from the start frames of `syn`; otherwise
     frames = (fx, fz) [C][nq] uint8 is the state at t_begin.  Returns a dict
@@ -234,7 +274,8 @@ def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_sca
     cn = np.zeros(Cn, np.int32)
     acc = np.zeros(Cn, np.uint64) if accepts else None
     tr = np.zeros(4 * (t_end - t_begin), np.int32) if trace else None
-    a = _Run(L, K, R, t_begin, t_end, burn_in, p, beta_scale, seed, ident, anneal_stages, anneal_beta0, scan, noise)
+    a = _Run(L, K, R, t_begin, t_end, burn_in, p, beta_scale, seed, ident, anneal_stages, anneal_beta0, scan, noise,
+             (C.c_int32 * 3)(*(energy if energy is not None else (1, 1, 1))))
     lib().orc_run_chains(C.addressof(a), np.ascontiguousarray(syn, np.uint8), 1 if frames is None else 0,
                          fx, fz, cs, cn.ctypes.data, None if acc is None else acc.ctypes.data,
                          None if tr is None else tr.ctypes.data)
@@ -255,7 +296,7 @@ def decide(K, R, n_sweeps, burn_in, beta_bar, chain_sum, samples_per_sweep=4):
 
 
 def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0, accepts=False,
-               anneal_stages=0, anneal_beta0=1.0, scan=0, noise=0):
+               anneal_stages=0, anneal_beta0=1.0, scan=0, noise=0, energy=None):
     """Decode one syndrome; returns a dict with the chosen class, per-class
     sums and log-ratios, per-chain sums, final n and final frames."""
     Cn = K * R
@@ -269,7 +310,8 @@ def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0
     acc = np.zeros(Cn, np.uint64) if accepts else None
     k = lib().orc_decode_one(L, p, K, R, n_sweeps, burn_in, beta_scale, anneal_stages, anneal_beta0, seed, ident,
                              np.ascontiguousarray(syn, np.uint8), S, lr, cs, cn, fx, fz,
-                             None if acc is None else acc.ctypes.data, scan, noise)
+                             None if acc is None else acc.ctypes.data, scan, noise,
+                             None if noise != 2 else _energy(noise, energy).ctypes.data)
     out = {"cls": k, "class_sum": S, "log_ratio": lr, "chain_sum": cs, "chain_n": cn,
            "frames_x": fx, "frames_z": fz}
     if accepts:
@@ -277,21 +319,24 @@ def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0
     return out
 
 
-def exact_histogram(L: int, syn: np.ndarray, noise: int = 0) -> np.ndarray:
+def exact_histogram(L: int, syn: np.ndarray, noise: int = 0, energy=None) -> np.ndarray:
     """[4][nmax+1] counts of frames with n = w in each class (L <= 4); n is
-    the number of qubits in error (noise 0) or of bit plus phase flips
-    (noise 1, nmax = 2 nq)."""
-    h = np.zeros((4, (2 if noise else 1) * nq(L) + 1), np.uint64)
-    rc = lib().orc_exact_histogram_noise(L, np.ascontiguousarray(syn, np.uint8), noise, h)
+    the number of qubits in error (noise 0), of bit plus phase flips (noise
+    1, nmax = 2 nq) or the summed Pauli energies (noise 2, nmax = max(e) nq)."""
+    emax = max(energy) if noise == 2 else (2 if noise else 1)
+    h = np.zeros((4, emax * nq(L) + 1), np.uint64)
+    e = _energy(noise, energy)
+    rc = lib().orc_exact_histogram_energy(L, np.ascontiguousarray(syn, np.uint8), noise,
+                                          None if e is None else e.ctypes.data, h.shape[1], h)
     if rc != 0:
         raise ValueError("exact enumeration needs n_stab <= 30")
     return h
 
 
-def exact_class_stats(L: int, syn: np.ndarray, beta: float, noise: int = 0):
+def exact_class_stats(L: int, syn: np.ndarray, beta: float, noise: int = 0, energy=None):
     """log Z_k(beta) (Eq. 3, up to the common factor) and <n>_{beta,k} (Eq. 4)
     from the exact histogram."""
-    h = exact_histogram(L, syn, noise).astype(np.float64)
+    h = exact_histogram(L, syn, noise, energy).astype(np.float64)
     n = np.arange(h.shape[1], dtype=np.float64)
     logw = -beta * n
     m = logw.max()
@@ -301,9 +346,10 @@ def exact_class_stats(L: int, syn: np.ndarray, beta: float, noise: int = 0):
 
 
 def _decode_worker(args):
-    (L, p, K, R, n_sweeps, seed, ident, syn, burn_in, beta_scale, anneal_stages, anneal_beta0, scan, noise) = args
+    (L, p, K, R, n_sweeps, seed, ident, syn, burn_in, beta_scale, anneal_stages, anneal_beta0, scan, noise,
+     energy) = args
     d = decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=burn_in, beta_scale=beta_scale,
-                   anneal_stages=anneal_stages, anneal_beta0=anneal_beta0, scan=scan, noise=noise)
+                   anneal_stages=anneal_stages, anneal_beta0=anneal_beta0, scan=scan, noise=noise, energy=energy)
     return d
 
 
@@ -316,13 +362,13 @@ def anneal_stage(t, B, S):
 
 
 def decode_batch(L, p, K, R, n_sweeps, seed, ids, syns, burn_in=0, beta_scale=1.0, processes=None,
-                 anneal_stages=0, anneal_beta0=1.0, scan=0, noise=0):
+                 anneal_stages=0, anneal_beta0=1.0, scan=0, noise=0, energy=None):
     """decode_one over many syndromes, one process per syndrome block
     (multiprocessing with the spawn start method, safe after CUDA use).
     Returns the list of per-syndrome result dicts in input order."""
     import multiprocessing as mp
     jobs = [(L, p, K, R, n_sweeps, seed, int(i), np.ascontiguousarray(s, np.uint8), burn_in, beta_scale,
-             anneal_stages, anneal_beta0, scan, noise) for i, s in zip(ids, syns)]
+             anneal_stages, anneal_beta0, scan, noise, energy) for i, s in zip(ids, syns)]
     if processes == 1 or len(jobs) <= 1:
         return [_decode_worker(j) for j in jobs]
     with mp.get_context("spawn").Pool(processes or os.cpu_count()) as pool:
@@ -341,13 +387,14 @@ def simpson_integral(mean, beta_bar):
 
 
 def decode_ti(L, p, K, R, n_sweeps, seed, ident, syn, n_beta=21, burn_in=0, beta_scale=1.0, anneal_stages=0,
-              anneal_beta0=1.0, scan=0, noise=0):
+              anneal_beta0=1.0, scan=0, noise=0, energy=None):
     """Thermodynamic-integration decode (Eq. 6, Simpson over n_beta points):
     returns (class, log Z_k - max log Z, means [K][n_beta])."""
     mean = np.zeros((K, n_beta), np.float64)
     lz = np.zeros(K, np.float64)
     k = lib().orc_decode_ti(L, p, K, R, n_sweeps, burn_in, beta_scale, anneal_stages, anneal_beta0, n_beta, seed,
-                            ident, np.ascontiguousarray(syn, np.uint8), mean, lz, scan, noise)
+                            ident, np.ascontiguousarray(syn, np.uint8), mean, lz, scan, noise,
+                            None if noise != 2 else _energy(noise, energy).ctypes.data)
     if k < 0:
         raise ValueError("bad TI arguments")
     return k, lz, mean

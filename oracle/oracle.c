@@ -318,6 +318,74 @@ void orc_thresholds(double p, double beta_scale, uint64_t* T, double* beta_bar)
     orc_thresholds_noise(p, 0, beta_scale, T, beta_bar);
 }
 
+/* General Pauli channel (Eq. 1 with integer energies, Sec. IV: the method
+ * "generalizes straightforwardly to arbitrary error models" of that form):
+ * p_X : p_Y : p_Z : p_I = r^eX : r^eY : r^eZ : 1 with e_P in 1..8 and total
+ * error probability p = p_X + p_Y + p_Z in (0, 3/4].  r in (0, 1] solves
+ * (1 - p)(r^eX + r^eY + r^eZ) = p; found by 100 halvings of [0, 1] (the
+ * left end moves when the value at the midpoint is below p), powers by
+ * repeated multiplication. */
+static double powi(double r, int e)
+{
+    double v = 1.0;
+    for (int i = 0; i < e; ++i) v *= r;
+    return v;
+}
+
+double orc_rate_general(double p, int eX, int eY, int eZ)
+{
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 100; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double f = (1.0 - p) * (powi(mid, eX) + powi(mid, eY) + powi(mid, eZ));
+        if (f < p) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* T[d] = floor(r*^d 2^32), d = 1..dmax, r* = r or exp(-beta_scale * -log r). */
+void orc_thresholds_r(double r, double beta_scale, int dmax, uint64_t* T, double* beta_bar)
+{
+    double rs = beta_scale == 1.0 ? r : exp(-beta_scale * -log(r));
+    double rd = rs;
+    T[0] = 0;
+    for (int d = 1; d <= dmax; ++d) {
+        T[d] = (uint64_t)floor(rd * 4294967296.0);
+        rd = rd * rs;
+    }
+    if (beta_bar) *beta_bar = -log(r);
+}
+
+/* Sampled errors of the general channel: u of qubit q is word q mod 4 of the
+ * block with counter (id, q div 4, 2, 0) (key as for the other models); X if
+ * u < floor(pX 2^32), Y if u < floor((pX + pY) 2^32), Z if u < floor((pX +
+ * pY + pZ) 2^32), else I. */
+void orc_gen_syndromes_pauli(uint64_t seed, uint32_t id0, int64_t n, int L, double px, double py, double pz,
+                             uint8_t* syn, int32_t* true_class)
+{
+    int nq = orc_nq(L), ns = orc_nstab(L);
+    uint8_t* ex = malloc(nq);
+    uint8_t* ez = malloc(nq);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u};
+    uint64_t t1 = (uint64_t)floor(px * 4294967296.0);
+    uint64_t t2 = (uint64_t)floor((px + py) * 4294967296.0);
+    uint64_t t3 = (uint64_t)floor((px + py + pz) * 4294967296.0);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t blk[4];
+        for (int q = 0; q < nq; ++q) {
+            uint32_t ctr[4] = {id0 + (uint32_t)i, (uint32_t)(q / 4), 2, 0};
+            orc_philox4x32_10(ctr, key, blk);
+            uint64_t u = blk[q % 4];
+            ex[q] = (uint8_t)(u < t2);
+            ez[q] = (uint8_t)(u >= t1 && u < t3);
+        }
+        orc_syndrome(L, ex, ez, syn + i * ns);
+        if (true_class) true_class[i] = orc_class_code(L, ex, ez);
+    }
+    free(ex);
+    free(ez);
+}
+
 /* ------------------------------------------------------------------------ */
 /* The uniform u of one chain for one proposal.                             */
 /*                                                                          */
@@ -391,12 +459,27 @@ int orc_chain_uniform_less(uint64_t seed, uint32_t s, uint32_t t, int col, int m
 /* The single-temperature algorithm (Sec. IV.A) for one syndrome.           */
 /* ------------------------------------------------------------------------ */
 
-/* n of a frame: qubits carrying an error (depolarizing, Sec. IV), or bit
- * flips plus phase flips (independent flips, Sec. IV.B). */
-static int weight(int nq, const uint8_t* ex, const uint8_t* ez, int noise)
+/* Energy of a qubit's Pauli, E[x + 2z] for I, X, Z, Y: depolarizing {0, 1,
+ * 1, 1} (n = qubits in error, Sec. IV), independent flips {0, 1, 1, 2}
+ * (n = bit flips + phase flips, Sec. IV.B), general {0, eX, eZ, eY}. */
+static void energy_table(int noise, const int32_t* e, int E[4])
+{
+    E[0] = 0;
+    if (noise == 2) {
+        E[1] = e[0];
+        E[2] = e[2];
+        E[3] = e[1];
+    } else {
+        E[1] = 1;
+        E[2] = 1;
+        E[3] = noise ? 2 : 1;
+    }
+}
+
+static int weight(int nq, const uint8_t* ex, const uint8_t* ez, const int E[4])
 {
     int n = 0;
-    for (int q = 0; q < nq; ++q) n += noise ? ex[q] + ez[q] : (ex[q] | ez[q]);
+    for (int q = 0; q < nq; ++q) n += E[ex[q] + 2 * ez[q]];
     return n;
 }
 
@@ -404,14 +487,14 @@ static int weight(int nq, const uint8_t* ex, const uint8_t* ez, int noise)
  * total number of errors n in the code would change if that stabilizer were
  * applied"); a sigma_x generator flips x on its support, a sigma_z generator
  * flips z.  Plain before/after count over the support. */
-static int delta_n(int type, int w, const int32_t* q, const uint8_t* ex, const uint8_t* ez, int noise)
+static int delta_n(int type, int w, const int32_t* q, const uint8_t* ex, const uint8_t* ez, const int E[4])
 {
     int before = 0, after = 0;
     for (int k = 0; k < w; ++k) {
         int x = ex[q[k]], z = ez[q[k]];
-        before += noise ? x + z : (x | z);
+        before += E[x + 2 * z];
         if (type == 0) x ^= 1; else z ^= 1;
-        after += noise ? x + z : (x | z);
+        after += E[x + 2 * z];
     }
     return after - before;
 }
@@ -425,8 +508,16 @@ typedef struct {
     int32_t anneal_stages;
     double anneal_beta0;
     int32_t scan;          /* 0: colour sweeps (Sec. V); 1: one random generator per step (Sec. IV) */
-    int32_t noise;         /* 0: depolarizing; 1: independent bit and phase flips */
+    int32_t noise;         /* 0: depolarizing; 1: independent bit and phase flips; 2: general */
+    int32_t energy[3];     /* eX, eY, eZ of the general channel (noise 2) */
 } orc_run_t;
+
+/* r = e^{-beta_bar} of a run's noise model. */
+static double run_rate(const orc_run_t* a)
+{
+    if (a->noise == 2) return orc_rate_general(a->p, a->energy[0], a->energy[1], a->energy[2]);
+    return a->noise ? a->p / (1.0 - a->p) : (a->p / 3.0) / (1.0 - a->p);
+}
 
 /* Start preparation (reading of Sec. IV: the chains should start near the
  * low-energy configurations of their class, because heating up from them is
@@ -461,11 +552,14 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                     int32_t* chain_n, uint64_t* accepts, int32_t* trace)
 {
     int L = a->L, nq = orc_nq(L), C = a->K * a->R;
-    uint64_t Tmain[5], Tst[64][5];
-    orc_thresholds_noise(a->p, a->noise, a->beta_scale, Tmain, NULL);
+    uint64_t Tmain[33], Tst[64][33];
+    int E[4];
+    energy_table(a->noise, a->energy, E);
+    double rate = run_rate(a);
+    orc_thresholds_r(rate, a->beta_scale, 32, Tmain, NULL);
     for (int j = 0; j < a->anneal_stages && j < 64; ++j)
-        orc_thresholds_noise(a->p, a->noise, orc_anneal_scale(a->beta_scale, a->anneal_beta0, j, a->anneal_stages),
-                             Tst[j], NULL);
+        orc_thresholds_r(rate, orc_anneal_scale(a->beta_scale, a->anneal_beta0, j, a->anneal_stages), 32, Tst[j],
+                         NULL);
     int ncol[4], members[4][ORC_MAX_L * ORC_MAX_L];
     for (int col = 0; col < 4; ++col) {
         ncol[col] = orc_colour_count(L, col);
@@ -475,7 +569,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
         uint8_t* ex = frames_x + (size_t)c * nq;
         uint8_t* ez = frames_z + (size_t)c * nq;
         if (start_from_syndrome) orc_start_frame(L, syn, c / a->R, ex, ez);
-        int n = weight(nq, ex, ez, a->noise);
+        int n = weight(nq, ex, ez, E);
         for (uint32_t t = a->t_begin; t < a->t_end; ++t) {
             int stage = a->anneal_stages > 0 ? orc_anneal_stage(t, a->burn_in, a->anneal_stages) : -1;
             const uint64_t* T = stage >= 0 ? Tst[stage] : Tmain;
@@ -496,7 +590,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                     int type = orc_stab_pos(L, g, &r, &cc);
                     int32_t q[4];
                     int w = orc_stab_support(L, g, q);
-                    int dn = delta_n(type, w, q, ex, ez, a->noise);
+                    int dn = delta_n(type, w, q, ex, ez, E);
                     if (dn <= 0 || (uint64_t)blk[1] < T[dn]) {
                         for (int k = 0; k < w; ++k) {
                             if (type == 0) ex[q[k]] ^= 1; else ez[q[k]] ^= 1;
@@ -514,7 +608,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                 for (int m = 0; m < ncol[col]; ++m) {
                     int32_t q[4];
                     int w = orc_stab_support(L, members[col][m], q);
-                    int dn = delta_n(type, w, q, ex, ez, a->noise);
+                    int dn = delta_n(type, w, q, ex, ez, E);
                     /* Metropolis (Sec. IV): apply if Delta n <= 0, otherwise
                      * with probability e^{-beta* Delta n} = T[Delta n] / 2^32. */
                     int accept = dn <= 0 ||
@@ -569,10 +663,13 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
                    double beta_scale, int anneal_stages, double anneal_beta0, uint64_t seed, uint32_t id,
                    const uint8_t* syn, uint64_t* class_sum, double* log_ratio, uint64_t* chain_sum,
                    int32_t* chain_n, uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts, int scan,
-                   int noise)
+                   int noise, const int32_t* energy)
 {
     int nq = orc_nq(L), C = K * R;
-    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0, scan, noise};
+    orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0, scan, noise,
+                   {1, 1, 1}};
+    if (noise == 2)
+        for (int i = 0; i < 3; ++i) a.energy[i] = energy[i];
     uint8_t* fx = frames_x ? frames_x : malloc((size_t)C * nq);
     uint8_t* fz = frames_z ? frames_z : malloc((size_t)C * nq);
     uint64_t* cs = chain_sum ? chain_sum : malloc(sizeof(uint64_t) * C);
@@ -581,7 +678,7 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
     orc_run_chains(&a, syn, 1, fx, fz, cs, chain_n, accepts, NULL);
     double beta_bar;
     uint64_t T[5];
-    orc_thresholds_noise(p, noise, 1.0, T, &beta_bar);
+    orc_thresholds_r(run_rate(&a), 1.0, 4, T, &beta_bar);
     int k = orc_decide(K, R, n_sweeps, burn_in, scan ? (uint32_t)orc_nstab(L) : 4u, beta_bar, cs, class_sum,
                        log_ratio);
     if (!frames_x) free(fx);
@@ -597,8 +694,11 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
 /* Z_k(beta) = sum_n hist[k][n] e^{-beta n} and <n>_{beta,k} follows         */
 /* (Eq. 4).  Gray-code order: one generator is toggled per step.  L <= 4.   */
 /* ------------------------------------------------------------------------ */
-int orc_exact_histogram_noise(int L, const uint8_t* syn, int noise, uint64_t* hist /* [4][2 nq + 1] */)
+int orc_exact_histogram_energy(int L, const uint8_t* syn, int noise, const int32_t* energy, int width,
+                               uint64_t* hist /* [4][width] */)
 {
+    int E[4];
+    energy_table(noise, energy, E);
     int nq = orc_nq(L), ns = orc_nstab(L);
     if (ns > 30) return -1;
     int32_t sup[4 * 64];
@@ -609,21 +709,25 @@ int orc_exact_histogram_noise(int L, const uint8_t* syn, int noise, uint64_t* hi
         wt[g] = orc_stab_support(L, g, sup + 4 * g);
     }
     uint8_t ex[64], ez[64];
-    int width = noise ? 2 * nq + 1 : nq + 1;
     for (int k = 0; k < 4; ++k) {
         uint64_t* h = hist + (size_t)k * width;
         memset(h, 0, sizeof(uint64_t) * width);
         orc_start_frame(L, syn, k, ex, ez);
-        h[weight(nq, ex, ez, noise)] += 1;
+        h[weight(nq, ex, ez, E)] += 1;
         for (uint64_t i = 1; i < ((uint64_t)1 << ns); ++i) {
             int g = __builtin_ctzll(i); /* generator toggled between Gray codes i-1 and i */
             for (int e = 0; e < wt[g]; ++e) {
                 if (type[g] == 0) ex[sup[4 * g + e]] ^= 1; else ez[sup[4 * g + e]] ^= 1;
             }
-            h[weight(nq, ex, ez, noise)] += 1;
+            h[weight(nq, ex, ez, E)] += 1;
         }
     }
     return 0;
+}
+
+int orc_exact_histogram_noise(int L, const uint8_t* syn, int noise, uint64_t* hist /* [4][2 nq + 1] */)
+{
+    return orc_exact_histogram_energy(L, syn, noise, NULL, noise ? 2 * orc_nq(L) + 1 : orc_nq(L) + 1, hist);
 }
 
 int orc_exact_histogram(int L, const uint8_t* syn, uint64_t* hist /* [4][nq+1] */)
@@ -662,7 +766,8 @@ int orc_simpson_integral(int K, int N, const double* mean, double beta_bar, doub
  * log_z[k] = -(I_k - min_k I_k).  mean_out[k*N + j] receives the means. */
 int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t burn_in, double beta_scale,
                   int anneal_stages, double anneal_beta0, int N, uint64_t seed, uint32_t id,
-                  const uint8_t* syn, double* mean_out, double* log_z, int scan, int noise)
+                  const uint8_t* syn, double* mean_out, double* log_z, int scan, int noise,
+                  const int32_t* energy)
 {
     int nq = orc_nq(L), C = K * R;
     if (N < 3 || N % 2 == 0 || N > 129 || K > 64) return -1;
@@ -675,11 +780,15 @@ int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bur
     double* mean = malloc(sizeof(double) * K * N);
     /* beta = 0: every frame of the class equally likely, so each qubit's x
      * and z are uniform: <n> = 3/4 n_q (depolarizing), n_q (flips) */
-    for (int k = 0; k < K; ++k) mean[k * N] = noise ? (double)nq : 0.75 * (double)nq;
+    int E[4];
+    energy_table(noise, energy, E);
+    for (int k = 0; k < K; ++k) mean[k * N] = (double)nq * (double)(E[1] + E[2] + E[3]) / 4.0;
     for (int j = 1; j < N; ++j) {
         double bs = beta_scale * (double)j / (double)(N - 1);
         orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, bs, seed + (uint64_t)j, id, anneal_stages, anneal_beta0,
-                       scan, noise};
+                       scan, noise, {1, 1, 1}};
+        if (noise == 2)
+            for (int i = 0; i < 3; ++i) a.energy[i] = energy[i];
         memset(cs, 0, sizeof(uint64_t) * C);
         orc_run_chains(&a, syn, 1, fx, fz, cs, NULL, NULL, NULL);
         for (int k = 0; k < K; ++k) {
@@ -690,7 +799,10 @@ int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bur
     }
     double beta_bar;
     uint64_t T[5];
-    orc_thresholds_noise(p, noise, 1.0, T, &beta_bar);
+    orc_run_t a0 = {L, K, R, 0, 0, 0, p, 1.0, 0, 0, 0, 1.0, scan, noise, {1, 1, 1}};
+    if (noise == 2)
+        for (int i = 0; i < 3; ++i) a0.energy[i] = energy[i];
+    orc_thresholds_r(run_rate(&a0), 1.0, 4, T, &beta_bar);
     double I[64];
     orc_simpson_integral(K, N, mean, beta_scale * beta_bar, I);
     int best = 0;
