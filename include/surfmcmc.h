@@ -99,7 +99,16 @@ typedef struct surfmcmc_server surfmcmc_server;
  *                    1: independent bit and phase flips (Sec. IV.B), p in
  *                    (0, 1/2] the probability of each: n = bit flips + phase
  *                    flips, e^{-beta_bar} = p/(1-p) (the paper finds beta* =
- *                    0.85 beta_bar best, beta_scale = 0.85). */
+ *                    0.85 beta_bar best, beta_scale = 0.85).
+ *                    2: general Pauli channel (Eq. 1) with integer energies
+ *                    pauli_energy = (eX, eY, eZ) in 1..8: p_X : p_Y : p_Z :
+ *                    p_I = r^eX : r^eY : r^eZ : 1, p in (0, 3/4] the total
+ *                    error probability, r = e^{-beta_bar} the root of
+ *                    (1 - p)(r^eX + r^eY + r^eZ) = p after 100 halvings of
+ *                    [0, 1]; n = the summed energies of the qubits' Paulis.
+ *                    Needs scan = 1 (the sweep kernels are specialised to
+ *                    the two models above).
+ *   pauli_energy     (eX, eY, eZ) of noise 2; ignored otherwise. */
 typedef struct {
     int32_t n_classes;
     int32_t chains_per_class;
@@ -111,6 +120,7 @@ typedef struct {
     double anneal_beta0;
     int32_t scan;
     int32_t noise;
+    int32_t pauli_energy[3];
 } surfmcmc_opts;
 
 /* Fills opts with K = 4, R = 4, 2000 sweeps, no burn-in, beta* = beta_bar,
@@ -150,6 +160,14 @@ int surfmcmc_gen_syndromes(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64
  * (id, q div 2, 1, 0) and the same key). */
 int surfmcmc_gen_syndromes_noise(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
                                  int32_t noise, uint8_t* syndromes, int32_t* true_class, void* stream);
+
+/* Errors of a general Pauli channel with probabilities pX, pY, pZ (>= 0,
+ * sum <= 3/4): u = word q mod 4 of the Philox block with counter (id, q div
+ * 4, 2, 0) (same key); X if u < floor(pX 2^32), Y if u < floor((pX + pY)
+ * 2^32), Z if u < floor((pX + pY + pZ) 2^32), else I.  Outputs as for
+ * surfmcmc_gen_syndromes. */
+int surfmcmc_gen_syndromes_pauli(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double px,
+                                 double py, double pz, uint8_t* syndromes, int32_t* true_class, void* stream);
 
 /* Start state (Sec. IV: one syndrome-compatible error per class, Sec. III's
  * boundary rule): the pure error joins every anyon to its nearer absorbing

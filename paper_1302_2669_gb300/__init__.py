@@ -36,7 +36,7 @@ class _Opts(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("chains_per_class", C.c_int32), ("n_sweeps", C.c_uint32),
                 ("burn_in", C.c_uint32), ("beta_scale", C.c_double), ("lanes_per_bundle", C.c_int32),
                 ("anneal_stages", C.c_int32), ("anneal_beta0", C.c_double), ("scan", C.c_int32),
-                ("noise", C.c_int32)]
+                ("noise", C.c_int32), ("pauli_energy", C.c_int32 * 3)]
 
 
 class _ServerOpts(C.Structure):
@@ -57,14 +57,17 @@ class Opts:
     anneal_beta0: float = 1.0
     scan: int = 0
     noise: int = 0
+    pauli_energy: tuple = (1, 1, 1)
 
     def c(self) -> _Opts:
         return _Opts(self.n_classes, self.chains_per_class, self.n_sweeps, self.burn_in, self.beta_scale,
-                     self.lanes_per_bundle, self.anneal_stages, self.anneal_beta0, self.scan, self.noise)
+                     self.lanes_per_bundle, self.anneal_stages, self.anneal_beta0, self.scan, self.noise,
+                     (C.c_int32 * 3)(*self.pauli_energy))
 
 
 EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surfmcmc_strerror",
-           "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_gen_syndromes_noise", "surfmcmc_start_frames", "surfmcmc_decode",
+           "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_gen_syndromes_noise",
+           "surfmcmc_gen_syndromes_pauli", "surfmcmc_start_frames", "surfmcmc_decode",
            "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time", "surfmcmc_noalloc_scratch_needed",
            "surfmcmc_decode_noalloc", "surfmcmc_decode_ti", "surfmcmc_decode_ragged", "surfmcmc_ragged_plan_create",
            "surfmcmc_plan_launch", "surfmcmc_plan_destroy", "surfmcmc_autotune", "surfmcmc_server_default_opts",
@@ -95,6 +98,7 @@ def lib():
         L.surfmcmc_last_error.restype = C.c_char_p
         L.surfmcmc_gen_syndromes.argtypes = [vp, u64, u32, i64, i32, dbl, vp, vp, vp]
         L.surfmcmc_gen_syndromes_noise.argtypes = [vp, u64, u32, i64, i32, dbl, i32, vp, vp, vp]
+        L.surfmcmc_gen_syndromes_pauli.argtypes = [vp, u64, u32, i64, i32, dbl, dbl, dbl, vp, vp, vp]
         L.surfmcmc_start_frames.argtypes = [vp, vp, i64, i32, vp, vp, vp]
         L.surfmcmc_decode.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
         L.surfmcmc_decode_ex.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, u32, vp, vp, vp, vp,
@@ -220,6 +224,18 @@ class Context:
             true_class = _empty(like, (n,), np.int32)
         st = stream if stream is not None else _stream_of(syndromes)
         self._check(lib().surfmcmc_gen_syndromes_noise(self._h, seed, id0, n, L, p, noise, _ptr(syndromes),
+                                                       _ptr(true_class), st))
+        return syndromes, true_class
+
+    def gen_syndromes_pauli(self, seed, id0, n, L, px, py, pz, like=None, syndromes=None, true_class=None,
+                            stream=None):
+        """surfmcmc_gen_syndromes_pauli: errors of a general Pauli channel."""
+        if syndromes is None:
+            syndromes = _empty(like, (n, n_stabs(L)), np.uint8)
+        if true_class is None:
+            true_class = _empty(like, (n,), np.int32)
+        st = stream if stream is not None else _stream_of(syndromes)
+        self._check(lib().surfmcmc_gen_syndromes_pauli(self._h, seed, id0, n, L, px, py, pz, _ptr(syndromes),
                                                        _ptr(true_class), st))
         return syndromes, true_class
 

@@ -135,15 +135,51 @@ int check_common(surfmcmc_ctx* ctx, int64_t n, int32_t L, uint32_t id0) {
     return SURFMCMC_OK;
 }
 
-// Eq. 2: r = (p/3)/(1-p) = e^{-beta_bar} (depolarizing), r = p/(1-p)
-// (independent bit and phase flips, Sec. IV.B); r* = e^{-beta_scale
-// beta_bar}; T[d] = floor(r*^d 2^32), r*^d by repeated multiplication.
-void acceptance_table(double p, int noise, double beta_scale, uint64_t T[5], double* beta_bar) {
-    const double r = noise ? p / (1.0 - p) : (p / 3.0) / (1.0 - p);
+// Energy of a qubit's Pauli, index x + 2z (I, X, Z, Y), of a noise model:
+// depolarizing {0, 1, 1, 1} (n = qubits in error, Sec. IV), independent
+// flips {0, 1, 1, 2} (Sec. IV.B), general channel {0, eX, eZ, eY}.
+void energy_table(const surfmcmc_opts& o, int E[4]) {
+    E[0] = 0;
+    if (o.noise == 2) {
+        E[1] = o.pauli_energy[0];
+        E[2] = o.pauli_energy[2];
+        E[3] = o.pauli_energy[1];
+    } else {
+        E[1] = 1;
+        E[2] = 1;
+        E[3] = o.noise ? 2 : 1;
+    }
+}
+
+double powi(double r, int e) {
+    double v = 1.0;
+    for (int i = 0; i < e; ++i) v *= r;
+    return v;
+}
+
+// r = e^{-beta_bar}: (p/3)/(1-p) (Eq. 2, depolarizing), p/(1-p)
+// (independent flips), or for the general channel the root r in (0, 1] of
+// (1 - p)(r^eX + r^eY + r^eZ) = p after 100 halvings of [0, 1] (the left end
+// moves when the value at the midpoint is below p).
+double noise_rate(double p, int noise, const int E[4]) {
+    if (noise == 0) return (p / 3.0) / (1.0 - p);
+    if (noise == 1) return p / (1.0 - p);
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 100; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const double f = (1.0 - p) * (powi(mid, E[1]) + powi(mid, E[3]) + powi(mid, E[2]));
+        if (f < p) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// r* = e^{-beta_scale beta_bar}; T[d] = floor(r*^d 2^32), d = 1..32, r*^d by
+// repeated multiplication.
+void acceptance_table(double r, double beta_scale, uint64_t T[33], double* beta_bar) {
     const double rs = beta_scale == 1.0 ? r : exp(-beta_scale * -log(r));
     double rd = rs;
     T[0] = 0;
-    for (int d = 1; d <= 4; ++d) {
+    for (int d = 1; d <= 32; ++d) {
         T[d] = (uint64_t)floor(rd * 4294967296.0);
         rd = rd * rs;
     }
@@ -159,10 +195,10 @@ double anneal_scale(double beta_scale, double a0, int j, int S) {
 // number of leading all-zero digit planes, and per plane k the algebraic
 // normal form of d-1 -> bit (31-k) of T[d].
 void set_temperature(SweepParams& sp, double p, double beta_scale) {
-    uint64_t T[5];
+    uint64_t T[33];
     double beta_bar;
-    acceptance_table(p, sp.noise, beta_scale, T, &beta_bar);
-    for (int d = 0; d < 5; ++d) sp.T[d] = T[d];
+    acceptance_table(noise_rate(p, sp.noise, sp.energy), beta_scale, T, &beta_bar);
+    for (int d = 0; d < 33; ++d) sp.T[d] = T[d];
     sp.accept_all = T[1] >= 4294967296ull;
     sp.reject_all = T[1] == 0;
     sp.qmodes = 0;
@@ -231,15 +267,21 @@ int widen_lanes(const surfmcmc_ctx* ctx, int L, int requested, int lam, long lon
 }
 
 int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
-    if (o.noise != 0 && o.noise != 1) return fail(ctx, SURFMCMC_EINVAL, "noise=%d must be 0 or 1", o.noise);
-    if (o.noise == 0 && !(p > 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside (0, 0.75]", p);
+    if (o.noise < 0 || o.noise > 2) return fail(ctx, SURFMCMC_EINVAL, "noise=%d must be 0, 1 or 2", o.noise);
+    if (o.noise != 1 && !(p > 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside (0, 0.75]", p);
+    if (o.noise == 2) {
+        for (int i = 0; i < 3; ++i)
+            if (o.pauli_energy[i] < 1 || o.pauli_energy[i] > 8)
+                return fail(ctx, SURFMCMC_EINVAL, "pauli_energy[%d]=%d outside 1..8", i, o.pauli_energy[i]);
+        if (o.scan != 1) return fail(ctx, SURFMCMC_EINVAL, "the general Pauli channel runs in random scan (scan=1)");
+    }
     if (o.noise == 1 && !(p > 0.0 && p <= 0.5)) return fail(ctx, SURFMCMC_EINVAL, "flip p=%g outside (0, 0.5]", p);
     if (o.n_classes != 4) return fail(ctx, SURFMCMC_EINVAL, "n_classes must be 4 (planar code)");
     if (o.chains_per_class < 1 || 4 * o.chains_per_class > 1024)
         return fail(ctx, SURFMCMC_EINVAL, "chains_per_class=%d outside 1..256", o.chains_per_class);
     if (o.burn_in > o.n_sweeps) return fail(ctx, SURFMCMC_EINVAL, "burn_in > n_sweeps");
     if (!(o.beta_scale >= 0.0)) return fail(ctx, SURFMCMC_EINVAL, "beta_scale must be >= 0");
-    if (std::isinf(o.beta_scale) && p == (o.noise ? 0.5 : 0.75))
+    if (std::isinf(o.beta_scale) && p == (o.noise == 1 ? 0.5 : 0.75))
         return fail(ctx, SURFMCMC_EINVAL, "infinite beta_scale needs beta_bar > 0");
     if (o.anneal_stages < 0 || o.anneal_stages > 64)
         return fail(ctx, SURFMCMC_EINVAL, "anneal_stages=%d outside 0..64", o.anneal_stages);
@@ -459,6 +501,7 @@ int ragged_layout(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* sweeps, 
     init_chains(lay.sp, Cn, o.chains_per_class, 0);
     lay.sp.scan = o.scan;
     lay.sp.noise = o.noise;
+    energy_table(o, lay.sp.energy);
     long long dst = 0, item = 0, e0w = 0, stw = 0;
     for (auto& g : lay.groups) {
         add_group(lay.sp, g.L, (long long)g.items.size(), item, e0w, 0, stw, lay.lam);
@@ -560,9 +603,11 @@ int ragged_enqueue(surfmcmc_ctx* ctx, const RaggedLayout& lay, long long n, cons
     io.state = rs.state;
     io.unit_counter = rs.ctr;
     if ((rc = run_segments(ctx, sp, plans, burn, p, lay.lam, io, s))) return rc;
-    uint64_t T[5];
+    uint64_t T[33];
     double beta_bar;
-    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
+    int Eo[4];
+    energy_table(o, Eo);
+    acceptance_table(noise_rate(p, o.noise, Eo), 1.0, T, &beta_bar);
     DecideParams dp;
     memset(&dp, 0, sizeof dp);
     dp.n = n;
@@ -636,6 +681,7 @@ void surfmcmc_default_opts(surfmcmc_opts* o) {
     o->anneal_beta0 = 1.0;
     o->scan = 0;
     o->noise = 0;
+    o->pauli_energy[0] = o->pauli_energy[1] = o->pauli_energy[2] = 1;
 }
 
 const char* surfmcmc_strerror(int code) {
@@ -712,6 +758,30 @@ int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches) {
 int surfmcmc_gen_syndromes(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
                            uint8_t* syndromes, int32_t* true_class, void* stream) {
     return surfmcmc_gen_syndromes_noise(ctx, seed, id0, n, L, p, 0, syndromes, true_class, stream);
+}
+
+int surfmcmc_gen_syndromes_pauli(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double px,
+                                 double py, double pz, uint8_t* syndromes, int32_t* true_class, void* stream) {
+    int rc = check_common(ctx, n, L, id0);
+    if (rc) return rc;
+    if (!(px >= 0.0 && py >= 0.0 && pz >= 0.0 && px + py + pz <= 0.75))
+        return fail(ctx, SURFMCMC_EINVAL, "pX, pY, pZ must be >= 0 with pX + pY + pZ <= 0.75");
+    if (n > 0 && !syndromes) return fail(ctx, SURFMCMC_EINVAL, "syndromes is NULL");
+    if (n == 0) return SURFMCMC_OK;
+    ctx->last_error.clear();
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver cv;
+    Buf bs, bt;
+    plan(bs, syndromes, (size_t)n * n_stabs(L), cv);
+    plan(bt, true_class, true_class ? (size_t)n * 4 : 0, cv);
+    if ((rc = ensure_arena(ctx, cv.off))) return rc;
+    bind(bs, ctx);
+    bind(bt, ctx);
+    CK(launch_gen_syndromes_pauli(seed, id0, n, L, px, py, pz, (uint8_t*)bs.dev, (int32_t*)bt.dev, s));
+    if ((rc = copy_out(ctx, bs, s)) || (rc = copy_out(ctx, bt, s))) return rc;
+    if (!stream || bs.staged || bt.staged) CK(cudaStreamSynchronize(s));
+    return SURFMCMC_OK;
 }
 
 int surfmcmc_gen_syndromes_noise(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
@@ -797,6 +867,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     init_chains(sp, Cn, R, id0);
     sp.scan = o.scan;
     sp.noise = o.noise;
+    energy_table(o, sp.energy);
     lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
@@ -844,9 +915,11 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     io.unit_counter = ctr;
     if ((rc = run_segments(ctx, sp, segs, o.burn_in, p, lam, io, s))) return rc;
 
-    uint64_t T[5];
+    uint64_t T[33];
     double beta_bar;
-    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
+    int Eo[4];
+    energy_table(o, Eo);
+    acceptance_table(noise_rate(p, o.noise, Eo), 1.0, T, &beta_bar);
     DecideParams dp;
     memset(&dp, 0, sizeof dp);
     dp.n = n;
@@ -901,6 +974,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     init_chains(sp, Cn, R, id0);
     sp.scan = o.scan;
     sp.noise = o.noise;
+    energy_table(o, sp.energy);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
     const int W = n_words(L), nq = n_qubits(L);
@@ -944,12 +1018,15 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
         if ((rc = run_segments(ctx, sp, plan_segments(o, bs, 0), o.burn_in, p, lam, io, s))) return rc;
         CK(launch_class_means(n, K, R, N, j, samples, chain_sum, mean, s));
     }
-    uint64_t T[5];
+    uint64_t T[33];
     double beta_bar;
-    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
+    int Eo[4];
+    energy_table(o, Eo);
+    acceptance_table(noise_rate(p, o.noise, Eo), 1.0, T, &beta_bar);
     const double h = (o.beta_scale * beta_bar) / (double)(N - 1);
-    // <n> at beta = 0: 3/4 n_q (depolarizing), n_q (independent flips)
-    const double mean0 = (o.noise ? 1.0 : 0.75) * (double)nq;
+    // <n> at beta = 0: every Pauli equally likely on each qubit, so n_q times
+    // the mean of the four energies (3/4 n_q depolarizing, n_q flips)
+    const double mean0 = (double)nq * (double)(Eo[1] + Eo[2] + Eo[3]) / 4.0;
     CK(launch_ti_decide(n, K, N, mean0, h / 3.0, mean, (int32_t*)b_cls.dev, (double*)b_lz.dev, s));
 
     bool any_host = false;
@@ -1243,9 +1320,11 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
     CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, (uint32_t*)at(off_e0), (int32_t*)at(off_code), s));
     CK(launch_iota(n, (long long*)at(off_perm[0]), s));
 
-    uint64_t T[5];
+    uint64_t T[33];
     double beta_bar;
-    acceptance_table(p, o.noise, 1.0, T, &beta_bar);
+    int Eo[4];
+    energy_table(o, Eo);
+    acceptance_table(noise_rate(p, o.noise, Eo), 1.0, T, &beta_bar);
     long long n_act = n;
     uint32_t t = 0;
     int cur = 0;  // pair holding the active items' caller indices and ids
@@ -1257,6 +1336,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
         init_chains(sp, Cn, R, id0);
         sp.scan = o.scan;
         sp.noise = o.noise;
+        energy_table(o, sp.energy);
         sp.ids = t == 0 ? nullptr : (const uint32_t*)at(off_ids[cur]);
         const int lam_k = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n_act), sp.G);
         add_group(sp, L, n_act, 0, 0, 0, 0, lam_k);

@@ -49,7 +49,7 @@ __global__ void gen_syndromes_kernel(RoundKeys rk, uint32_t id0, long long n, in
     uint32_t ex[kMaxWords], ez[kMaxWords];
     for (int w = 0; w < W; ++w) ex[w] = ez[w] = 0;
     const uint32_t id = id0 + (uint32_t)i;
-    if (noise) {
+    if (noise == 1) {
         // independent flips: qubit q uses words 2 (q mod 2) (bit flip) and
         // 2 (q mod 2) + 1 (phase flip) of block (id, q div 2, 1, 0); tau1 =
         // floor(p 2^32)
@@ -64,8 +64,11 @@ __global__ void gen_syndromes_kernel(RoundKeys rk, uint32_t id0, long long n, in
         if (true_class) true_class[i] = class_code(L, ex, ez);
         return;
     }
+    // depolarizing: domain 0, thresholds tau, 2 tau, 3 tau; general channel:
+    // domain 2, thresholds pX, pX + pY, pX + pY + pZ (times 2^32)
+    const uint32_t domain = noise == 2 ? 2u : 0u;
     for (int q0 = 0; q0 < nq; q0 += 4) {
-        const uint4 b = philox10(make_uint4(id, (uint32_t)(q0 / 4), 0u, 0u), rk);
+        const uint4 b = philox10(make_uint4(id, (uint32_t)(q0 / 4), domain, 0u), rk);
         const uint32_t u[4] = {b.x, b.y, b.z, b.w};
         for (int k = 0; k < 4 && q0 + k < nq; ++k) {
             // X for u < tau, Y for tau <= u < 2 tau, Z for 2 tau <= u < 3 tau
@@ -280,6 +283,20 @@ __global__ void iota_kernel(long long n, long long* perm) {
 cudaError_t launch_iota(long long n, long long* perm, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     iota_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_syndromes_pauli(uint64_t seed, uint32_t id0, long long n, int L, double px, double py,
+                                       double pz, uint8_t* syn, int32_t* true_class, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    RoundKeys rk;
+    make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u, &rk);
+    const uint64_t t1 = (uint64_t)floor(px * 4294967296.0);
+    const uint64_t t2 = (uint64_t)floor((px + py) * 4294967296.0);
+    const uint64_t t3 = (uint64_t)floor((px + py + pz) * 4294967296.0);
+    const int bs = 128;
+    gen_syndromes_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rk, id0, n, L, 2, (uint32_t)t1, (uint32_t)t2,
+                                                                      (uint32_t)t3, syn, true_class);
     return cudaGetLastError();
 }
 

@@ -124,7 +124,8 @@ struct SweepParams {
     const uint32_t* ids;       // per-syndrome ids (NULL: id0 + global index)
     int scan;                  // 0: colour sweeps; 1: random scan (one random generator per step)
     int noise;                 // 0: depolarizing; 1: independent bit and phase flips
-    uint64_t T[5];             // acceptance thresholds T[d] = floor(r*^d 2^32) (random scan)
+    uint64_t T[33];            // acceptance thresholds T[d] = floor(r*^d 2^32), d <= 32 (random scan)
+    int energy[4];             // energy of a qubit's Pauli, index x + 2z (I, X, Z, Y) (random scan)
     int accept_all;            // r* == 1: every proposal accepted
     int reject_all;            // T[1] == 0: no uphill proposal accepted
     uint32_t qmodes;           // per quad of planes 4q..4q+3, 2 bits: 0 every threshold digit is 0,
@@ -171,6 +172,8 @@ size_t sweep_smem_bytes(int nq, int nc, int lanes_per_bundle);  // dynamic share
 long long sweep_units(long long n_bundles, int lanes_per_bundle);  // work units of a group
 cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L, double p,
                                  uint8_t* syn, int32_t* true_class, cudaStream_t s, int noise = 0);
+cudaError_t launch_gen_syndromes_pauli(uint64_t seed, uint32_t id0, long long n, int L, double px, double py,
+                                       double pz, uint8_t* syn, int32_t* true_class, cudaStream_t s);
 cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
                                 cudaStream_t s);
 cudaError_t launch_decide(const DecideParams& p, cudaStream_t s);

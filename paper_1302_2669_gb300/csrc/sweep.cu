@@ -15,11 +15,13 @@ long long sweep_units(long long n_bundles, int lam) { return (n_bundles + (long 
 
 // Sets the kernel's shared-memory limit ahead of a stream capture.
 cudaError_t prepare_sweep(const SweepParams& p, int lam) {
-    return p.noise ? prepare_sweep_flips(p, lam) : prepare_noise<false>(p, lam);
+    return p.noise == 1 ? prepare_sweep_flips(p, lam) : prepare_noise<false>(p, lam);
 }
 
 cudaError_t launch_sweep(const SweepParams& p, int lam, cudaStream_t s) {
-    return p.noise ? launch_sweep_flips(p, lam, s) : launch_noise<false>(p, lam, s);
+    // the general channel (noise 2) runs only in random scan, which reads the
+    // energy table and not the template's noise model
+    return p.noise == 1 ? launch_sweep_flips(p, lam, s) : launch_noise<false>(p, lam, s);
 }
 
 }  // namespace surfmcmc

@@ -455,6 +455,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
     uint32_t since_flush = 0;
     __syncwarp();
 
+    int scan_n = 0;  // random scan: the lane's chain's n at the end
     if constexpr (SCAN) {
         static_assert(LAM == 32, "random scan runs one chain per lane");
         // Sec. IV as written: each step draws one generator g = floor(w0
@@ -467,9 +468,12 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
         const uint32_t my_sid = sid[G == 32 ? 0 : b / G];
         const uint32_t chain = (uint32_t)chain_of(b);
         const int ns = 2 * L * (L - 1);
+        // energy of a qubit's Pauli, index x + 2z (I, X, Z, Y): the noise
+        // model's table (depolarizing 0 1 1 1, flips 0 1 1 2, general)
+        const int E0 = p.energy[0], E1 = p.energy[1], E2 = p.energy[2], E3 = p.energy[3];
+        auto energy = [&](uint32_t x, uint32_t z) { return x ? (z ? E3 : E1) : (z ? E2 : E0); };
         int n = 0;
-        for (int q = 0; q < nq; ++q)
-            n += IND ? (int)(((X[q] >> b) & 1u) + ((Z[q] >> b) & 1u)) : (int)(((X[q] | Z[q]) >> b) & 1u);
+        for (int q = 0; q < nq; ++q) n += energy((X[q] >> b) & 1u, (Z[q] >> b) & 1u);
         uint64_t sum = 0;
         for (uint32_t t = gd.t_begin; t < gd.t_end; ++t) {
             const bool sample = t >= gd.burn_in;
@@ -482,8 +486,11 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                 const uint32_t* oth = type == 0 ? Z : X;
                 int dn = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (IND ? q[k] < nq : !((oth[q[k]] >> b) & 1u)) dn += ((own[q[k]] >> b) & 1u) ? -1 : 1;
+                for (int k = 0; k < 4; ++k) {
+                    if (q[k] >= nq) continue;  // dummy slot of a weight-3 generator
+                    const uint32_t o = (own[q[k]] >> b) & 1u, t2 = (oth[q[k]] >> b) & 1u;
+                    dn += type == 0 ? energy(o ^ 1u, t2) - energy(o, t2) : energy(t2, o ^ 1u) - energy(t2, o);
+                }
                 if (mine && (dn <= 0 || (uint64_t)r.y < p.T[dn])) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) atomicXor(&own[q[k]], bit);
@@ -493,6 +500,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
             }
         }
         if (mine && p.chain_sum) p.chain_sum[ci_of(b)] += sum;
+        scan_n = n;
         __syncwarp();
     } else
     for (uint32_t t = gd.t_begin; t < gd.t_end; ++t) {
@@ -606,14 +614,14 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
             st[nq + q] = Z[q];
         }
     }
-    uint32_t cnt[kCountBits];
-    recount<LAM, IND>(X, Z, nq, sub, cnt);
+    uint32_t cnt[kCountBits] = {};
+    if constexpr (!SCAN) recount<LAM, IND>(X, Z, nq, sub, cnt);
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
         const int b = sub + j * LAM;
         if (!((valid >> b) & 1u)) continue;
         const size_t ci = (size_t)syn_of(b) * p.C + chain_of(b);
-        if (p.chain_n) p.chain_n[ci] = (int32_t)bit_of(cnt, b);
+        if (p.chain_n) p.chain_n[ci] = SCAN ? scan_n : (int32_t)bit_of(cnt, b);
         if (cfg) {
             uint32_t* f = cfg + ci * 2 * W;
             for (int wi = 0; wi < W; ++wi) {
