@@ -50,6 +50,13 @@ SM_COUNT = 152
 INT_LANES_PER_SM = 128
 
 
+# DRAM bytes (read + write) of one sampled sweep launch per syndrome of the
+# L = 13, 4 x 16-chain workload, from one ncu capture at 8,192 syndromes
+# (41,096,960 B read + 1,280 B written: the bit-sliced chain state handed
+# over from the annealing launch, proportional to the syndromes).
+SWEEP_DRAM_BYTES_PER_SYNDROME = (41096960 + 1280) / 8192
+
+
 def ops_per_update() -> float:
     """Algorithmic integer operations per proposal of one chain in the
     bit-sliced formulation (32 chains per word): 28 bitwise ops to classify
@@ -292,7 +299,9 @@ def main():
                                                                      / max(m, 1)), "syndromes": m}
                 for p, (f, m) in fails.items() if m},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": None,
+                     "frac": achieved / peak_ops,
+                     "traffic": SWEEP_DRAM_BYTES_PER_SYNDROME * n,
+                     "traffic_unit": "bytes per sampled sweep launch",
                      "kernel": "sweep_kernel", "ops_per_update": ops_per_update(),
                      "kernel_ms_per_step": sweep_s_per_step * 1000.0, "kernel_launches": sweep_launches,
                      "peak_basis": f"{SM_COUNT} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_max:.0f} MHz "
