@@ -61,6 +61,16 @@ def lib():
         L.orc_thresholds_noise.argtypes = [C.c_double, C.c_int, C.c_double, u64p, C.POINTER(C.c_double)]
         L.orc_exact_histogram_noise.argtypes = [C.c_int, u8p, C.c_int, u64p]
         L.orc_exact_histogram_energy.argtypes = [C.c_int, u8p, C.c_int, C.c_void_p, C.c_int, u64p]
+        L.orc_t_stab_pos.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.orc_t_stab_support.argtypes = [C.c_int, C.c_int, i32p]
+        L.orc_t_stab_colour.argtypes = [C.c_int, C.c_int]
+        L.orc_t_syndrome.argtypes = [C.c_int, u8p, u8p, u8p]
+        L.orc_t_class_code.argtypes = [C.c_int, u8p, u8p]
+        L.orc_t_apply_logical.argtypes = [C.c_int, C.c_int, u8p, u8p]
+        L.orc_t_pure_error.argtypes = [C.c_int, u8p, u8p, u8p]
+        L.orc_t_start_frame.argtypes = [C.c_int, u8p, C.c_int, u8p, u8p]
+        L.orc_t_gen_syndromes.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_double, u8p, i32p]
+        L.orc_t_exact_histogram.argtypes = [C.c_int, u8p, u64p]
         L.orc_rate_general.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int]
         L.orc_rate_general.restype = C.c_double
         L.orc_thresholds_r.argtypes = [C.c_double, C.c_double, C.c_int, u64p, C.POINTER(C.c_double)]
@@ -201,6 +211,77 @@ def start_frame(L: int, syn: np.ndarray, k: int):
     return ex, ez, code0
 
 
+# --- toric code (16 classes) -------------------------------------------------
+def t_nq(L: int) -> int:
+    return 2 * L * L
+
+
+def t_nstab(L: int) -> int:
+    return 2 * L * L
+
+
+def t_stab_pos(L: int, g: int):
+    r, c = C.c_int(), C.c_int()
+    t = lib().orc_t_stab_pos(L, g, C.byref(r), C.byref(c))
+    return t, r.value, c.value
+
+
+def t_stab_support(L: int, g: int) -> np.ndarray:
+    q = np.zeros(4, np.int32)
+    lib().orc_t_stab_support(L, g, q)
+    return q
+
+
+def t_stab_colour(L: int, g: int) -> int:
+    return lib().orc_t_stab_colour(L, g)
+
+
+def t_syndrome(L: int, ex, ez) -> np.ndarray:
+    s = np.zeros(t_nstab(L), np.uint8)
+    lib().orc_t_syndrome(L, np.ascontiguousarray(ex, np.uint8), np.ascontiguousarray(ez, np.uint8), s)
+    return s
+
+
+def t_class_code(L: int, ex, ez) -> int:
+    return lib().orc_t_class_code(L, np.ascontiguousarray(ex, np.uint8), np.ascontiguousarray(ez, np.uint8))
+
+
+def t_apply_logical(L: int, k: int, ex, ez):
+    ex = np.array(ex, np.uint8)
+    ez = np.array(ez, np.uint8)
+    lib().orc_t_apply_logical(L, k, ex, ez)
+    return ex, ez
+
+
+def t_pure_error(L: int, syn):
+    ex = np.zeros(t_nq(L), np.uint8)
+    ez = np.zeros(t_nq(L), np.uint8)
+    lib().orc_t_pure_error(L, np.ascontiguousarray(syn, np.uint8), ex, ez)
+    return ex, ez
+
+
+def t_start_frame(L: int, syn, k: int):
+    ex = np.zeros(t_nq(L), np.uint8)
+    ez = np.zeros(t_nq(L), np.uint8)
+    code0 = lib().orc_t_start_frame(L, np.ascontiguousarray(syn, np.uint8), k, ex, ez)
+    return ex, ez, code0
+
+
+def t_gen_syndromes(seed: int, id0: int, n: int, L: int, p: float):
+    syn = np.zeros((n, t_nstab(L)), np.uint8)
+    tc = np.zeros(n, np.int32)
+    if n:
+        lib().orc_t_gen_syndromes(seed, id0, n, L, p, syn, tc)
+    return syn, tc
+
+
+def t_exact_histogram(L: int, syn) -> np.ndarray:
+    h = np.zeros((16, t_nq(L) + 1), np.uint64)
+    if lib().orc_t_exact_histogram(L, np.ascontiguousarray(syn, np.uint8), h) != 0:
+        raise ValueError("exact enumeration needs n_stab <= 30")
+    return h
+
+
 def rate_general(p: float, energy) -> float:
     """r = e^{-beta_bar} of the general channel with energies (eX, eY, eZ)."""
     return lib().orc_rate_general(p, int(energy[0]), int(energy[1]), int(energy[2]))
@@ -267,7 +348,7 @@ def run_chains(L, K, R, p, seed, ident, syn, t_begin, t_end, burn_in=0, beta_sca
     with frames_x/z, chain_sum, chain_n and optionally the colour-phase trace
     of chain 0 and accept counts."""
     Cn = K * R
-    n = nq(L)
+    n = t_nq(L) if K == 16 else nq(L)
     fx = np.zeros((Cn, n), np.uint8) if frames is None else np.array(frames[0], np.uint8)
     fz = np.zeros((Cn, n), np.uint8) if frames is None else np.array(frames[1], np.uint8)
     cs = np.zeros(Cn, np.uint64) if chain_sum is None else np.array(chain_sum, np.uint64)
@@ -300,7 +381,7 @@ def decode_one(L, p, K, R, n_sweeps, seed, ident, syn, burn_in=0, beta_scale=1.0
     """Decode one syndrome; returns a dict with the chosen class, per-class
     sums and log-ratios, per-chain sums, final n and final frames."""
     Cn = K * R
-    n = nq(L)
+    n = t_nq(L) if K == 16 else nq(L)
     S = np.zeros(K, np.uint64)
     lr = np.zeros(K, np.float64)
     cs = np.zeros(Cn, np.uint64)

@@ -294,6 +294,219 @@ int orc_start_frame(int L, const uint8_t* syn, int k, uint8_t* ex, uint8_t* ez)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Toric code (the 16-class variant): an L x L torus, L even, on the periodic */
+/* 2L x 2L grid.  Data qubits at r+c odd, index r L + (c div 2) (2L^2 of     */
+/* them); sigma_x generators (stars) at (even r, even c), sigma_z generators */
+/* (plaquettes) at (odd r, odd c), all of weight 4; syndrome layout: stars   */
+/* row-major over (i, j) = (r/2, c/2), then plaquettes over ((r-1)/2,        */
+/* (c-1)/2).  Two encoded qubits, so 4 logical operators and 16 classes:     */
+/* X1 = sigma_x on row 1, X2 = sigma_x on column 1, Z1 = sigma_z on column   */
+/* 0, Z2 = sigma_z on row 0 (X1, Z1 and X2, Z2 anticommute, other pairs     */
+/* commute).  Class code a1 + 2 a2 + 4 b1 + 8 b2 with a1 (a2) the parity of */
+/* x on the support of Z1 (Z2) and b1 (b2) the parity of z on the support  */
+/* of X1 (X2).                                                               */
+/* ------------------------------------------------------------------------ */
+int orc_t_nq(int L) { return 2 * L * L; }
+int orc_t_nstab(int L) { return 2 * L * L; }
+
+static int t_mod(int L, int v) { int m = 2 * L; return ((v % m) + m) % m; }
+static int t_qidx(int L, int r, int c) { r = t_mod(L, r); c = t_mod(L, c); return r * L + c / 2; }
+
+int orc_t_stab_pos(int L, int g, int* r, int* c)
+{
+    int type = g >= L * L;
+    if (type) g -= L * L;
+    *r = 2 * (g / L) + type;
+    *c = 2 * (g % L) + type;
+    return type;
+}
+
+int orc_t_stab_support(int L, int g, int32_t* q)
+{
+    int r, c;
+    orc_t_stab_pos(L, g, &r, &c);
+    q[0] = t_qidx(L, r - 1, c);
+    q[1] = t_qidx(L, r + 1, c);
+    q[2] = t_qidx(L, r, c - 1);
+    q[3] = t_qidx(L, r, c + 1);
+    return 4;
+}
+
+/* Colours: stars with (i+j) even -> 0, odd -> 1; plaquettes -> 2, 3 (with L
+ * even, generators of one colour share no qubit across the periodic edges). */
+int orc_t_stab_colour(int L, int g)
+{
+    int type = g >= L * L;
+    int h = type ? g - L * L : g;
+    return 2 * type + ((h / L + h % L) & 1);
+}
+
+int orc_t_colour_member(int L, int col, int m)
+{
+    for (int g = 0; g < orc_t_nstab(L); ++g)
+        if (orc_t_stab_colour(L, g) == col && m-- == 0) return g;
+    return -1;
+}
+
+void orc_t_syndrome(int L, const uint8_t* ex, const uint8_t* ez, uint8_t* syn)
+{
+    int32_t q[4];
+    for (int g = 0; g < orc_t_nstab(L); ++g) {
+        int r, c;
+        int type = orc_t_stab_pos(L, g, &r, &c);
+        orc_t_stab_support(L, g, q);
+        int par = 0;
+        for (int k = 0; k < 4; ++k) par ^= type == 0 ? ez[q[k]] : ex[q[k]];
+        syn[g] = (uint8_t)par;
+    }
+}
+
+int orc_t_class_code(int L, const uint8_t* ex, const uint8_t* ez)
+{
+    int a1 = 0, a2 = 0, b1 = 0, b2 = 0;
+    for (int i = 0; i < L; ++i) {
+        a1 ^= ex[t_qidx(L, 2 * i + 1, 0)];   /* Z1: column 0, odd rows */
+        a2 ^= ex[t_qidx(L, 0, 2 * i + 1)];   /* Z2: row 0, odd columns */
+        b1 ^= ez[t_qidx(L, 1, 2 * i)];       /* X1: row 1, even columns */
+        b2 ^= ez[t_qidx(L, 2 * i, 1)];       /* X2: column 1, even rows */
+    }
+    return a1 + 2 * a2 + 4 * b1 + 8 * b2;
+}
+
+void orc_t_apply_logical(int L, int k, uint8_t* ex, uint8_t* ez)
+{
+    for (int i = 0; i < L; ++i) {
+        if (k & 1) ex[t_qidx(L, 1, 2 * i)] ^= 1;       /* X1 */
+        if (k & 2) ex[t_qidx(L, 2 * i, 1)] ^= 1;       /* X2 */
+        if (k & 4) ez[t_qidx(L, 2 * i + 1, 0)] ^= 1;   /* Z1 */
+        if (k & 8) ez[t_qidx(L, 0, 2 * i + 1)] ^= 1;   /* Z2 */
+    }
+}
+
+/* Pure error on the torus: the violated generators of each type (an even
+ * number) are paired in syndrome order, first with second, third with
+ * fourth, ...; a pair is joined by a string that runs from the first to the
+ * column of the second in the direction of increasing c (mod 2L), then down
+ * to its row in the direction of increasing r; sigma_z strings through the
+ * qubits between consecutive stars, sigma_x strings between consecutive
+ * plaquettes. */
+void orc_t_pure_error(int L, const uint8_t* syn, uint8_t* ex, uint8_t* ez)
+{
+    int nq = orc_t_nq(L);
+    memset(ex, 0, nq);
+    memset(ez, 0, nq);
+    for (int type = 0; type < 2; ++type) {
+        int first = -1;
+        for (int h = 0; h < L * L; ++h) {
+            int g = h + type * L * L;
+            if (!syn[g]) continue;
+            if (first < 0) { first = g; continue; }
+            int r0, c0, r1, c1;
+            orc_t_stab_pos(L, first, &r0, &c0);
+            orc_t_stab_pos(L, g, &r1, &c1);
+            uint8_t* f = type == 0 ? ez : ex;
+            for (int c = c0; c != c1; c = t_mod(L, c + 2)) f[t_qidx(L, r0, c + 1)] ^= 1;
+            for (int r = r0; r != r1; r = t_mod(L, r + 2)) f[t_qidx(L, r + 1, c1)] ^= 1;
+            first = -1;
+        }
+    }
+}
+
+int orc_t_start_frame(int L, const uint8_t* syn, int k, uint8_t* ex, uint8_t* ez)
+{
+    orc_t_pure_error(L, syn, ex, ez);
+    int code0 = orc_t_class_code(L, ex, ez);
+    orc_t_apply_logical(L, k ^ code0, ex, ez);
+    return code0;
+}
+
+/* Depolarizing errors on the torus (same draws per qubit as the planar
+ * generator: counter (id, q div 4, 0, 0), word q mod 4). */
+void orc_t_gen_syndromes(uint64_t seed, uint32_t id0, int64_t n, int L, double p, uint8_t* syn,
+                         int32_t* true_class)
+{
+    int nq = orc_t_nq(L), ns = orc_t_nstab(L);
+    uint8_t* ex = malloc(nq);
+    uint8_t* ez = malloc(nq);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u};
+    uint64_t tau = (uint64_t)floor((p / 3.0) * 4294967296.0);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t blk[4];
+        for (int q = 0; q < nq; ++q) {
+            uint32_t ctr[4] = {id0 + (uint32_t)i, (uint32_t)(q / 4), 0, 0};
+            orc_philox4x32_10(ctr, key, blk);
+            uint64_t u = blk[q % 4];
+            ex[q] = (uint8_t)(u < 2 * tau);
+            ez[q] = (uint8_t)(u >= tau && u < 3 * tau);
+        }
+        orc_t_syndrome(L, ex, ez, syn + i * ns);
+        if (true_class) true_class[i] = orc_t_class_code(L, ex, ez);
+    }
+    free(ex);
+    free(ez);
+}
+
+/* Exact weight histogram of the 16 classes on the torus (as for the planar
+ * code): all 2^{n_stab} products of generators times each class's start
+ * frame, Gray-code order; every frame of a class appears 4 times (the star
+ * product and the plaquette product are both the identity).  n_stab <= 30. */
+int orc_t_exact_histogram(int L, const uint8_t* syn, uint64_t* hist /* [16][nq+1] */)
+{
+    int nq = orc_t_nq(L), ns = orc_t_nstab(L);
+    if (ns > 30) return -1;
+    int32_t sup[4 * 64];
+    int type[64];
+    for (int g = 0; g < ns; ++g) {
+        int r, c;
+        type[g] = orc_t_stab_pos(L, g, &r, &c);
+        orc_t_stab_support(L, g, sup + 4 * g);
+    }
+    uint8_t ex[64], ez[64];
+    for (int k = 0; k < 16; ++k) {
+        uint64_t* h = hist + (size_t)k * (nq + 1);
+        memset(h, 0, sizeof(uint64_t) * (nq + 1));
+        orc_t_start_frame(L, syn, k, ex, ez);
+        int n = 0;
+        for (int q = 0; q < nq; ++q) n += ex[q] | ez[q];
+        h[n] += 1;
+        for (uint64_t i = 1; i < ((uint64_t)1 << ns); ++i) {
+            int g = __builtin_ctzll(i);
+            for (int e = 0; e < 4; ++e) {
+                if (type[g] == 0) ex[sup[4 * g + e]] ^= 1; else ez[sup[4 * g + e]] ^= 1;
+            }
+            n = 0;
+            for (int q = 0; q < nq; ++q) n += ex[q] | ez[q];
+            h[n] += 1;
+        }
+    }
+    return 0;
+}
+
+/* Geometry of a run: the planar code for 4 classes, the torus for 16. */
+static int geo_nq(int K, int L) { return K == 16 ? orc_t_nq(L) : orc_nq(L); }
+static int geo_nstab(int K, int L) { return K == 16 ? orc_t_nstab(L) : orc_nstab(L); }
+static int geo_stab_pos(int K, int L, int g, int* r, int* c)
+{
+    return K == 16 ? orc_t_stab_pos(L, g, r, c) : orc_stab_pos(L, g, r, c);
+}
+static int geo_stab_support(int K, int L, int g, int32_t* q)
+{
+    return K == 16 ? orc_t_stab_support(L, g, q) : orc_stab_support(L, g, q);
+}
+static int geo_colour_count(int K, int L, int col)
+{
+    return K == 16 ? orc_t_nstab(L) / 4 : orc_colour_count(L, col);
+}
+static int geo_colour_member(int K, int L, int col, int m)
+{
+    return K == 16 ? orc_t_colour_member(L, col, m) : orc_colour_member(L, col, m);
+}
+static int geo_start_frame(int K, int L, const uint8_t* syn, int k, uint8_t* ex, uint8_t* ez)
+{
+    return K == 16 ? orc_t_start_frame(L, syn, k, ex, ez) : orc_start_frame(L, syn, k, ex, ez);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Acceptance table (Eq. 2): r = (p/3)/(1-p) = e^{-beta_bar}; with a        */
 /* scaled temperature beta* = s beta_bar, r* = e^{-beta*}.                   */
 /* T[d] = floor(r*^d 2^32) for d = 1..4, r*^d by repeated multiplication.   */
@@ -551,7 +764,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                     uint8_t* frames_x, uint8_t* frames_z, uint64_t* chain_sum,
                     int32_t* chain_n, uint64_t* accepts, int32_t* trace)
 {
-    int L = a->L, nq = orc_nq(L), C = a->K * a->R;
+    int L = a->L, nq = geo_nq(a->K, L), C = a->K * a->R;
     uint64_t Tmain[33], Tst[64][33];
     int E[4];
     energy_table(a->noise, a->energy, E);
@@ -562,13 +775,13 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                          NULL);
     int ncol[4], members[4][ORC_MAX_L * ORC_MAX_L];
     for (int col = 0; col < 4; ++col) {
-        ncol[col] = orc_colour_count(L, col);
-        for (int m = 0; m < ncol[col]; ++m) members[col][m] = orc_colour_member(L, col, m);
+        ncol[col] = geo_colour_count(a->K, L, col);
+        for (int m = 0; m < ncol[col]; ++m) members[col][m] = geo_colour_member(a->K, L, col, m);
     }
     for (int c = 0; c < C; ++c) {
         uint8_t* ex = frames_x + (size_t)c * nq;
         uint8_t* ez = frames_z + (size_t)c * nq;
-        if (start_from_syndrome) orc_start_frame(L, syn, c / a->R, ex, ez);
+        if (start_from_syndrome) geo_start_frame(a->K, L, syn, c / a->R, ex, ez);
         int n = weight(nq, ex, ez, E);
         for (uint32_t t = a->t_begin; t < a->t_end; ++t) {
             int stage = a->anneal_stages > 0 ? orc_anneal_stage(t, a->burn_in, a->anneal_stages) : -1;
@@ -579,7 +792,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                  * Delta n <= 0 or w1 < T[Delta n]; f(n) = n is summed after
                  * every step.  A sweep is n_stab steps; Philox counter
                  * (id, chain, t, step), words w0, w1. */
-                int ns = orc_nstab(L);
+                int ns = geo_nstab(a->K, L);
                 for (int step = 0; step < ns; ++step) {
                     uint32_t ctr[4] = {a->id, (uint32_t)c, t, (uint32_t)step}, key[2], blk[4];
                     key[0] = (uint32_t)a->seed;
@@ -587,9 +800,9 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                     orc_philox4x32_10(ctr, key, blk);
                     int g = (int)(((uint64_t)blk[0] * (uint64_t)ns) >> 32);
                     int r, cc;
-                    int type = orc_stab_pos(L, g, &r, &cc);
+                    int type = geo_stab_pos(a->K, L, g, &r, &cc);
                     int32_t q[4];
-                    int w = orc_stab_support(L, g, q);
+                    int w = geo_stab_support(a->K, L, g, q);
                     int dn = delta_n(type, w, q, ex, ez, E);
                     if (dn <= 0 || (uint64_t)blk[1] < T[dn]) {
                         for (int k = 0; k < w; ++k) {
@@ -607,7 +820,7 @@ void orc_run_chains(const orc_run_t* a, const uint8_t* syn, int start_from_syndr
                 int type = col / 2;
                 for (int m = 0; m < ncol[col]; ++m) {
                     int32_t q[4];
-                    int w = orc_stab_support(L, members[col][m], q);
+                    int w = geo_stab_support(a->K, L, members[col][m], q);
                     int dn = delta_n(type, w, q, ex, ez, E);
                     /* Metropolis (Sec. IV): apply if Delta n <= 0, otherwise
                      * with probability e^{-beta* Delta n} = T[Delta n] / 2^32. */
@@ -665,7 +878,7 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
                    int32_t* chain_n, uint8_t* frames_x, uint8_t* frames_z, uint64_t* accepts, int scan,
                    int noise, const int32_t* energy)
 {
-    int nq = orc_nq(L), C = K * R;
+    int nq = geo_nq(K, L), C = K * R;
     orc_run_t a = {L, K, R, 0, n_sweeps, burn_in, p, beta_scale, seed, id, anneal_stages, anneal_beta0, scan, noise,
                    {1, 1, 1}};
     if (noise == 2)
@@ -679,7 +892,7 @@ int orc_decode_one(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bu
     double beta_bar;
     uint64_t T[5];
     orc_thresholds_r(run_rate(&a), 1.0, 4, T, &beta_bar);
-    int k = orc_decide(K, R, n_sweeps, burn_in, scan ? (uint32_t)orc_nstab(L) : 4u, beta_bar, cs, class_sum,
+    int k = orc_decide(K, R, n_sweeps, burn_in, scan ? (uint32_t)geo_nstab(K, L) : 4u, beta_bar, cs, class_sum,
                        log_ratio);
     if (!frames_x) free(fx);
     if (!frames_z) free(fz);
@@ -769,9 +982,9 @@ int orc_decode_ti(int L, double p, int K, int R, uint32_t n_sweeps, uint32_t bur
                   const uint8_t* syn, double* mean_out, double* log_z, int scan, int noise,
                   const int32_t* energy)
 {
-    int nq = orc_nq(L), C = K * R;
+    int nq = geo_nq(K, L), C = K * R;
     if (N < 3 || N % 2 == 0 || N > 129 || K > 64) return -1;
-    uint64_t per_sweep = scan ? (uint64_t)orc_nstab(L) : 4u;
+    uint64_t per_sweep = scan ? (uint64_t)geo_nstab(K, L) : 4u;
     uint64_t samples = n_sweeps > burn_in ? per_sweep * (uint64_t)R * (n_sweeps - burn_in) : 0;
     if (samples == 0) return -1;
     uint8_t* fx = malloc((size_t)C * nq);
