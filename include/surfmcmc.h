@@ -64,8 +64,21 @@ typedef struct surfmcmc_plan surfmcmc_plan;
 typedef struct surfmcmc_server surfmcmc_server;
 
 /* Decoder options.
- *   n_classes        number of equivalence classes; must be 4 (planar code,
- *                    Sec. II "there are four such equivalence classes").
+ *   n_classes        number of equivalence classes: 4 (planar code, Sec. II
+ *                    "there are four such equivalence classes"), or 16: the
+ *                    toric code on an L x L torus (L even, 2..30; decode,
+ *                    decode_ex and decode_ti only).  Torus layout: the
+ *                    periodic 2L x 2L grid, 2L^2 qubits at r+c odd with
+ *                    index r L + (c div 2); syndrome = 2L^2 bytes, the stars
+ *                    (sigma_x generators at (2i, 2j)) row-major, then the
+ *                    plaquettes (sigma_z at (2i+1, 2j+1)); class code
+ *                    a1 + 2 a2 + 4 b1 + 8 b2 with a1 (a2) the x parity on
+ *                    column 0, odd rows (row 0, odd columns) and b1 (b2)
+ *                    the z parity on row 1, even columns (column 1, even
+ *                    rows); colours 0/1 stars, 2/3 plaquettes by (i+j)
+ *                    parity.  Pure error: defects of each type paired in
+ *                    syndrome order, joined towards increasing c to the
+ *                    partner's column, then towards increasing r.
  *   chains_per_class R >= 1 independent replica chains per class;
  *                    n_classes * R <= 1024.
  *   n_sweeps         sweeps per chain; one sweep proposes every generator
@@ -168,6 +181,12 @@ int surfmcmc_gen_syndromes_noise(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0,
  * surfmcmc_gen_syndromes. */
 int surfmcmc_gen_syndromes_pauli(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double px,
                                  double py, double pz, uint8_t* syndromes, int32_t* true_class, void* stream);
+
+/* Depolarizing errors on the toric code (n_classes = 16 layout above, even L
+ * in 2..30): the same per-qubit draws as surfmcmc_gen_syndromes with the
+ * torus's 2L^2 qubits; syndromes [n][2L^2], true_class = 4-bit class code. */
+int surfmcmc_gen_syndromes_toric(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
+                                 uint8_t* syndromes, int32_t* true_class, void* stream);
 
 /* Start state (Sec. IV: one syndrome-compatible error per class, Sec. III's
  * boundary rule): the pure error joins every anyon to its nearer absorbing

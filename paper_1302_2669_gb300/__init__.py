@@ -67,7 +67,7 @@ class Opts:
 
 EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surfmcmc_strerror",
            "surfmcmc_last_error", "surfmcmc_gen_syndromes", "surfmcmc_gen_syndromes_noise",
-           "surfmcmc_gen_syndromes_pauli", "surfmcmc_start_frames", "surfmcmc_decode",
+           "surfmcmc_gen_syndromes_pauli", "surfmcmc_gen_syndromes_toric", "surfmcmc_start_frames", "surfmcmc_decode",
            "surfmcmc_decode_ex", "surfmcmc_set_timing", "surfmcmc_sweep_time", "surfmcmc_noalloc_scratch_needed",
            "surfmcmc_decode_noalloc", "surfmcmc_decode_ti", "surfmcmc_decode_ragged", "surfmcmc_ragged_plan_create",
            "surfmcmc_plan_launch", "surfmcmc_plan_destroy", "surfmcmc_autotune", "surfmcmc_server_default_opts",
@@ -99,6 +99,7 @@ def lib():
         L.surfmcmc_gen_syndromes.argtypes = [vp, u64, u32, i64, i32, dbl, vp, vp, vp]
         L.surfmcmc_gen_syndromes_noise.argtypes = [vp, u64, u32, i64, i32, dbl, i32, vp, vp, vp]
         L.surfmcmc_gen_syndromes_pauli.argtypes = [vp, u64, u32, i64, i32, dbl, dbl, dbl, vp, vp, vp]
+        L.surfmcmc_gen_syndromes_toric.argtypes = [vp, u64, u32, i64, i32, dbl, vp, vp, vp]
         L.surfmcmc_start_frames.argtypes = [vp, vp, i64, i32, vp, vp, vp]
         L.surfmcmc_decode.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
         L.surfmcmc_decode_ex.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, u32, vp, vp, vp, vp,
@@ -239,6 +240,17 @@ class Context:
                                                        _ptr(true_class), st))
         return syndromes, true_class
 
+    def gen_syndromes_toric(self, seed, id0, n, L, p, like=None, syndromes=None, true_class=None, stream=None):
+        """surfmcmc_gen_syndromes_toric: depolarizing errors on the L x L torus."""
+        if syndromes is None:
+            syndromes = _empty(like, (n, 2 * L * L), np.uint8)
+        if true_class is None:
+            true_class = _empty(like, (n,), np.int32)
+        st = stream if stream is not None else _stream_of(syndromes)
+        self._check(lib().surfmcmc_gen_syndromes_toric(self._h, seed, id0, n, L, p, _ptr(syndromes),
+                                                       _ptr(true_class), st))
+        return syndromes, true_class
+
     def start_frames(self, syndromes, L, frames=None, e0_class=None, stream=None):
         """surfmcmc_start_frames; returns (frames [n][2][W] uint32, e0_class [n])."""
         n = syndromes.shape[0]
@@ -280,7 +292,8 @@ class Context:
                "log_ratio": _empty(syndromes, (n, K), np.float64)}
         out["chain_sum"] = _empty(syndromes, (n, Cn), np.uint64) if chain_sum else None
         out["chain_n"] = _empty(syndromes, (n, Cn), np.int32) if chain_n else None
-        out["chain_frames"] = _empty(syndromes, (n, Cn, 2, n_words(L)), np.uint32) if chain_frames else None
+        W = (2 * L * L + 31) // 32 if K == 16 else n_words(L)    # toric code: 2 L^2 qubits
+        out["chain_frames"] = _empty(syndromes, (n, Cn, 2, W), np.uint32) if chain_frames else None
         st = stream if stream is not None else _stream_of(syndromes, out["cls"])
         o = opts.c()
         self._check(lib().surfmcmc_decode_ex(
@@ -293,9 +306,10 @@ class Context:
         """surfmcmc_decode_ti; returns (class [n], log_z [n][4], mean [n][4][n_beta])."""
         opts = opts or Opts()
         n = syndromes.shape[0]
+        K = opts.n_classes
         cls = _empty(syndromes, (n,), np.int32)
-        lz = _empty(syndromes, (n, 4), np.float64)
-        mean = _empty(syndromes, (n, 4, n_beta), np.float64)
+        lz = _empty(syndromes, (n, K), np.float64)
+        mean = _empty(syndromes, (n, K, n_beta), np.float64)
         st = stream if stream is not None else _stream_of(syndromes, cls)
         o = opts.c()
         self._check(lib().surfmcmc_decode_ti(self._h, _ptr(syndromes), n, L, p, C.byref(o), n_beta, seed, id0,

@@ -221,8 +221,8 @@ void set_temperature(SweepParams& sp, double p, double beta_scale) {
     }
 }
 
-int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nullptr, int R = 0) {
-    const int nq = n_qubits(L), nc = L * (L - 1) / 2;
+int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nullptr, int R = 0, int code = 0) {
+    const int nq = geo_nq(code, L), nc = geo_nc(code, L);
     auto smem_ok = [&](int lam) { return sweep_smem_bytes(nq, nc, lam) <= 200 * 1024; };
     if (requested) {
         if (requested != 2 && requested != 4 && requested != 8 && requested != 16 && requested != 32)
@@ -256,9 +256,9 @@ int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nul
 // time is the latency of one unit.  Unless the caller fixed the lanes, widen
 // (more lanes share a bundle's generators, shorter units) until the units
 // fill the resident blocks once.  The results do not depend on the lanes.
-int widen_lanes(const surfmcmc_ctx* ctx, int L, int requested, int lam, long long n_bundles, int G) {
+int widen_lanes(const surfmcmc_ctx* ctx, int L, int requested, int lam, long long n_bundles, int G, int code = 0) {
     if (requested || !ctx || ctx->sms <= 0) return lam;
-    const int nq = n_qubits(L), nc = L * (L - 1) / 2;
+    const int nq = geo_nq(code, L), nc = geo_nc(code, L);
     const long long capacity = (long long)ctx->sms * (G >= 16 ? 5 : 3);
     while (lam < 32 && sweep_units(n_bundles, lam) < capacity &&
            sweep_smem_bytes(nq, nc, 2 * lam) <= 200 * 1024)
@@ -276,9 +276,10 @@ int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
         if (o.scan != 1) return fail(ctx, SURFMCMC_EINVAL, "the general Pauli channel runs in random scan (scan=1)");
     }
     if (o.noise == 1 && !(p > 0.0 && p <= 0.5)) return fail(ctx, SURFMCMC_EINVAL, "flip p=%g outside (0, 0.5]", p);
-    if (o.n_classes != 4) return fail(ctx, SURFMCMC_EINVAL, "n_classes must be 4 (planar code)");
-    if (o.chains_per_class < 1 || 4 * o.chains_per_class > 1024)
-        return fail(ctx, SURFMCMC_EINVAL, "chains_per_class=%d outside 1..256", o.chains_per_class);
+    if (o.n_classes != 4 && o.n_classes != 16)
+        return fail(ctx, SURFMCMC_EINVAL, "n_classes must be 4 (planar code) or 16 (toric code)");
+    if (o.chains_per_class < 1 || o.n_classes * o.chains_per_class > 1024)
+        return fail(ctx, SURFMCMC_EINVAL, "n_classes * chains_per_class must be in 1..1024");
     if (o.burn_in > o.n_sweeps) return fail(ctx, SURFMCMC_EINVAL, "burn_in > n_sweeps");
     if (!(o.beta_scale >= 0.0)) return fail(ctx, SURFMCMC_EINVAL, "beta_scale must be >= 0");
     if (std::isinf(o.beta_scale) && p == (o.noise == 1 ? 0.5 : 0.75))
@@ -295,7 +296,22 @@ int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
 
 // Samples of n per chain and sweep: one per colour phase (sweeps), one per
 // step (random scan: n_stab steps per sweep).
-uint64_t samples_per_sweep(const surfmcmc_opts& o, int L) { return o.scan ? (uint64_t)n_stabs(L) : 4u; }
+uint64_t samples_per_sweep(const surfmcmc_opts& o, int L) {
+    return o.scan ? (uint64_t)geo_nstab(o.n_classes == 16, L) : 4u;
+}
+
+// The toric code (16 classes) needs an even L in 2..30 (its colouring) and
+// runs through decode, decode_ex and decode_ti only.
+int check_toric(surfmcmc_ctx* ctx, const surfmcmc_opts& o, int L) {
+    if (o.n_classes != 16) return SURFMCMC_OK;
+    if (L < 2 || L > 30 || (L & 1)) return fail(ctx, SURFMCMC_EINVAL, "toric code needs an even L in 2..30");
+    return SURFMCMC_OK;
+}
+
+int reject_toric(surfmcmc_ctx* ctx, const surfmcmc_opts& o, const char* what) {
+    if (o.n_classes == 16) return fail(ctx, SURFMCMC_EINVAL, "%s supports the planar code (4 classes) only", what);
+    return SURFMCMC_OK;
+}
 
 // Chain layout of a run: C chains per syndrome, plane width G, bundles of 32
 // chains (G = 32: C/32 bundles per syndrome; G < 32: 32/G syndromes per
@@ -323,9 +339,9 @@ void add_group(SweepParams& sp, int L, long long n, long long item_base, long lo
                long long state_off, int lam) {
     GroupDesc& g = sp.grp[sp.n_groups++];
     g.L = L;
-    g.nq = n_qubits(L);
-    g.W = n_words(L);
-    g.nc = L * (L - 1) / 2;
+    g.nq = geo_nq(sp.code, L);
+    g.W = geo_words(sp.code, L);
+    g.nc = geo_nc(sp.code, L);
     g.n = n;
     g.n_bundles = bundles_of(sp, n);
     g.item_base = item_base;
@@ -633,6 +649,7 @@ int ragged_check(surfmcmc_ctx* ctx, const int32_t* Ls, int64_t n, const surfmcmc
     if (!ids && (uint64_t)id0 + (uint64_t)n > 4294967296ull)
         return fail(ctx, SURFMCMC_EINVAL, "syndrome ids id0+n exceed 2^32");
     if ((rc = check_opts(ctx, o, p))) return rc;
+    if ((rc = reject_toric(ctx, o, "ragged decoding"))) return rc;
     return SURFMCMC_OK;
 }
 
@@ -760,6 +777,30 @@ int surfmcmc_gen_syndromes(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64
     return surfmcmc_gen_syndromes_noise(ctx, seed, id0, n, L, p, 0, syndromes, true_class, stream);
 }
 
+int surfmcmc_gen_syndromes_toric(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double p,
+                                 uint8_t* syndromes, int32_t* true_class, void* stream) {
+    int rc = check_common(ctx, n, L, id0);
+    if (rc) return rc;
+    if (L < 2 || L > 30 || (L & 1)) return fail(ctx, SURFMCMC_EINVAL, "toric code needs an even L in 2..30");
+    if (!(p >= 0.0 && p <= 0.75)) return fail(ctx, SURFMCMC_EINVAL, "p=%g outside [0, 0.75]", p);
+    if (n > 0 && !syndromes) return fail(ctx, SURFMCMC_EINVAL, "syndromes is NULL");
+    if (n == 0) return SURFMCMC_OK;
+    ctx->last_error.clear();
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver cv;
+    Buf bs, bt;
+    plan(bs, syndromes, (size_t)n * geo_nstab(1, L), cv);
+    plan(bt, true_class, true_class ? (size_t)n * 4 : 0, cv);
+    if ((rc = ensure_arena(ctx, cv.off))) return rc;
+    bind(bs, ctx);
+    bind(bt, ctx);
+    CK(launch_gen_syndromes_toric(seed, id0, n, L, p, (uint8_t*)bs.dev, (int32_t*)bt.dev, s));
+    if ((rc = copy_out(ctx, bs, s)) || (rc = copy_out(ctx, bt, s))) return rc;
+    if (!stream || bs.staged || bt.staged) CK(cudaStreamSynchronize(s));
+    return SURFMCMC_OK;
+}
+
 int surfmcmc_gen_syndromes_pauli(surfmcmc_ctx* ctx, uint64_t seed, uint32_t id0, int64_t n, int32_t L, double px,
                                  double py, double pz, uint8_t* syndromes, int32_t* true_class, void* stream) {
     int rc = check_common(ctx, n, L, id0);
@@ -849,8 +890,10 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     if (!init_frames && sweep_begin != 0)
         return fail(ctx, SURFMCMC_EINVAL, "sweep_begin > 0 needs init_frames");
     if (n > 0 && (!syndromes || !out_class)) return fail(ctx, SURFMCMC_EINVAL, "NULL syndromes or out_class");
+    if ((rc = check_toric(ctx, o, L))) return rc;
+    const int toric = o.n_classes == 16 ? 1 : 0;
     int lam = 0;
-    if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class))
+    if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class, toric))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
     if (o.scan) lam = 32;
     if (n == 0) return SURFMCMC_OK;
@@ -858,17 +901,18 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
 
-    const int K = 4, R = o.chains_per_class, Cn = K * R;
-    const int nq = n_qubits(L), W = n_words(L), ns = n_stabs(L);
+    const int K = o.n_classes, R = o.chains_per_class, Cn = K * R;
+    const int nq = geo_nq(toric, L), W = geo_words(toric, L), ns = geo_nstab(toric, L);
     int G = 1;
     while (G < Cn && G < 32) G *= 2;
 
     SweepParams sp;
     init_chains(sp, Cn, R, id0);
+    sp.code = toric;
     sp.scan = o.scan;
     sp.noise = o.noise;
     energy_table(o, sp.energy);
-    lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G);
+    lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G, toric);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32), &sp.rk);
 
@@ -901,7 +945,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     unsigned int* ctr = (unsigned int*)(base + off_ctr);
 
     if ((rc = copy_in(ctx, b_syn, s)) || (rc = copy_in(ctx, b_if, s)) || (rc = copy_in(ctx, b_is, s))) return rc;
-    if (!init_frames) CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
+    if (!init_frames) CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s, toric));
 
     SweepIO io;
     io.e0 = e0;
@@ -961,27 +1005,30 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
         return fail(ctx, SURFMCMC_EINVAL, "n_beta=%d must be odd in 3..129", n_beta);
     if (o.n_sweeps <= o.burn_in) return fail(ctx, SURFMCMC_EINVAL, "no sampled sweeps");
     if (n > 0 && (!syndromes || !out_class)) return fail(ctx, SURFMCMC_EINVAL, "NULL syndromes or out_class");
+    if ((rc = check_toric(ctx, o, L))) return rc;
+    const int toric = o.n_classes == 16 ? 1 : 0;
     int lam = 0;
-    if (pick_lanes(L, o.lanes_per_bundle, &lam))
+    if (pick_lanes(L, o.lanes_per_bundle, &lam, nullptr, 0, toric))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
     if (o.scan) lam = 32;
     if (n == 0) return SURFMCMC_OK;
     ctx->last_error.clear();
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const int K = 4, R = o.chains_per_class, Cn = K * R, N = n_beta;
+    const int K = o.n_classes, R = o.chains_per_class, Cn = K * R, N = n_beta;
     SweepParams sp;
     init_chains(sp, Cn, R, id0);
+    sp.code = toric;
     sp.scan = o.scan;
     sp.noise = o.noise;
     energy_table(o, sp.energy);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
-    const int W = n_words(L), nq = n_qubits(L);
+    const int W = geo_words(toric, L), nq = geo_nq(toric, L);
 
     Carver cv;
     Buf b_syn, b_cls, b_lz;
-    plan(b_syn, (void*)syndromes, (size_t)n * n_stabs(L), cv);
+    plan(b_syn, (void*)syndromes, (size_t)n * geo_nstab(toric, L), cv);
     plan(b_cls, out_class, (size_t)n * 4, cv);
     plan(b_lz, out_log_z, out_log_z ? (size_t)n * K * 8 : 0, cv);
     const bool mean_scratch = !out_mean || !is_device_ptr(out_mean);
@@ -1002,7 +1049,7 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     unsigned int* ctr = (unsigned int*)(base + off_ctr);
 
     if ((rc = copy_in(ctx, b_syn, s))) return rc;
-    CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s));
+    CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s, toric));
     const uint64_t samples = samples_per_sweep(o, L) * R * (o.n_sweeps - o.burn_in);
     for (int j = 1; j < N; ++j) {
         // grid point j: beta_j = beta* j/(N-1), randomness keyed by seed + j
@@ -1252,6 +1299,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
     surfmcmc_default_opts(&o);
     if (opts_in) o = *opts_in;
     if ((rc = check_opts(ctx, o, p))) return rc;
+    if ((rc = reject_toric(ctx, o, "early stop"))) return rc;
     if (!net || cnn_code_size(net) != L) return fail(ctx, SURFMCMC_EINVAL, "network missing or built for another L");
     if (chunk_sweeps == 0) return fail(ctx, SURFMCMC_EINVAL, "chunk_sweeps must be > 0");
     if (tau != tau) return fail(ctx, SURFMCMC_EINVAL, "tau is NaN");

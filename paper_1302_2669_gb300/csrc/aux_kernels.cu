@@ -83,6 +83,99 @@ __global__ void gen_syndromes_kernel(RoundKeys rk, uint32_t id0, long long n, in
 // Pure error: a straight string from every anyon to its nearer absorbing
 // boundary (Sec. III), s-anyons vertically (z string), p-anyons horizontally
 // (x string); ties go up/left.
+// Toric code: syndrome of a frame, its 4-bit class code, and the pure error
+// (defects of each type paired in syndrome order, first with second, ...;
+// a pair joined from the first towards increasing c to the second's
+// column, then towards increasing r to its row; sigma_z strings between
+// stars, sigma_x strings between plaquettes).
+__device__ void write_syndrome_toric(int L, const uint32_t* ex, const uint32_t* ez, uint8_t* out) {
+    for (int g = 0; g < 2 * L * L; ++g) {
+        int q[4];
+        const int type = toric_generator_support(L, g, q);
+        const uint32_t* f = type == 0 ? ez : ex;
+        out[g] = (uint8_t)(getb(f, q[0]) ^ getb(f, q[1]) ^ getb(f, q[2]) ^ getb(f, q[3]));
+    }
+}
+
+__device__ int class_code_toric(int L, const uint32_t* ex, const uint32_t* ez) {
+    int a1 = 0, a2 = 0, b1 = 0, b2 = 0;
+    for (int i = 0; i < L; ++i) {
+        a1 ^= getb(ex, t_qidx(L, 2 * i + 1, 0));
+        a2 ^= getb(ex, t_qidx(L, 0, 2 * i + 1));
+        b1 ^= getb(ez, t_qidx(L, 1, 2 * i));
+        b2 ^= getb(ez, t_qidx(L, 2 * i, 1));
+    }
+    return a1 + 2 * a2 + 4 * b1 + 8 * b2;
+}
+
+__device__ void pure_error_toric(int L, const uint8_t* s, uint32_t* ex, uint32_t* ez) {
+    const int m = 2 * L;
+    for (int type = 0; type < 2; ++type) {
+        uint32_t* f = type == 0 ? ez : ex;
+        int r0 = -1, c0 = -1;
+        for (int h = 0; h < L * L; ++h) {
+            if (!s[h + type * L * L]) continue;
+            const int r = 2 * (h / L) + type, c = 2 * (h % L) + type;
+            if (r0 < 0) {
+                r0 = r;
+                c0 = c;
+                continue;
+            }
+            for (int cc = c0; cc != c; cc = (cc + 2) % m) flipb(f, t_qidx(L, r0, cc + 1));
+            for (int rr = r0; rr != r; rr = (rr + 2) % m) flipb(f, t_qidx(L, rr + 1, c));
+            r0 = -1;
+        }
+    }
+}
+
+__global__ void start_frames_toric_kernel(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int W = geo_words(1, L);
+    uint32_t ex[kMaxWords], ez[kMaxWords];
+    for (int w = 0; w < W; ++w) ex[w] = ez[w] = 0;
+    pure_error_toric(L, syn + i * 2 * L * L, ex, ez);
+    uint32_t* f = frames + i * 2 * W;
+    for (int w = 0; w < W; ++w) {
+        f[w] = ex[w];
+        f[W + w] = ez[w];
+    }
+    if (code) code[i] = class_code_toric(L, ex, ez);
+}
+
+// Depolarizing errors on the torus: the planar generator's draws per qubit.
+__global__ void gen_syndromes_toric_kernel(RoundKeys rk, uint32_t id0, long long n, int L, uint32_t tau1,
+                                           uint32_t tau2, uint32_t tau3, uint8_t* syn, int32_t* true_class) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nq = 2 * L * L, W = geo_words(1, L);
+    uint32_t ex[kMaxWords], ez[kMaxWords];
+    for (int w = 0; w < W; ++w) ex[w] = ez[w] = 0;
+    const uint32_t id = id0 + (uint32_t)i;
+    for (int q0 = 0; q0 < nq; q0 += 4) {
+        const uint4 b = philox10(make_uint4(id, (uint32_t)(q0 / 4), 0u, 0u), rk);
+        const uint32_t u[4] = {b.x, b.y, b.z, b.w};
+        for (int k = 0; k < 4 && q0 + k < nq; ++k) {
+            if (u[k] < tau2) flipb(ex, q0 + k);
+            if (u[k] >= tau1 && u[k] < tau3) flipb(ez, q0 + k);
+        }
+    }
+    write_syndrome_toric(L, ex, ez, syn + i * 2 * L * L);
+    if (true_class) true_class[i] = class_code_toric(L, ex, ez);
+}
+
+cudaError_t launch_gen_syndromes_toric(uint64_t seed, uint32_t id0, long long n, int L, double p, uint8_t* syn,
+                                       int32_t* true_class, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    RoundKeys rk;
+    make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x53594E44u, &rk);
+    const uint64_t tau = (uint64_t)floor((p / 3.0) * 4294967296.0);
+    gen_syndromes_toric_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(rk, id0, n, L, (uint32_t)tau,
+                                                                           (uint32_t)(2 * tau), (uint32_t)(3 * tau),
+                                                                           syn, true_class);
+    return cudaGetLastError();
+}
+
 __global__ void start_frames_kernel(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -124,7 +217,7 @@ __global__ void decide_kernel(DecideParams p) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n) return;
     const uint64_t* cs = p.chain_sum + i * p.K * p.R;
-    uint64_t S[4];
+    uint64_t S[16];
     int best = 0;
     for (int k = 0; k < p.K; ++k) {
         uint64_t s = 0;
@@ -171,7 +264,7 @@ __global__ void ti_decide_kernel(long long n, int K, int N, double mean0, double
                                  int32_t* out_class, double* out_log_z) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double I[4];
+    double I[16];
     int best = 0;
     for (int k = 0; k < K; ++k) {
         double* m = mean + (i * K + k) * N;
@@ -359,10 +452,13 @@ cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L
 }
 
 cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
-                                cudaStream_t s) {
+                                cudaStream_t s, int toric) {
     if (n == 0) return cudaSuccess;
     const int bs = 128;
-    start_frames_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(syn, n, L, frames, code);
+    if (toric)
+        start_frames_toric_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(syn, n, L, frames, code);
+    else
+        start_frames_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(syn, n, L, frames, code);
     return cudaGetLastError();
 }
 

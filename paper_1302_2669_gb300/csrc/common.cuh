@@ -91,6 +91,52 @@ __host__ __device__ __forceinline__ void colour_support(int L, int col, int m, i
     q[3] = c < n - 1 ? (base + 1) / 2 : dummy;
 }
 
+// ---------------------------------------------------------------------------
+// Geometry of the toric code (16 classes): an L x L torus, L even, on the
+// periodic 2L x 2L grid; 2L^2 qubits at r+c odd with index r L + (c div 2);
+// stars (sigma_x generators) at (even r, even c), plaquettes (sigma_z) at
+// (odd r, odd c), all of weight 4; syndrome layout stars row-major over
+// (r/2, c/2), then plaquettes.  Colours 0/1: stars with (i+j) even/odd,
+// 2/3: plaquettes; within a colour row-major (each row holds L/2).
+// Logicals: X1 on row 1, X2 on column 1 (even rows), Z1 on column 0 (odd
+// rows), Z2 on row 0; class code a1 + 2 a2 + 4 b1 + 8 b2 (a: x parity on
+// Z1 / Z2's qubits, b: z parity on X1 / X2's qubits).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int t_qidx(int L, int r, int c) {
+    const int m = 2 * L;
+    r = ((r % m) + m) % m;
+    c = ((c % m) + m) % m;
+    return r * L + c / 2;
+}
+
+__host__ __device__ __forceinline__ void toric_support(int L, int r, int c, int q[4]) {
+    q[0] = t_qidx(L, r - 1, c);
+    q[1] = t_qidx(L, r + 1, c);
+    q[2] = t_qidx(L, r, c - 1);
+    q[3] = t_qidx(L, r, c + 1);
+}
+
+__host__ __device__ __forceinline__ void toric_colour_support(int L, int col, int m, int q[4]) {
+    const int type = col >> 1, par = col & 1, half = L / 2;
+    const int i = m / half, t = m - i * half;
+    const int j = ((par + i) & 1) + 2 * t;
+    toric_support(L, 2 * i + type, 2 * j + type, q);
+}
+
+// Generator g in the syndrome layout: support and type (0 star, 1 plaquette).
+__host__ __device__ __forceinline__ int toric_generator_support(int L, int g, int q[4]) {
+    const int type = g >= L * L ? 1 : 0;
+    const int h = g - type * L * L, i = h / L, j = h - i * L;
+    toric_support(L, 2 * i + type, 2 * j + type, q);
+    return type;
+}
+
+// Code-dependent counts: code 0 planar, 1 toric.
+__host__ __device__ __forceinline__ int geo_nq(int code, int L) { return code ? 2 * L * L : n_qubits(L); }
+__host__ __device__ __forceinline__ int geo_nstab(int code, int L) { return code ? 2 * L * L : n_stabs(L); }
+__host__ __device__ __forceinline__ int geo_words(int code, int L) { return (geo_nq(code, L) + 31) / 32; }
+__host__ __device__ __forceinline__ int geo_nc(int code, int L) { return code ? L * L / 2 : L * (L - 1) / 2; }
+
 // Shared-memory words of one bundle: X[0..nq+1] then Z[0..nq+1] (two dummy
 // slots each).  The stride is odd so that the bundles of a warp fall on banks
 // of opposite parity: same-colour generators in a row are two qubits apart.
@@ -122,6 +168,7 @@ struct SweepParams {
     int bps, spb;              // bundles per syndrome (G == 32), syndromes per bundle (G < 32)
     uint32_t id0;
     const uint32_t* ids;       // per-syndrome ids (NULL: id0 + global index)
+    int code;                  // 0: planar code (4 classes); 1: toric code (16 classes)
     int scan;                  // 0: colour sweeps; 1: random scan (one random generator per step)
     int noise;                 // 0: depolarizing; 1: independent bit and phase flips
     uint64_t T[33];            // acceptance thresholds T[d] = floor(r*^d 2^32), d <= 32 (random scan)
@@ -175,7 +222,9 @@ cudaError_t launch_gen_syndromes(uint64_t seed, uint32_t id0, long long n, int L
 cudaError_t launch_gen_syndromes_pauli(uint64_t seed, uint32_t id0, long long n, int L, double px, double py,
                                        double pz, uint8_t* syn, int32_t* true_class, cudaStream_t s);
 cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t* frames, int32_t* code,
-                                cudaStream_t s);
+                                cudaStream_t s, int toric = 0);
+cudaError_t launch_gen_syndromes_toric(uint64_t seed, uint32_t id0, long long n, int L, double p, uint8_t* syn,
+                                       int32_t* true_class, cudaStream_t s);
 cudaError_t launch_decide(const DecideParams& p, cudaStream_t s);
 cudaError_t launch_gather_rows(long long n, const uint8_t* src, const long long* src_off, const long long* dst_off,
                                const int32_t* len, const long long* perm, const uint32_t* ids, uint32_t id0,

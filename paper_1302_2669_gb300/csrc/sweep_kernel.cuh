@@ -391,13 +391,20 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
 
     // Start state: pure error times the logical that gives chain c the class
     // code c / R (bit 0: X-bar on row 0, bit 1: Z-bar on column 0).
-    uint32_t lx = 0, lzm = 0;
+    // (toric code: 4 logical bits X1, X2, Z1, Z2)
+    uint32_t lx = 0, lzm = 0, lx2 = 0, lz2 = 0;
     for (int b = 0; b < 32 && !p.init_frames && !p.state_in; ++b) {
         if (!((valid >> b) & 1u)) continue;
         const int k = chain_of(b) / p.R;
         const int l = k ^ p.e0code[syn_of(b)];
         lx |= (uint32_t)(l & 1) << b;
-        lzm |= (uint32_t)((l >> 1) & 1) << b;
+        if (p.code) {
+            lx2 |= (uint32_t)((l >> 1) & 1) << b;
+            lzm |= (uint32_t)((l >> 2) & 1) << b;
+            lz2 |= (uint32_t)((l >> 3) & 1) << b;
+        } else {
+            lzm |= (uint32_t)((l >> 1) & 1) << b;
+        }
     }
     const int W = gd.W;
     // per-item arrays of the group: pure errors and frames are laid out per group
@@ -429,8 +436,16 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                 if ((e[q >> 5] >> (q & 31)) & 1u) xw |= vm;
                 if ((e[W + (q >> 5)] >> (q & 31)) & 1u) zw |= vm;
             }
-            if (q < L) xw ^= lx;                  // row-0 qubits: X-bar
-            if (q % (2 * L - 1) == 0) zw ^= lzm;  // column-0 qubits: Z-bar
+            if (!p.code) {
+                if (q < L) xw ^= lx;                  // row-0 qubits: X-bar
+                if (q % (2 * L - 1) == 0) zw ^= lzm;  // column-0 qubits: Z-bar
+            } else {
+                const int r = q / L;
+                if (r == 1) xw ^= lx;                       // X1: row 1
+                if (q % L == 0 && !(r & 1)) xw ^= lx2;      // X2: column 1, even rows
+                if (q % L == 0 && (r & 1)) zw ^= lzm;       // Z1: column 0, odd rows
+                if (r == 0) zw ^= lz2;                      // Z2: row 0
+            }
         }
         X[q] = xw;
         Z[q] = zw;
@@ -467,7 +482,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
         const uint32_t bit = 1u << b;
         const uint32_t my_sid = sid[G == 32 ? 0 : b / G];
         const uint32_t chain = (uint32_t)chain_of(b);
-        const int ns = 2 * L * (L - 1);
+        const int ns = geo_nstab(p.code, L);
         // energy of a qubit's Pauli, index x + 2z (I, X, Z, Y): the noise
         // model's table (depolarizing 0 1 1 1, flips 0 1 1 2, general)
         const int E0 = p.energy[0], E1 = p.energy[1], E2 = p.energy[2], E3 = p.energy[3];
@@ -481,7 +496,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                 const uint4 r = philox10(make_uint4(my_sid, chain, t, (uint32_t)step), p.rk);
                 const int g = (int)__umulhi(r.x, (uint32_t)ns);
                 int q[4];
-                const int type = generator_support(L, g, q);
+                const int type = p.code ? toric_generator_support(L, g, q) : generator_support(L, g, q);
                 uint32_t* own = type == 0 ? X : Z;
                 const uint32_t* oth = type == 0 ? Z : X;
                 int dn = 0;
@@ -664,7 +679,8 @@ __global__ void __launch_bounds__(128, (G >= 16 ? 5 : 3)) sweep_kernel(const __g
             for (int idx = threadIdx.x; idx < 4 * gd.nc; idx += blockDim.x) {
                 const int col = idx / gd.nc, m = idx - col * gd.nc;
                 int q[4];
-                colour_support(gd.L, col, m, q);
+                if (p.code) toric_colour_support(gd.L, col, m, q);
+                else colour_support(gd.L, col, m, q);
                 tab[idx] = make_ushort4((unsigned short)q[0], (unsigned short)q[1], (unsigned short)q[2],
                                         (unsigned short)q[3]);
             }
