@@ -108,7 +108,7 @@ __device__ __forceinline__ uint32_t bit_of(const uint32_t cnt[kCountBits], int b
 // counter of kAccHi planes).  Each lane accumulates only its own slice of the
 // qubits; the slices of a bundle's LAM lanes are added together only when the
 // accumulator is flushed into the chains' 64-bit sums.
-constexpr int kAccHi = 10;
+constexpr int kAccHi = 8;
 constexpr uint32_t kAccCapacity = 8u * (1u << kAccHi) - 1u;
 constexpr int kFlushPlanes = 3 + kAccHi + 5;  // + butterfly growth over <= 32 lanes
 
@@ -660,7 +660,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
 // the host arranged (largest work first), and rebuilds the support table in
 // shared memory when the group's code size changes.
 template <int G, int LAM, bool SCAN, bool IND>
-__global__ void __launch_bounds__(128, (G >= 16 ? 5 : 3)) sweep_kernel(const __grid_constant__ SweepParams p) {
+__global__ void __launch_bounds__(128, (G >= 16 ? 6 : 3)) sweep_kernel(const __grid_constant__ SweepParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ long long s_unit;
     ushort4* tab = reinterpret_cast<ushort4*>(smem);
