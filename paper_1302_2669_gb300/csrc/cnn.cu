@@ -12,23 +12,30 @@
 // independent flips P(odd) = (1 - M)/2, M = prod(-tanh(s/2)) clipped to
 // +-(1 - 1e-6), and log p_{a + 2b} = log P_x(a xor a0) + log P_z(b xor b0).
 //
-// Layouts: activations are NHWC bfloat16, [M][C] with M = n L^2 positions
-// (syndrome-major, then row, then column).  Weights live as float32 master
+// Layouts: activations are NHWC bfloat16, [M][C] with M = n P^2 positions of
+// the maps zero-padded to P = L + 2 (syndrome-major, then row, then column):
+// every 3x3 tap is then a shift of the position index by dy P + dx, and the
+// epilogues keep the one-position border at zero.  Weights live as float32 master
 // copies in the flat order W[co][kh][kw][ci] then b[co], layer after layer;
 // every step packs them into bfloat16 GEMM operands.
 //
 // Tensor-core work (tcgen05, BF16 in, FP32 accumulate in tensor memory):
-//   forward conv and input-gradient conv: an implicit GEMM, M = positions in
-//     tiles of 128, N = output channels, K = 9 C_in taken one 3x3 tap (64
-//     channels) per pipeline stage; the weight operand stays in shared memory
-//     for the whole persistent block; warps 0-3 gather the shifted activation
-//     rows, warp 8 issues the MMAs, warps 4-7 drain the two tensor-memory
-//     accumulators (bias + ReLU, or the ReLU mask of the layer below);
+//   forward conv and input-gradient conv (64 input channels): an implicit
+//     GEMM, M = positions in tiles of 128, N = output channels, K = 9 x 64
+//     taken one 3x3 tap per pipeline stage; a tap's operand is 128 shifted
+//     position rows, loaded by one TMA tiled copy (128-byte swizzle) from
+//     one thread; the weight operand stays in shared memory for the whole
+//     persistent block; one thread issues the MMAs, four warps drain the two
+//     tensor-memory accumulators (bias + ReLU, logits, or the ReLU gate of
+//     the layer below).  The first layer (2 input channels, K = 18 padded to
+//     32) gathers its operand with producer warps;
 //   weight gradient: D[(tap, ci)][co] = sum_p X[p + tap][ci] dZ[p][co], a
 //     GEMM over positions split across blocks, with a row of ones that yields
 //     the bias gradient; partial sums are added in a fixed order.
 // The last layer's backward (2 outputs, gradient nonzero on the middle lines
 // only), the readout, loss and Adam steps run on the CUDA cores.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -49,7 +56,7 @@ typedef __nv_bfloat16 bf16;
 constexpr int kHid = 64;          // hidden channels
 constexpr int kOut = 2;           // flip logits per position (last layer)
 constexpr float kClip = 1e-6f;    // |M| <= 1 - kClip
-constexpr int kConvProd = 8;      // gather warps of the conv kernel
+constexpr int kConvProd = 8;      // gather warps of the first layer's conv kernel
 constexpr int kWgProd = 8;        // gather warps of the weight-gradient kernel
 constexpr int kEpiWarps = 4;      // accumulator-draining warps
 constexpr int kConvThreads = (kConvProd + kEpiWarps + 1) * 32;
@@ -57,6 +64,8 @@ constexpr int kWgThreads = (kWgProd + kEpiWarps + 1) * 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWaitTimeout = 1;   // error codes written to the device flag
 constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
+constexpr int kTmaStages = 6;     // tap tiles in flight in the TMA conv kernel
+constexpr int kTmaThreads = 6 * 32;  // TMA warp, MMA warp, 4 accumulator warps
 
 // Channels of the five layers and the offsets of their weights and biases in
 // the flat parameter vector.
@@ -179,6 +188,50 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// Shared-memory descriptor of a K-major tile written by TMA with the 128-byte
+// swizzle: rows of 128 bytes (64 bf16 of K), atoms of 8 rows (1024 bytes, the
+// stride between 8-row groups); the K step of an MMA (16 elements) advances
+// the start address by 32 bytes inside the atom.  The tile must start on a
+// 1024-byte boundary.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// The transaction count the barrier's current phase waits for, then this
+// thread's arrival.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA tiled load of box (c0, c1) of a 2-D tensor map into shared memory,
+// completing on the barrier (rows outside the tensor read as zero).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Padded maps: P = L + 2, position m of a batch; interior positions are the
+// L x L map, the rest is the zero border.
+__device__ __forceinline__ bool interior(long long m, int L) {
+    const int P = L + 2, PP = P * P;
+    const int rem = (int)(m % PP), y = rem / P, x = rem - (rem / P) * P;
+    return y >= 1 && y <= L && x >= 1 && x <= L;
+}
+
+// Position shift of tap t = 3 kh + kw: (kh - 1) P + (kw - 1).
+__device__ __forceinline__ int tap_shift(int t, int L) { return (t / 3 - 1) * (L + 2) + (t % 3 - 1); }
+
 // 16 consecutive f32 columns of this warp's 32 tensor-memory lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];
@@ -202,63 +255,46 @@ __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w 
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
 // ---------------------------------------------------------------------------
-// Implicit-GEMM 3x3 conv on tcgen05 (forward and input gradient).
+// Implicit-GEMM 3x3 conv of the first layer on tcgen05.
 // ---------------------------------------------------------------------------
-enum Epi { kEpiRelu = 0, kEpiLogit = 1, kEpiMask = 2 };
-
 struct ConvArgs {
-    const bf16* act;     // [M][CIN] input of the conv
-    const bf16* wmat;    // [NP][KP] operand B (k = tap * CIN + ci)
-    const float* bias;   // [NP] (kEpiRelu, kEpiLogit) or NULL
-    const bf16* mask;    // [M][64] ReLU gate (kEpiMask) or NULL
-    bf16* out_bf16;      // [M][64] (kEpiRelu, kEpiMask)
-    float* out_f32;      // [M][2]  (kEpiLogit)
-    long long M;
+    const bf16* act;     // [M][2] input maps (padded)
+    const bf16* wmat;    // [64][32] operand B (k = tap * 2 + ci, zero from k = 18)
+    const float* bias;   // [64]
+    bf16* out_bf16;      // [M][64]
+    long long M;         // positions n P^2
     int L;
     int* err;
 };
 
-template <int CIN>
-struct ConvShape {
-    static constexpr int KP = CIN == 2 ? 32 : 9 * CIN;   // K of the GEMM, padded
-    static constexpr int KC = CIN == 2 ? 32 : CIN;       // K per pipeline stage (one tap)
-    static constexpr int NCH = KP / KC;                  // stages per tile
-    static constexpr int KGS = KC / 8;                   // 16-byte groups per stage row
-    static constexpr int KG = KP / 8;                    // 16-byte groups per B row
-    static constexpr int STAGE_BYTES = 128 * KC * 2;
-    static constexpr int S = 4;                          // pipeline depth
-};
+constexpr int kC1KP = 32;                      // K of the first layer: 9 taps x 2 channels, padded
+constexpr int kC1Stage = 128 * kC1KP * 2;      // one tile's operand
+constexpr int kC1S = 4;                        // pipeline depth
+constexpr size_t kC1Smem = (size_t)64 * kC1KP * 2 + kC1S * kC1Stage + 1024;
 
-template <int CIN, int NP>
-constexpr size_t conv_smem_bytes() {
-    return (size_t)((NP * ConvShape<CIN>::KP * 2 + 1023) / 1024 * 1024) +
-           (size_t)ConvShape<CIN>::S * ConvShape<CIN>::STAGE_BYTES + 1024;
-}
-
-template <int CIN, int NP, int EPI>
-__global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
-    typedef ConvShape<CIN> Sh;
-    constexpr int S = Sh::S;
-    constexpr uint32_t NCOLS = 2 * NP < 32 ? 32 : 2 * NP;
+// First layer (2 input channels): producer warps gather the 18 values of a
+// position's 3x3 neighbourhood (one 32-bit pair per tap) into the operand.
+__global__ void __launch_bounds__(kConvThreads, 1) conv1_kernel(ConvArgs a) {
+    constexpr int S = kC1S, KGS = kC1KP / 8, NP = 64;
+    constexpr uint32_t NCOLS = 2 * NP;
     constexpr uint32_t IDESC = idesc_bf16(128, NP);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sB = smem;
-    uint8_t* sA = smem + (NP * Sh::KP * 2 + 1023) / 1024 * 1024;
+    uint8_t* sA = smem + NP * kC1KP * 2;
     __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
-    const int L = a.L, LL = L * L;
+    const int L = a.L;
     const long long n_tiles = (M + 127) / 128;
 
-    // resident weight operand
-    for (int idx = tid; idx < NP * Sh::KG; idx += kConvThreads) {
-        const int r = idx / Sh::KG, g = idx - r * Sh::KG;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.wmat + (size_t)r * Sh::KP) + g);
-        *reinterpret_cast<uint4*>(sB + core_off(r, g, Sh::KG)) = v;
+    for (int idx = tid; idx < NP * KGS; idx += kConvThreads) {
+        const int r = idx / KGS, g = idx - r * KGS;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.wmat + (size_t)r * kC1KP) + g);
+        *reinterpret_cast<uint4*>(sB + core_off(r, g, KGS)) = v;
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -281,89 +317,41 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
     const uint32_t tmem = tmem_slot;
 
     if (warp < kConvProd) {
-        // ---------------- gather: tap c of the tile's 128 positions --------
-        // warp w covers rows 32 (w mod 4) .. +31; the two halves of the
-        // producers split the 16-byte groups of a row.  All loads of a stage
-        // are issued before its slot is awaited and written.
-        const int rowblock = warp & 3, half = warp >> 2;
+        // warp w covers rows 32 (w mod 4) .. +31; a thread loads group g =
+        // taps 4g .. 4g+3 of rows 2 half, 2 half + 1 of its 8-row blocks
+        const int rowblock = warp & 3, half = warp >> 2, g = lane >> 3;
         uint32_t q = 0;
         bool ok = true;
-        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-            constexpr int ROWS = 4;  // rows per thread
-            int ry[ROWS], rx[ROWS];
-            long long rm[ROWS];
+        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++q) {
+            const uint32_t stage = q % S, use = q / S;
+            uint4 v[2];
 #pragma unroll
-            for (int i = 0; i < ROWS; ++i) {
-                const int r = rowblock * 32 + (lane & 7) + 8 * i;
-                const long long m = tile * 128 + r;
-                rm[i] = m;
-                if (m < M) {
-                    const int rem = (int)(m % LL);
-                    ry[i] = rem / L;
-                    rx[i] = rem - ry[i] * L;
-                } else {
-                    ry[i] = -1000;  // every neighbour out of range
-                    rx[i] = -1000;
+            for (int k = 0; k < 2; ++k) {
+                const long long m = tile * 128 + rowblock * 32 + (lane & 7) + 8 * (2 * half + k);
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int t = 4 * g + j;
+                    const long long src = m + tap_shift(t, L);
+                    w[j] = (t < 9 && m < M && src >= 0 && src < M)
+                               ? __ldg(reinterpret_cast<const uint32_t*>(a.act) + src) : 0u;
                 }
+                v[k] = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            for (int c = 0; c < Sh::NCH; ++c, ++q) {
-                const uint32_t stage = q % S, use = q / S;
-                uint4 v[4];
-                if (CIN == 2) {
-                    // K = 18 (9 taps x 2 channels) padded to 32: group g
-                    // holds taps 4g..4g+3; this thread: rows 2 half, 2 half + 1
-                    const int g = lane >> 3;
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const int yk = half ? ry[2 + k] : ry[k], xk = half ? rx[2 + k] : rx[k];
-                        const long long mk = half ? rm[2 + k] : rm[k];
-                        uint32_t w[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int t = 4 * g + j;
-                            const int dy = t / 3 - 1, dx = t % 3 - 1;
-                            const int yy = yk + dy, xx = xk + dx;
-                            w[j] = 0;
-                            if (t < 9 && yy >= 0 && yy < L && xx >= 0 && xx < L)
-                                w[j] = __ldg(reinterpret_cast<const uint32_t*>(a.act) + mk + dy * L + dx);
-                        }
-                        v[k] = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
-                } else {
-                    const int dy = c / 3 - 1, dx = c % 3 - 1;
-                    const int g = half * 4 + (lane >> 3);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int yy = ry[i] + dy, xx = rx[i] + dx;
-                        v[i] = make_uint4(0, 0, 0, 0);
-                        if (yy >= 0 && yy < L && xx >= 0 && xx < L)
-                            v[i] = __ldg(reinterpret_cast<const uint4*>(a.act + (rm[i] + dy * L + dx) * CIN) + g);
-                    }
-                }
-                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t* st = sA + stage * Sh::STAGE_BYTES;
-                if (CIN == 2) {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const int r = rowblock * 32 + (lane & 7) + 8 * (2 * half + k);
-                        *reinterpret_cast<uint4*>(st + core_off(r, lane >> 3, Sh::KGS)) = v[k];
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = rowblock * 32 + (lane & 7) + 8 * i;
-                        *reinterpret_cast<uint4*>(st + core_off(r, half * 4 + (lane >> 3), Sh::KGS)) = v[i];
-                    }
-                }
-                fence_async_smem();
-                mbar_arrive(&full[stage]);
+            if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) {
+                ok = false;
+                break;
             }
+            uint8_t* st = sA + stage * kC1Stage;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = rowblock * 32 + (lane & 7) + 8 * (2 * half + k);
+                *reinterpret_cast<uint4*>(st + core_off(r, g, KGS)) = v[k];
+            }
+            fence_async_smem();
+            mbar_arrive(&full[stage]);
         }
     } else if (warp < kConvProd + kEpiWarps) {
-        // ---------------- drain the accumulators ---------------------------
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
         uint32_t it = 0;
@@ -373,13 +361,194 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
             if (!ok) break;
             tc_fence_after();
             const long long m = tile * 128 + row;
+            const bool keep = m < M && interior(m, L);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
+#pragma unroll
+            for (int cc = 0; cc < NP / 16; ++cc) {
+                float v[16];
+                tmem_ld16(taddr + cc * 16, v);
+                if (m < M) {
+                    uint32_t w[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float x0 = keep ? fmaxf(v[2 * j] + __ldg(a.bias + cc * 16 + 2 * j), 0.0f) : 0.0f;
+                        const float x1 = keep ? fmaxf(v[2 * j + 1] + __ldg(a.bias + cc * 16 + 2 * j + 1), 0.0f) : 0.0f;
+                        w[j] = pack_bf16(x0, x1);
+                    }
+                    uint4* op = reinterpret_cast<uint4*>(a.out_bf16 + m * 64 + cc * 16);
+                    op[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    op[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[b]);
+        }
+    } else if (lane == 0) {
+        uint32_t it = 0;
+        bool ok = true;
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+            const uint32_t b = it & 1, u = it >> 1;
+            if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
+            tc_fence_after();
+            const uint32_t stage = it % S, use = it / S;
+            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < kC1KP / 16; ++ks) {
+                const uint64_t ad = smem_desc(a0 + stage * kC1Stage + ks * 256, 128, KGS * 128);
+                const uint64_t bd = smem_desc(b0 + ks * 256, 128, KGS * 128);
+                mma_bf16(tmem + b * NP, ad, bd, IDESC, ks > 0 ? 1u : 0u);
+            }
+            mma_commit(&empty[stage]);
+            mma_commit(&accf[b]);
+        }
+        mma_commit(&fin);
+        mbar_drain(&fin, 0, a.err);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kConvProd + kEpiWarps) tmem_dealloc(tmem, NCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// Convolutions with 64 input channels: tap operands by TMA.
+// ---------------------------------------------------------------------------
+enum Epi { kEpiRelu = 0, kEpiLogit = 1, kEpiMask = 2 };
+
+struct alignas(64) ConvTmaArgs {
+    CUtensorMap map;     // input [M_alloc][64] bf16, box 64 x 128, 128-byte swizzle
+    const bf16* wmat;    // [NP][576] operand B (k = tap * 64 + ci)
+    const float* bias;   // [NP] (kEpiRelu, kEpiLogit) or NULL
+    const bf16* mask;    // [M][64] ReLU gate (kEpiMask) or NULL
+    bf16* out_bf16;      // [M][64] (kEpiRelu, kEpiMask)
+    float* out_f32;      // [M][2]  (kEpiLogit)
+    long long M;         // positions n P^2
+    int L;
+    int* err;
+};
+
+constexpr int kTmaTile = 128 * 64 * 2;   // one tap's operand, 16 KB
+
+template <int NP>
+constexpr size_t conv_tma_smem_bytes() {
+    return (size_t)kTmaStages * kTmaTile + (size_t)NP * 576 * 2 + 1024;
+}
+
+// Warp 0 (one thread) loads the 9 tap tiles of each position tile by TMA
+// into a ring of stages; warp 1 (one thread) issues 4 MMAs per tap (K = 16
+// each) into one of two accumulators; warps 2-5 drain the accumulators.
+template <int NP, int EPI>
+__global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_constant__ ConvTmaArgs a) {
+    constexpr int S = kTmaStages, KG = 576 / 8;
+    constexpr uint32_t NCOLS = 2 * NP < 32 ? 32 : 2 * NP;
+    constexpr uint32_t IDESC = idesc_bf16(128, NP);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;                      // S tiles of 16 KB, 1024-byte aligned
+    uint8_t* sB = smem + S * kTmaTile;
+    __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = a.M;
+    const int L = a.L;
+    const long long n_tiles = (M + 127) / 128;
+
+    for (int idx = tid; idx < NP * KG; idx += kTmaThreads) {
+        const int r = idx / KG, g = idx - r * KG;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.wmat + (size_t)r * 576) + g);
+        *reinterpret_cast<uint4*>(sB + core_off(r, g, KG)) = v;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], kEpiWarps * 32);
+        }
+        mbar_init(&fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();
+    if (warp == 1) tmem_alloc(&tmem_slot, NCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t q = 0;
+            bool ok = true;
+            for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                for (int c = 0; c < 9; ++c, ++q) {
+                    const uint32_t stage = q % S, use = q / S;
+                    if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[stage], kTmaTile);
+                    tma_load_2d(sA + stage * kTmaTile, &a.map, 0, (int)(tile * 128 + tap_shift(c, L)), &full[stage]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t q = 0, it = 0;
+            bool ok = true;
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+                const uint32_t b = it & 1, u = it >> 1;
+                if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + b * NP;
+                for (int c = 0; c < 9; ++c, ++q) {
+                    const uint32_t stage = q % S, use = q / S;
+                    if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t ad = smem_desc_sw128(a0 + stage * kTmaTile + ks * 32);
+                        const uint64_t bd = smem_desc(b0 + (c * 8 + ks * 2) * 128, 128, KG * 128);
+                        mma_bf16(d, ad, bd, IDESC, (c > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[stage]);
+                }
+                if (ok) mma_commit(&accf[b]);
+            }
+            mma_commit(&fin);
+            mbar_drain(&fin, 0, a.err);
+        }
+    } else {
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        uint32_t it = 0;
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            const uint32_t b = it & 1, u = it >> 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[b], u & 1, &abort_flag, a.err));
+            if (!ok) break;
+            tc_fence_after();
+            const long long m = tile * 128 + row;
+            const bool keep = m < M && interior(m, L);
             const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
             if (EPI == kEpiLogit) {
                 float v[16];
                 tmem_ld16(taddr, v);
                 if (m < M)
                     *reinterpret_cast<float2*>(a.out_f32 + m * 2) =
-                        make_float2(v[0] + __ldg(a.bias + 0), v[1] + __ldg(a.bias + 1));
+                        keep ? make_float2(v[0] + __ldg(a.bias + 0), v[1] + __ldg(a.bias + 1)) : make_float2(0.f, 0.f);
             } else {
 #pragma unroll
                 for (int cc = 0; cc < NP / 16; ++cc) {
@@ -390,8 +559,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
                         if (EPI == kEpiRelu) {
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
-                                const float x0 = fmaxf(v[2 * j] + __ldg(a.bias + cc * 16 + 2 * j), 0.0f);
-                                const float x1 = fmaxf(v[2 * j + 1] + __ldg(a.bias + cc * 16 + 2 * j + 1), 0.0f);
+                                const float x0 = keep ? fmaxf(v[2 * j] + __ldg(a.bias + cc * 16 + 2 * j), 0.0f) : 0.0f;
+                                const float x1 =
+                                    keep ? fmaxf(v[2 * j + 1] + __ldg(a.bias + cc * 16 + 2 * j + 1), 0.0f) : 0.0f;
                                 w[j] = pack_bf16(x0, x1);
                             }
                         } else {
@@ -400,8 +570,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
                             const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
-                                const float x0 = bf16_lo(mw[j]) > 0.0f ? v[2 * j] : 0.0f;
-                                const float x1 = bf16_hi(mw[j]) > 0.0f ? v[2 * j + 1] : 0.0f;
+                                const float x0 = keep && bf16_lo(mw[j]) > 0.0f ? v[2 * j] : 0.0f;
+                                const float x1 = keep && bf16_hi(mw[j]) > 0.0f ? v[2 * j + 1] : 0.0f;
                                 w[j] = pack_bf16(x0, x1);
                             }
                         }
@@ -414,41 +584,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(ConvArgs a) {
             tc_fence_before();
             mbar_arrive(&acce[b]);
         }
-    } else if (lane == 0) {
-        // ---------------- MMA issue ----------------------------------------
-        uint32_t q = 0, it = 0;
-        bool ok = true;
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
-            const uint32_t b = it & 1, u = it >> 1;
-            if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
-            tc_fence_after();
-            const uint32_t d = tmem + b * NP;
-            for (int c = 0; c < Sh::NCH; ++c, ++q) {
-                const uint32_t stage = q % S, use = q / S;
-                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-#pragma unroll
-                for (int ks = 0; ks < Sh::KC / 16; ++ks) {
-                    const uint64_t ad = smem_desc(a0 + stage * Sh::STAGE_BYTES + ks * 256, 128, Sh::KGS * 128);
-                    const uint64_t bd = smem_desc(b0 + (c * Sh::KGS + ks * 2) * 128, 128, Sh::KG * 128);
-                    mma_bf16(d, ad, bd, IDESC, (c > 0 || ks > 0) ? 1u : 0u);
-                }
-                mma_commit(&empty[stage]);
-            }
-            if (ok) mma_commit(&accf[b]);
-        }
-        // every MMA of this block has completed before the memory is released
-        mma_commit(&fin);
-        mbar_drain(&fin, 0, a.err);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kConvProd + kEpiWarps) tmem_dealloc(tmem, NCOLS);
+    if (warp == 1) tmem_dealloc(tmem, NCOLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -522,11 +662,10 @@ __global__ void __launch_bounds__(kWgThreads, 2) wgrad_kernel(WgradArgs a) {
     __shared__ __align__(8) uint64_t full[kWgS], empty[kWgS], accf;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ int pos_yx[kWgProd][64];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
-    const int L = a.L, LL = L * L;
+    const int L = a.L;
     const long long n_chunks = (M + 63) / 64;
     const int slice = blockIdx.x, n_slices = gridDim.x, mt = blockIdx.y;
     const long long c_begin = n_chunks * slice / n_slices, c_end = n_chunks * (slice + 1) / n_slices;
@@ -558,18 +697,6 @@ __global__ void __launch_bounds__(kWgThreads, 2) wgrad_kernel(WgradArgs a) {
             const uint32_t stage = q % kWgS, use = q / kWgS;
             if (use > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)))
                 break;  // warp-uniform: the loop below has warp-wide shuffles
-            // positions of this chunk: (y << 8) | x, or -1 past the end
-            for (int j = lane; j < 64; j += 32) {
-                const long long p = ch * 64 + j;
-                int v = -1;
-                if (p < M) {
-                    const int rem = (int)(p % LL);
-                    const int y = rem / L;
-                    v = (y << 8) | (rem - y * L);
-                }
-                pos_yx[warp][j] = v;
-            }
-            __syncwarp();
             uint8_t* stA = sA + stage * kWgAStage;
             uint8_t* stB = sB + stage * kWgBStage;
             if constexpr (CIN == 64) {
@@ -577,15 +704,14 @@ __global__ void __launch_bounds__(kWgThreads, 2) wgrad_kernel(WgradArgs a) {
                 for (int pass = 0; pass < 128 / kGroups; ++pass) {
                     const int b = grp + kGroups * pass, rg = b >> 3, pg = b & 7;
                     const int R0 = mt * 128 + rg * 8, j = pg * 8 + l8;
-                    const int yx = pos_yx[warp][j];
+                    const long long pos = ch * 64 + j;
                     uint4 v = make_uint4(0, 0, 0, 0);
                     if (R0 < 9 * CIN) {
                         const int tap = R0 / CIN, ci0 = R0 % CIN;
-                        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-                        const int yy = (yx >> 8) + dy, xx = (yx & 255) + dx;
-                        if (yx >= 0 && yy >= 0 && yy < L && xx >= 0 && xx < L)
-                            v = __ldg(reinterpret_cast<const uint4*>(a.x + (ch * 64 + j + dy * L + dx) * CIN + ci0));
-                    } else if (R0 == 9 * CIN && yx >= 0) {
+                        const long long src = pos + tap_shift(tap, L);
+                        if (pos < M && src >= 0 && src < M)
+                            v = __ldg(reinterpret_cast<const uint4*>(a.x + src * CIN + ci0));
+                    } else if (R0 == 9 * CIN && pos < M) {
                         v.x = 0x3F80u;  // row 9 CIN: 1.0 (bias gradient)
                     }
                     v = transpose8(v, l8);
@@ -603,16 +729,13 @@ __global__ void __launch_bounds__(kWgThreads, 2) wgrad_kernel(WgradArgs a) {
                             uint32_t e[2];
 #pragma unroll
                             for (int k = 0; k < 2; ++k) {
-                                const int j = g * 8 + h * 2 + k;
-                                const int yx = pos_yx[warp][j];
+                                const long long pos = ch * 64 + g * 8 + h * 2 + k;
                                 uint32_t val = 0;
-                                if (yx >= 0) {
+                                if (pos < M) {
                                     if (R < 9 * CIN) {
                                         const int tap = R / CIN, ci = R % CIN;
-                                        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-                                        const int yy = (yx >> 8) + dy, xx = (yx & 255) + dx;
-                                        if (yy >= 0 && yy < L && xx >= 0 && xx < L)
-                                            val = __ldg(xs + (ch * 64 + j + dy * L + dx) * CIN + ci);
+                                        const long long src = pos + tap_shift(tap, L);
+                                        if (src >= 0 && src < M) val = __ldg(xs + src * CIN + ci);
                                     } else {
                                         val = 0x3F80u;
                                     }
@@ -628,13 +751,12 @@ __global__ void __launch_bounds__(kWgThreads, 2) wgrad_kernel(WgradArgs a) {
 #pragma unroll
             for (int pass = 0; pass < 64 / kGroups; ++pass) {
                 const int b = grp + kGroups * pass, cg = b >> 3, pg = b & 7;
-                const int j = pg * 8 + l8;
+                const long long pos = ch * 64 + pg * 8 + l8;
                 uint4 v = make_uint4(0, 0, 0, 0);
-                if (pos_yx[warp][j] >= 0) v = __ldg(reinterpret_cast<const uint4*>(a.dz + (ch * 64 + j) * 64 + cg * 8));
+                if (pos < M) v = __ldg(reinterpret_cast<const uint4*>(a.dz + pos * 64 + cg * 8));
                 v = transpose8(v, l8);
                 *reinterpret_cast<uint4*>(stB + core_off(cg * 8 + l8, pg, 8)) = v;
             }
-            __syncwarp();  // pos_yx is rewritten by the next chunk
             fence_async_smem();
             mbar_arrive(&full[stage]);
         }
@@ -703,18 +825,22 @@ __global__ void wgrad_reduce_kernel(const float* partial, int n_slices, int rows
 // CUDA-core kernels
 // ---------------------------------------------------------------------------
 
-// Syndromes [n][2L(L-1)] -> input maps [n L^2][2]: channel 0 the sigma_x
-// generators ((L-1) x L, last row zero), channel 1 the sigma_z generators
-// (L x (L-1), last column zero).
+// Syndromes [n][2L(L-1)] -> padded input maps [n P^2][2]: channel 0 the
+// sigma_x generators ((L-1) x L, last row zero), channel 1 the sigma_z
+// generators (L x (L-1), last column zero); map (y, x) at padded (y+1, x+1).
 __global__ void input_maps_kernel(const uint8_t* syn, long long n, int L, bf16* x0) {
     const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long LL = (long long)L * L;
-    if (m >= n * LL) return;
-    const long long item = m / LL;
-    const int rem = (int)(m - item * LL), y = rem / L, x = rem - (rem / L) * L;
-    const uint8_t* s = syn + item * 2 * L * (L - 1);
-    const float c0 = y < L - 1 ? (float)(s[y * L + x] & 1) : 0.0f;
-    const float c1 = x < L - 1 ? (float)(s[L * (L - 1) + y * (L - 1) + x] & 1) : 0.0f;
+    const int P = L + 2;
+    const long long PP = (long long)P * P;
+    if (m >= n * PP) return;
+    const long long item = m / PP;
+    const int rem = (int)(m - item * PP), y = rem / P - 1, x = rem - (rem / P) * P - 1;
+    float c0 = 0.0f, c1 = 0.0f;
+    if (y >= 0 && y < L && x >= 0 && x < L) {
+        const uint8_t* s = syn + item * 2 * L * (L - 1);
+        c0 = y < L - 1 ? (float)(s[y * L + x] & 1) : 0.0f;
+        c1 = x < L - 1 ? (float)(s[L * (L - 1) + y * (L - 1) + x] & 1) : 0.0f;
+    }
     reinterpret_cast<uint32_t*>(x0)[m] = pack_bf16(c0, c1);
 }
 
@@ -771,12 +897,12 @@ __global__ void readout_kernel(const float* z5, const uint8_t* syn, long long n,
     const long long item = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (item >= n) return;
-    const int m = (L - 1) / 2;
-    const long long base = item * L * L;
+    const int m = (L - 1) / 2, P = L + 2;
+    const long long base = item * P * P + P + 1;   // map (0, 0)
     float sa = 0.0f, sb = 0.0f, ta = 1.0f, tb = 1.0f;
     if (lane < L) {
-        sa = z5[(base + (long long)lane * L + m) * 2 + 0];
-        sb = z5[(base + (long long)m * L + lane) * 2 + 1];
+        sa = z5[(base + (long long)lane * P + m) * 2 + 0];
+        sb = z5[(base + (long long)m * P + lane) * 2 + 1];
         ta = -tanhf(0.5f * sa);
         tb = -tanhf(0.5f * sb);
     }
@@ -824,8 +950,8 @@ __global__ void readout_kernel(const float* z5, const uint8_t* syn, long long n,
     const float dMb = inb ? gb[0] / (1.0f + Mb) - gb[1] / (1.0f - Mb) : 0.0f;
     const float oa = warp_prod_except(ta, lane), ob = warp_prod_except(tb, lane);
     if (lane < L) {
-        dz5[(base + (long long)lane * L + m) * 2 + 0] = dMa * oa * (-0.5f * (1.0f - ta * ta));
-        dz5[(base + (long long)m * L + lane) * 2 + 1] = dMb * ob * (-0.5f * (1.0f - tb * tb));
+        dz5[(base + (long long)lane * P + m) * 2 + 0] = dMa * oa * (-0.5f * (1.0f - ta * ta));
+        dz5[(base + (long long)m * P + lane) * 2 + 1] = dMb * ob * (-0.5f * (1.0f - tb * tb));
     }
 }
 
@@ -843,24 +969,20 @@ __global__ void loss_sum_kernel(const float* loss_item, long long n, float* loss
     if (threadIdx.x == 0) *loss = part[0] / (float)n;
 }
 
-// Input gradient of the last layer, gated by the ReLU of layer 4:
-// dZ4[q][ci] = [a4[q][ci] > 0] sum over taps (kh, kw) with p = q - (kh-1,
-// kw-1) inside the map of sum_co W5[co][kh][kw][ci] dz5[p][co].
+// Input gradient of the last layer, gated by the ReLU of layer 4 (padded
+// maps; the border of dz5 is zero): dZ4[q][ci] = [a4[q][ci] > 0] sum over
+// taps t of sum_co W5[co][t][ci] dz5[q - shift(t)][co] for interior q, and 0
+// on the border.
 __global__ void conv5_dgrad_kernel(const bf16* w5, const float* dz5, const bf16* a4, long long M, int L,
                                    bf16* dz4) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // m * 8 + ci group
     if (i >= M * 8) return;
     const long long m = i >> 3;
     const int cg = (int)(i & 7) * 8;
-    const int LL = L * L;
-    const long long item = m / LL;
-    const int rem = (int)(m - item * LL), y = rem / L, x = rem - (rem / L) * L;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int t = 0; t < 9; ++t) {
-        const int dy = t / 3 - 1, dx = t % 3 - 1;
-        const int yy = y - dy, xx = x - dx;
-        if (yy < 0 || yy >= L || xx < 0 || xx >= L) continue;
-        const float2 d = *reinterpret_cast<const float2*>(dz5 + (m - dy * L - dx) * 2);
+    const bool in = interior(m, L);
+    for (int t = 0; t < 9 && in; ++t) {
+        const float2 d = *reinterpret_cast<const float2*>(dz5 + (m - tap_shift(t, L)) * 2);
         if (d.x == 0.0f && d.y == 0.0f) continue;
         const float g[2] = {d.x, d.y};
         for (int co = 0; co < kOut; ++co) {
@@ -882,24 +1004,22 @@ __global__ void conv5_dgrad_kernel(const bf16* w5, const float* dz5, const bf16*
 
 // Last-layer weight and bias gradients of one syndrome (block per item, 576
 // threads = (tap, ci)): S[item][co][tap * 64 + ci] = sum_p dz5[p][co]
-// a4[p + offset(tap)][ci] over positions p of the map with p + offset inside;
-// Sb[item][co] = sum_p dz5[p][co].  Positions in order.
+// a4[p + shift(tap)][ci] over the item's positions p (dz5 is zero outside
+// the map, and the neighbours of a map position lie in the item's padded
+// frame); Sb[item][co] = sum_p dz5[p][co].  Positions in order.
 __global__ void conv5_wgrad_item_kernel(const float* dz5, const bf16* a4, int L, float* S, float* Sb) {
     const long long item = blockIdx.x;
     const int t = threadIdx.x >> 6, ci = threadIdx.x & 63;
-    const int dy = t / 3 - 1, dx = t % 3 - 1;
-    const int LL = L * L;
-    const float* d = dz5 + item * LL * 2;
-    const bf16* a = a4 + item * LL * 64;
+    const int P = L + 2, PP = P * P, sh = tap_shift(t, L);
+    const float* d = dz5 + item * PP * 2;
+    const bf16* a = a4 + item * (long long)PP * 64;
     float acc0 = 0.0f, acc1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-    for (int p = 0; p < LL; ++p) {
+    for (int p = 0; p < PP; ++p) {
         const float d0 = d[2 * p], d1 = d[2 * p + 1];
         if (d0 == 0.0f && d1 == 0.0f) continue;
         b0 += d0;
         b1 += d1;
-        const int y = p / L + dy, x = p % L + dx;
-        if (y < 0 || y >= L || x < 0 || x >= L) continue;
-        const float v = __bfloat162float(a[(y * L + x) * 64 + ci]);
+        const float v = __bfloat162float(a[(p + sh) * 64 + ci]);
         acc0 += d0 * v;
         acc1 += d1 * v;
     }
@@ -965,7 +1085,7 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 // ---------------------------------------------------------------------------
 struct CnnNet {
     surfmcmc_ctx* ctx = nullptr;
-    int device = 0, L = 0, sms = 0;
+    int device = 0, L = 0, P = 0, sms = 0;
     long long max_batch = 0;
     long long step = 0;
     // parameters (float32) and Adam moments, gradient
@@ -983,6 +1103,8 @@ struct CnnNet {
     float *logprob = nullptr, *dz5 = nullptr, *loss_item = nullptr, *loss = nullptr, *S5 = nullptr, *Sb5 = nullptr;
     float* partial = nullptr;
     int* err = nullptr;
+    // TMA maps of the 64-channel tensors that convs read: act[0..3], dz[0..1]
+    CUtensorMap map_act[4], map_dz[2];
     std::vector<void*> allocs;
 };
 
@@ -998,23 +1120,53 @@ cudaError_t prepare_kernels() {
     static bool done = false;
     if (done) return cudaSuccess;
     cudaError_t e;
-    if ((e = set_smem(conv_kernel<2, 64, kEpiRelu>, conv_smem_bytes<2, 64>()))) return e;
-    if ((e = set_smem(conv_kernel<64, 64, kEpiRelu>, conv_smem_bytes<64, 64>()))) return e;
-    if ((e = set_smem(conv_kernel<64, 16, kEpiLogit>, conv_smem_bytes<64, 16>()))) return e;
-    if ((e = set_smem(conv_kernel<64, 64, kEpiMask>, conv_smem_bytes<64, 64>()))) return e;
+    if ((e = set_smem(conv1_kernel, kC1Smem))) return e;
+    if ((e = set_smem(conv_tma_kernel<64, kEpiRelu>, conv_tma_smem_bytes<64>()))) return e;
+    if ((e = set_smem(conv_tma_kernel<16, kEpiLogit>, conv_tma_smem_bytes<16>()))) return e;
+    if ((e = set_smem(conv_tma_kernel<64, kEpiMask>, conv_tma_smem_bytes<64>()))) return e;
     if ((e = set_smem(wgrad_kernel<2>, kWgSmem))) return e;
     if ((e = set_smem(wgrad_kernel<64>, kWgSmem))) return e;
     done = true;
     return cudaSuccess;
 }
 
-template <int CIN, int NP, int EPI>
-cudaError_t launch_conv(const CnnNet* net, const ConvArgs& a, cudaStream_t s) {
+cudaError_t launch_conv1(const CnnNet* net, const ConvArgs& a, cudaStream_t s) {
     const long long tiles = (a.M + 127) / 128;
     if (tiles == 0) return cudaSuccess;
     const int grid = (int)(tiles < net->sms ? tiles : net->sms);
-    conv_kernel<CIN, NP, EPI><<<grid, kConvThreads, conv_smem_bytes<CIN, NP>(), s>>>(a);
+    conv1_kernel<<<grid, kConvThreads, kC1Smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int NP, int EPI>
+cudaError_t launch_conv_tma(const CnnNet* net, const ConvTmaArgs& a, cudaStream_t s) {
+    const long long tiles = (a.M + 127) / 128;
+    if (tiles == 0) return cudaSuccess;
+    const int grid = (int)(tiles < net->sms ? tiles : net->sms);
+    conv_tma_kernel<NP, EPI><<<grid, kTmaThreads, conv_tma_smem_bytes<NP>(), s>>>(a);
+    return cudaGetLastError();
+}
+
+// TMA map of a [rows][64] bf16 tensor: boxes of 128 rows x 64 channels
+// (128 bytes, the 128-byte swizzle), rows outside read as zero.
+cudaError_t make_map(CUtensorMap* map, void* base, long long rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+        if (e != cudaSuccess) return e;
+        if (qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 int wgrad_slices(long long M, int row_tiles, int sms) {
@@ -1071,30 +1223,39 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
                             cudaStream_t s) {
     cudaError_t e;
     const int L = net->L;
-    const long long M = n * L * L;
+    const long long M = n * net->P * net->P;
     if (n == 0) return cudaSuccess;
     if ((e = prepare_kernels())) return e;
     input_maps_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(syn, n, L, net->x0);
     if ((e = cudaGetLastError())) return e;
-    ConvArgs a;
+    ConvArgs c1;
+    memset(&c1, 0, sizeof c1);
+    c1.act = net->x0;
+    c1.wmat = net->fwd[0];
+    c1.bias = net->theta + layer_boff(0);
+    c1.out_bf16 = net->act[0];
+    c1.M = M;
+    c1.L = L;
+    c1.err = net->err;
+    if ((e = launch_conv1(net, c1, s))) return e;
+    ConvTmaArgs a;
     memset(&a, 0, sizeof a);
     a.M = M;
     a.L = L;
     a.err = net->err;
-    for (int l = 0; l < 4; ++l) {
-        a.act = l == 0 ? net->x0 : net->act[l - 1];
+    for (int l = 1; l < 4; ++l) {
+        a.map = net->map_act[l - 1];
         a.wmat = net->fwd[l];
         a.bias = net->theta + layer_boff(l);
         a.out_bf16 = net->act[l];
-        e = l == 0 ? launch_conv<2, 64, kEpiRelu>(net, a, s) : launch_conv<64, 64, kEpiRelu>(net, a, s);
-        if (e) return e;
+        if ((e = launch_conv_tma<64, kEpiRelu>(net, a, s))) return e;
     }
-    a.act = net->act[3];
+    a.map = net->map_act[3];
     a.wmat = net->fwd[4];
     a.bias = net->theta + layer_boff(4);
     a.out_bf16 = nullptr;
     a.out_f32 = net->z5;
-    if ((e = launch_conv<64, 16, kEpiLogit>(net, a, s))) return e;
+    if ((e = launch_conv_tma<16, kEpiLogit>(net, a, s))) return e;
     if (targets && (e = cudaMemsetAsync(net->dz5, 0, (size_t)M * 8, s))) return e;
     readout_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(net->z5, syn, n, L, targets, logprob, net->dz5,
                                                            net->loss_item);
@@ -1105,7 +1266,7 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
 cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const float* targets, cudaStream_t s) {
     cudaError_t e;
     const int L = net->L;
-    const long long M = n * L * L;
+    const long long M = n * net->P * net->P;
     if ((e = cnn_forward_dev(net, syn, n, targets, net->logprob, s))) return e;
     loss_sum_kernel<<<1, 256, 0, s>>>(net->loss_item, n, net->loss);
     if ((e = cudaGetLastError())) return e;
@@ -1120,7 +1281,7 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
                                                                         net->dz[0]);
     if ((e = cudaGetLastError())) return e;
     // layers 4, 3, 2: weight gradient, then input gradient gated by the layer below
-    ConvArgs a;
+    ConvTmaArgs a;
     memset(&a, 0, sizeof a);
     a.M = M;
     a.L = L;
@@ -1128,11 +1289,11 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
     int cur = 0;
     for (int l = 3; l >= 1; --l) {
         if ((e = launch_wgrad<64>(net, net->act[l - 1], net->dz[cur], M, l, s))) return e;
-        a.act = net->dz[cur];
+        a.map = net->map_dz[cur];
         a.wmat = net->bwd[l - 1];
         a.mask = net->act[l - 1];
         a.out_bf16 = net->dz[cur ^ 1];
-        if ((e = launch_conv<64, 64, kEpiMask>(net, a, s))) return e;
+        if ((e = launch_conv_tma<64, kEpiMask>(net, a, s))) return e;
         cur ^= 1;
     }
     return launch_wgrad<2>(net, net->x0, net->dz[cur], M, 0, s);
@@ -1231,10 +1392,11 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     net->ctx = ctx;
     net->device = ctx_device(ctx);
     net->L = L;
+    net->P = L + 2;
     net->max_batch = max_batch;
     NetGuard g(net->device);
     cudaError_t e = cudaDeviceGetAttribute(&net->sms, cudaDevAttrMultiProcessorCount, net->device);
-    const long long M = max_batch * L * L;
+    const long long M = max_batch * net->P * net->P;   // padded positions
     const size_t P = (size_t)kParams * 4;
     auto na = [&](auto** field, size_t bytes) {
         void* p = nullptr;
@@ -1262,6 +1424,8 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     na(&net->Sb5, (size_t)max_batch * 2 * 4);
     na(&net->partial, (size_t)kMaxSplits * 640 * 64 * 4);
     na(&net->err, 4);
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->map_act[l], net->act[l], M);
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->map_dz[l], net->dz[l], M);
     if (e == cudaSuccess) e = cudaMemset(net->err, 0, 4);
     if (e == cudaSuccess) e = cudaMemset(net->theta, 0, P);
     if (e == cudaSuccess) e = cudaMemset(net->m1, 0, P);
