@@ -6,10 +6,12 @@ Training steps (forward, backward, Adam) on a fixed batch of synthetic
 syndromes (the library's generator, p = 0.12) with soft targets, and the
 inference forward on a larger batch, timed with CUDA events on the launching
 stream after warm-up.  Prints one JSON line with samples/s and the
-algorithmic tensor FLOP/s (2 x multiply-adds of the convolutions: forward =
-conv1..conv5, a training step = forward + input gradients of conv2..conv4 +
-weight gradients of conv1..conv4; the last layer's backward and the readout
-run on the CUDA cores and are not counted) against the measured bf16 peak.
+algorithmic tensor FLOP/s (2 x multiply-adds of the convolutions on the
+L x L maps: forward = conv1..conv4, a training step = forward + input
+gradients of conv2..conv4 + weight gradients of conv1..conv4; the last layer,
+evaluated and differentiated on the 2L middle-line outputs only, and the
+readout run on the CUDA cores and are not counted) against the measured bf16
+peak.
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ COUT = [64, 64, 64, 64, 2]
 
 
 def flops_per_position():
-    fwd = [2 * 9 * ci * co for ci, co in zip(CIN, COUT)]
+    fwd = [2 * 9 * ci * co for ci, co in zip(CIN, COUT)][:4]   # tensor-core convs conv1..conv4
     dgrad = sum(fwd[1:4])           # tensor-core input gradients of conv2..conv4
     wgrad = sum(fwd[0:4])           # tensor-core weight gradients of conv1..conv4
     return sum(fwd), sum(fwd) + dgrad + wgrad

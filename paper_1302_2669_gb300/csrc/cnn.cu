@@ -21,19 +21,22 @@
 //
 // Tensor-core work (tcgen05, BF16 in, FP32 accumulate in tensor memory):
 //   forward conv and input-gradient conv (64 input channels): an implicit
-//     GEMM, M = positions in tiles of 128, N = output channels, K = 9 x 64
-//     taken one 3x3 tap per pipeline stage; a tap's operand is 128 shifted
-//     position rows, loaded by one TMA tiled copy (128-byte swizzle) from
-//     one thread; the weight operand stays in shared memory for the whole
-//     persistent block; one thread issues the MMAs, four warps drain the two
-//     tensor-memory accumulators (bias + ReLU, logits, or the ReLU gate of
-//     the layer below).  The first layer (2 input channels, K = 18 padded to
+//     GEMM, M = positions in tiles of 128, N = output channels, K = 9 x 64.
+//     One TMA tiled copy (128-byte swizzle) per tile brings the tile's rows
+//     with a halo of P + 1 rows on each side; the operand of tap t is the
+//     128 rows starting at row P + 1 + shift(t) of that halo tile, so each
+//     input row crosses from L2 once per tile instead of once per tap.  The
+//     weight operand stays in shared memory for the whole persistent block;
+//     one thread issues the MMAs, four warps drain the two tensor-memory
+//     accumulators (bias + ReLU, logits, or the ReLU gate of the layer
+//     below).  The first layer (2 input channels, K = 18 padded to
 //     32) gathers its operand with producer warps;
 //   weight gradient: D[(tap, ci)][co] = sum_p X[p + tap][ci] dZ[p][co], a
 //     GEMM over positions split across blocks, with a row of ones that yields
 //     the bias gradient; partial sums are added in a fixed order.
-// The last layer's backward (2 outputs, gradient nonzero on the middle lines
-// only), the readout, loss and Adam steps run on the CUDA cores.
+// The last layer (2 outputs, read and differentiated on the middle lines
+// only: forward fused into the readout, backward), the readout, loss and
+// Adam steps run on the CUDA cores.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -64,7 +67,7 @@ constexpr int kWgThreads = (kWgProd + kEpiWarps + 1) * 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWaitTimeout = 1;   // error codes written to the device flag
 constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
-constexpr int kTmaStages = 6;     // tap tiles in flight in the TMA conv kernel
+constexpr int kTmaStages = 4;     // halo tiles in flight in the TMA conv kernel
 constexpr int kTmaThreads = 6 * 32;  // TMA warp, MMA warp, 4 accumulator warps
 
 // Channels of the five layers and the offsets of their weights and biases in
@@ -180,6 +183,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         : "memory");
 }
 
+// The same with each descriptor given as its 32-bit halves (the low half
+// holds the start address field, so moving an operand inside shared memory
+// is one 32-bit add).
+__device__ __forceinline__ void mma_bf16_lh(uint32_t d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                            uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\tmov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+        "setp.ne.b32 p, %6, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 // Arrives on the barrier once every tcgen05 operation issued so far by this
 // thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -221,11 +236,44 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// TMA tiled store of box (c0, c1) of a 2-D tensor map from shared memory
+// (rows outside the tensor are not written), in this thread's bulk group.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until at most N of this thread's bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Barrier 1 over the 128 accumulator-draining threads; the second form
+// returns whether the predicate held in all of them.
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool epi_all(bool v) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v)
+                 : "memory");
+    return r != 0;
+}
+
 // Padded maps: P = L + 2, position m of a batch; interior positions are the
 // L x L map, the rest is the zero border.
 __device__ __forceinline__ bool interior(long long m, int L) {
     const int P = L + 2, PP = P * P;
     const int rem = (int)(m % PP), y = rem / P, x = rem - (rem / P) * P;
+    return y >= 1 && y <= L && x >= 1 && x <= L;
+}
+
+// The same for position rem = m mod P^2 inside its map.
+__device__ __forceinline__ bool interior_rem(int rem, int L) {
+    const int P = L + 2, y = rem / P, x = rem - y * P;
     return y >= 1 && y <= L && x >= 1 && x <= L;
 }
 
@@ -418,46 +466,64 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv1_kernel(ConvArgs a) {
 // ---------------------------------------------------------------------------
 // Convolutions with 64 input channels: tap operands by TMA.
 // ---------------------------------------------------------------------------
-enum Epi { kEpiRelu = 0, kEpiLogit = 1, kEpiMask = 2 };
+enum Epi { kEpiRelu = 0, kEpiMask = 1 };
 
-struct alignas(64) ConvTmaArgs {
-    CUtensorMap map;     // input [M_alloc][64] bf16, box 64 x 128, 128-byte swizzle
+struct ConvTmaArgs {
+    CUtensorMap map;     // input [M_alloc][64] bf16, box 64 x halo_rows, 128-byte swizzle
+    CUtensorMap out_map;   // output [M_alloc][64] bf16, box 64 x 128 (kEpiRelu, kEpiMask)
+    CUtensorMap mask_map;  // ReLU gate [M_alloc][64] bf16, box 64 x 128 (kEpiMask)
     const bf16* wmat;    // [NP][576] operand B (k = tap * 64 + ci)
-    const float* bias;   // [NP] (kEpiRelu, kEpiLogit) or NULL
-    const bf16* mask;    // [M][64] ReLU gate (kEpiMask) or NULL
-    bf16* out_bf16;      // [M][64] (kEpiRelu, kEpiMask)
-    float* out_f32;      // [M][2]  (kEpiLogit)
+    const float* bias;   // [NP] (kEpiRelu) or NULL
     long long M;         // positions n P^2
     int L;
+    int halo_rows;       // rows of one halo tile, halo_tile_rows(L)
     int* err;
 };
 
-constexpr int kTmaTile = 128 * 64 * 2;   // one tap's operand, 16 KB
+// Rows of the halo tile of 128 output positions: the taps shift by up to
+// P + 1 = L + 3 rows either way; rounded up to whole 8-row swizzle atoms so
+// that every stage starts on a 1024-byte boundary.  At most 200 (L = 31),
+// inside the 256-row limit of a TMA box.
+__host__ __device__ constexpr int halo_tile_rows(int L) { return (128 + 2 * (L + 3) + 7) / 8 * 8; }
+constexpr int kHaloRowsMax = halo_tile_rows(SURFMCMC_MAX_L);
+constexpr int kTmaStage = kHaloRowsMax * 128;   // stage stride in bytes
+static_assert(kHaloRowsMax <= 256 && kTmaStage % 1024 == 0, "halo tile");
 
-template <int NP>
+constexpr int kOutTile = 128 * 128;   // one 128 x 64 bf16 output tile
+constexpr int kConvAcc = 4;           // tensor-memory accumulators of the conv kernel
+
+template <int NP, int EPI>
 constexpr size_t conv_tma_smem_bytes() {
-    return (size_t)kTmaStages * kTmaTile + (size_t)NP * 576 * 2 + 1024;
+    return (size_t)kTmaStages * kTmaStage + (size_t)NP * 576 * 2 + 2 * kOutTile + 1024;
 }
 
-// Warp 0 (one thread) loads the 9 tap tiles of each position tile by TMA
-// into a ring of stages; warp 1 (one thread) issues 4 MMAs per tap (K = 16
-// each) into one of two accumulators; warps 2-5 drain the accumulators.
+// Warp 0 (one thread) loads the halo tile of each position tile by TMA into
+// a ring of stages; warp 1 (one thread) issues 4 MMAs per tap (K = 16 each),
+// 36 per tile, into one of four accumulators; warps 2-5 drain the
+// accumulators.  A tap's operand starts at a 128-byte row inside the
+// 1024-byte-aligned halo tile: the 128-byte swizzle is a function of the
+// shared-memory address bits, so the descriptor keeps a zero base offset.
+// The bf16 epilogues write their tile into one of two output buffers in the
+// 128-byte-swizzled layout (16-byte chunk j of row r at chunk j ^ (r & 7)),
+// which one thread then stores with a single TMA copy; the ReLU gate of the
+// backward pass arrives in that buffer by TMA before the tile is drained.
 template <int NP, int EPI>
 __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_constant__ ConvTmaArgs a) {
-    constexpr int S = kTmaStages, KG = 576 / 8;
-    constexpr uint32_t NCOLS = 2 * NP < 32 ? 32 : 2 * NP;
+    constexpr int S = kTmaStages, KG = 576 / 8, NACC = kConvAcc;
+    constexpr uint32_t NCOLS = NACC * NP < 32 ? 32 : NACC * NP;
     constexpr uint32_t IDESC = idesc_bf16(128, NP);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;                      // S tiles of 16 KB, 1024-byte aligned
-    uint8_t* sB = smem + S * kTmaTile;
-    __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], fin;
+    uint8_t* sA = smem;                      // S halo tiles, 1024-byte aligned
+    uint8_t* sB = smem + S * kTmaStage;
+    uint8_t* sOut = sB + NP * 576 * 2;       // 2 output tiles (bf16 epilogues), 1024-byte aligned
+    __shared__ __align__(8) uint64_t full[S], empty[S], accf[NACC], acce[NACC], maskf[2], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
-    const int L = a.L;
+    const int L = a.L, P1 = L + 3;
     const long long n_tiles = (M + 127) / 128;
 
     for (int idx = tid; idx < NP * KG; idx += kTmaThreads) {
@@ -470,10 +536,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&accf[b], 1);
             mbar_init(&acce[b], kEpiWarps * 32);
         }
+        mbar_init(&maskf[0], 1);
+        mbar_init(&maskf[1], 1);
         mbar_init(&fin, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -487,46 +555,48 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
 
     if (warp == 0) {
         if (lane == 0) {
+            const uint32_t bytes = (uint32_t)a.halo_rows * 128;
             uint32_t q = 0;
-            bool ok = true;
-            for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                for (int c = 0; c < 9; ++c, ++q) {
-                    const uint32_t stage = q % S, use = q / S;
-                    if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(&full[stage], kTmaTile);
-                    tma_load_2d(sA + stage * kTmaTile, &a.map, 0, (int)(tile * 128 + tap_shift(c, L)), &full[stage]);
-                }
+            for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++q) {
+                const uint32_t stage = q % S, use = q / S;
+                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                mbar_expect_tx(&full[stage], bytes);
+                tma_load_2d(sA + stage * kTmaStage, &a.map, 0, (int)(tile * 128 - P1), &full[stage]);
             }
+            // the last S loads have landed before the block can exit (they
+            // are unconsumed only after an abort)
+            for (uint32_t k = q > (uint32_t)S ? q - S : 0; k < q; ++k) mbar_drain(&full[k % S], (k / S) & 1, a.err);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            uint32_t q = 0, it = 0;
-            bool ok = true;
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
-                const uint32_t b = it & 1, u = it >> 1;
+            uint32_t it = 0;
+            // descriptors as 32-bit halves: the high halves are fixed, the
+            // low halves are the start address / 16 plus the operand's offset
+            const uint64_t a_desc = smem_desc_sw128(smem_u32(sA) + P1 * 128);
+            const uint64_t b_desc = smem_desc(smem_u32(sB), 128, KG * 128);
+            const uint32_t a_hi = (uint32_t)(a_desc >> 32), b_hi = (uint32_t)(b_desc >> 32);
+            const uint32_t a_lo0 = (uint32_t)a_desc, b_lo0 = (uint32_t)b_desc;
+            uint32_t tap_lo[9];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) tap_lo[c] = (uint32_t)(tap_shift(c, L) * 8);   // 128 B rows / 16
+            for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+                const uint32_t b = it % NACC, u = it / NACC;
+                const uint32_t stage = it % S, use = it / S;
                 if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
+                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + b * NP;
-                for (int c = 0; c < 9; ++c, ++q) {
-                    const uint32_t stage = q % S, use = q / S;
-                    if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
+                const uint32_t a_st = a_lo0 + stage * (kTmaStage / 16);
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = smem_desc_sw128(a0 + stage * kTmaTile + ks * 32);
-                        const uint64_t bd = smem_desc(b0 + (c * 8 + ks * 2) * 128, 128, KG * 128);
-                        mma_bf16(d, ad, bd, IDESC, (c > 0 || ks > 0) ? 1u : 0u);
-                    }
-                    mma_commit(&empty[stage]);
+                for (int c = 0; c < 9; ++c) {
+                    const uint32_t a_tap = a_st + tap_lo[c];
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        mma_bf16_lh(d, a_tap + ks * 2, a_hi, b_lo0 + (c * 8 + ks * 2) * 8, b_hi, IDESC,
+                                    (c > 0 || ks > 0) ? 1u : 0u);
                 }
-                if (ok) mma_commit(&accf[b]);
+                mma_commit(&empty[stage]);
+                mma_commit(&accf[b]);
             }
             mma_commit(&fin);
             mbar_drain(&fin, 0, a.err);
@@ -534,55 +604,72 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
     } else {
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
+        const bool elected = warp == 2 && lane == 0;
+        const int PP = (L + 2) * (L + 2);
+        float bias[EPI == kEpiRelu ? NP : 1];
+#pragma unroll
+        for (int j = 0; j < (EPI == kEpiRelu ? NP : 1); ++j) bias[j] = EPI == kEpiRelu ? __ldg(a.bias + j) : 0.0f;
         uint32_t it = 0;
         for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-            const uint32_t b = it & 1, u = it >> 1;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[b], u & 1, &abort_flag, a.err));
-            if (!ok) break;
-            tc_fence_after();
-            const long long m = tile * 128 + row;
-            const bool keep = m < M && interior(m, L);
-            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
-            if (EPI == kEpiLogit) {
-                float v[16];
-                tmem_ld16(taddr, v);
-                if (m < M)
-                    *reinterpret_cast<float2*>(a.out_f32 + m * 2) =
-                        keep ? make_float2(v[0] + __ldg(a.bias + 0), v[1] + __ldg(a.bias + 1)) : make_float2(0.f, 0.f);
-            } else {
-#pragma unroll
-                for (int cc = 0; cc < NP / 16; ++cc) {
-                    float v[16];
-                    tmem_ld16(taddr + cc * 16, v);
-                    if (m < M) {
-                        uint32_t w[8];
-                        if (EPI == kEpiRelu) {
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float x0 = keep ? fmaxf(v[2 * j] + __ldg(a.bias + cc * 16 + 2 * j), 0.0f) : 0.0f;
-                                const float x1 =
-                                    keep ? fmaxf(v[2 * j + 1] + __ldg(a.bias + cc * 16 + 2 * j + 1), 0.0f) : 0.0f;
-                                w[j] = pack_bf16(x0, x1);
-                            }
-                        } else {
-                            const uint4* mp = reinterpret_cast<const uint4*>(a.mask + m * 64 + cc * 16);
-                            const uint4 m0 = __ldg(mp), m1 = __ldg(mp + 1);
-                            const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float x0 = keep && bf16_lo(mw[j]) > 0.0f ? v[2 * j] : 0.0f;
-                                const float x1 = keep && bf16_hi(mw[j]) > 0.0f ? v[2 * j + 1] : 0.0f;
-                                w[j] = pack_bf16(x0, x1);
-                            }
-                        }
-                        uint4* op = reinterpret_cast<uint4*>(a.out_bf16 + m * 64 + cc * 16);
-                        op[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                        op[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                    }
+            const uint32_t b = it % NACC, u = it / NACC, ob = it & 1;
+            uint8_t* out = sOut + ob * kOutTile;
+            if (elected) {
+                bulk_wait_read<1>();   // the store of two tiles back has left this buffer
+                if (EPI == kEpiMask) {
+                    mbar_expect_tx(&maskf[ob], kOutTile);
+                    tma_load_2d(out, &a.mask_map, 0, (int)(tile * 128), &maskf[ob]);
                 }
             }
+            const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err);
+            if (!epi_all(ok)) break;
+            tc_fence_after();
+            const long long m = tile * 128 + row;
+            const int rem = (int)((tile * 128) % PP + row) % PP;
+            const bool keep = m < M && interior_rem(rem, L);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
+            float v[NP];
+#pragma unroll
+            for (int cc = 0; cc < NP / 16; ++cc) tmem_ld16(taddr + cc * 16, v + cc * 16);
             tc_fence_before();
             mbar_arrive(&acce[b]);
+            uint8_t* orow = out + row * 128;
+            const int sw = row & 7;
+            if (EPI == kEpiMask) mbar_wait(&maskf[ob], (it >> 1) & 1, &abort_flag, a.err);
+#pragma unroll
+            for (int j = 0; j < NP / 8; ++j) {
+                uint4* chunk = reinterpret_cast<uint4*>(orow + ((j ^ sw) << 4));
+                uint32_t w[4];
+                if (EPI == kEpiRelu) {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int c = 8 * j + 2 * h;
+                        w[h] = keep ? pack_bf16(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f)) : 0u;
+                    }
+                } else {
+                    const uint4 g = *chunk;
+                    const uint32_t mw[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int c = 8 * j + 2 * h;
+                        const float x0 = keep && bf16_lo(mw[h]) > 0.0f ? v[c] : 0.0f;
+                        const float x1 = keep && bf16_hi(mw[h]) > 0.0f ? v[c + 1] : 0.0f;
+                        w[h] = pack_bf16(x0, x1);
+                    }
+                }
+                *chunk = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            fence_async_smem();
+            epi_sync();
+            if (elected) {
+                tma_store_2d(&a.out_map, out, 0, (int)(tile * 128));
+                bulk_commit();
+            }
+        }
+        if (elected) {
+            // after an abort a gate load may still be in flight
+            if (EPI == kEpiMask && it < (uint32_t)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x))
+                mbar_drain(&maskf[it & 1], (it >> 1) & 1, a.err);
+            bulk_wait_all();
         }
     }
     tc_fence_before();
@@ -878,11 +965,15 @@ __global__ void pack_kernel(PackArgs a) {
     }
 }
 
-// One warp per syndrome: the parity readout.  Lane i < L holds the flip
-// logits on the middle column (row i) and middle row (column j = i); the
-// products are taken in lane order 0..31 by every lane.  With targets, also
-// the loss and d loss / d z5 at the middle-line positions (dz5 must be zero
-// elsewhere).
+// One warp per syndrome: the last layer on the middle lines and the parity
+// readout.  The readout needs the last layer's channel 0 only on the middle
+// column (map positions (i, m)) and channel 1 only on the middle row ((m, j)),
+// so it computes just those 2L outputs: lane l holds the bf16 weights of
+// input channels 2l, 2l + 1 for both outputs and the 9 taps, every output is
+// a warp-wide sum (xor butterfly, fp32) plus the bias, and lane i < L keeps
+// the logits of row i / column i.  The products are taken in lane order
+// 0..31 by every lane.  With targets, also the loss and d loss / d z5 at the
+// middle-line positions (dz5 must be zero elsewhere).
 __device__ __forceinline__ float warp_prod_except(float t, int skip) {
     float r = 1.0f;
     for (int j = 0; j < 32; ++j) {
@@ -892,17 +983,48 @@ __device__ __forceinline__ float warp_prod_except(float t, int skip) {
     return r;
 }
 
-__global__ void readout_kernel(const float* z5, const uint8_t* syn, long long n, int L, const float* targets,
-                               float* logprob, float* dz5, float* loss_item) {
+__global__ void readout_kernel(const bf16* w5, const float* b5, const bf16* a4, const uint8_t* syn, long long n,
+                               int L, const float* targets, float* logprob, float* dz5, float* loss_item) {
     const long long item = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (item >= n) return;
     const int m = (L - 1) / 2, P = L + 2;
     const long long base = item * P * P + P + 1;   // map (0, 0)
-    float sa = 0.0f, sb = 0.0f, ta = 1.0f, tb = 1.0f;
+    float w[2][9][2];
+#pragma unroll
+    for (int co = 0; co < 2; ++co)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(w5 + co * 576 + t * 64) + lane);
+            w[co][t][0] = bf16_lo(v);
+            w[co][t][1] = bf16_hi(v);
+        }
+    const uint32_t* a = reinterpret_cast<const uint32_t*>(a4) + lane;   // 32 words per position
+    float sa = 0.0f, sb = 0.0f;
+    for (int i = 0; i < L; ++i) {
+        const long long qa = base + (long long)i * P + m, qb = base + (long long)m * P + i;
+        float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int sh = (t / 3 - 1) * P + (t % 3 - 1);
+            const uint32_t x0 = __ldg(a + (qa + sh) * 32), x1 = __ldg(a + (qb + sh) * 32);
+            acc0 = fmaf(bf16_lo(x0), w[0][t][0], acc0);
+            acc0 = fmaf(bf16_hi(x0), w[0][t][1], acc0);
+            acc1 = fmaf(bf16_lo(x1), w[1][t][0], acc1);
+            acc1 = fmaf(bf16_hi(x1), w[1][t][1], acc1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+            acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+        }
+        if (lane == i) {
+            sa = acc0 + __ldg(b5 + 0);
+            sb = acc1 + __ldg(b5 + 1);
+        }
+    }
+    float ta = 1.0f, tb = 1.0f;
     if (lane < L) {
-        sa = z5[(base + (long long)lane * P + m) * 2 + 0];
-        sb = z5[(base + (long long)m * P + lane) * 2 + 1];
         ta = -tanhf(0.5f * sa);
         tb = -tanhf(0.5f * sb);
     }
@@ -1004,24 +1126,25 @@ __global__ void conv5_dgrad_kernel(const bf16* w5, const float* dz5, const bf16*
 
 // Last-layer weight and bias gradients of one syndrome (block per item, 576
 // threads = (tap, ci)): S[item][co][tap * 64 + ci] = sum_p dz5[p][co]
-// a4[p + shift(tap)][ci] over the item's positions p (dz5 is zero outside
-// the map, and the neighbours of a map position lie in the item's padded
-// frame); Sb[item][co] = sum_p dz5[p][co].  Positions in order.
+// a4[p + shift(tap)][ci] over the item's positions p, Sb[item][co] = sum_p
+// dz5[p][co].  dz5 is nonzero only on channel 0 of the middle column and
+// channel 1 of the middle row, so the sums run over those lines, row by row
+// (column by column).  The neighbours of a map position lie in the item's
+// padded frame.
 __global__ void conv5_wgrad_item_kernel(const float* dz5, const bf16* a4, int L, float* S, float* Sb) {
     const long long item = blockIdx.x;
     const int t = threadIdx.x >> 6, ci = threadIdx.x & 63;
-    const int P = L + 2, PP = P * P, sh = tap_shift(t, L);
+    const int P = L + 2, PP = P * P, sh = tap_shift(t, L), m = (L - 1) / 2;
     const float* d = dz5 + item * PP * 2;
     const bf16* a = a4 + item * (long long)PP * 64;
     float acc0 = 0.0f, acc1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-    for (int p = 0; p < PP; ++p) {
-        const float d0 = d[2 * p], d1 = d[2 * p + 1];
-        if (d0 == 0.0f && d1 == 0.0f) continue;
+    for (int i = 0; i < L; ++i) {
+        const int pa = (i + 1) * P + m + 1, pb = (m + 1) * P + i + 1;
+        const float d0 = d[2 * pa], d1 = d[2 * pb + 1];
         b0 += d0;
         b1 += d1;
-        const float v = __bfloat162float(a[(p + sh) * 64 + ci]);
-        acc0 += d0 * v;
-        acc1 += d1 * v;
+        acc0 += d0 * __bfloat162float(a[(pa + sh) * 64 + ci]);
+        acc1 += d1 * __bfloat162float(a[(pb + sh) * 64 + ci]);
     }
     S[(item * 2 + 0) * 576 + threadIdx.x] = acc0;
     S[(item * 2 + 1) * 576 + threadIdx.x] = acc1;
@@ -1098,13 +1221,14 @@ struct CnnNet {
     float* targets = nullptr;
     bf16* x0 = nullptr;
     bf16* act[4] = {};
-    float* z5 = nullptr;
     bf16* dz[2] = {};
     float *logprob = nullptr, *dz5 = nullptr, *loss_item = nullptr, *loss = nullptr, *S5 = nullptr, *Sb5 = nullptr;
     float* partial = nullptr;
     int* err = nullptr;
     // TMA maps of the 64-channel tensors that convs read: act[0..3], dz[0..1]
     CUtensorMap map_act[4], map_dz[2];
+    // the same tensors in boxes of 128 rows (output tiles, ReLU gates)
+    CUtensorMap tile_act[4], tile_dz[2];
     std::vector<void*> allocs;
 };
 
@@ -1121,9 +1245,8 @@ cudaError_t prepare_kernels() {
     if (done) return cudaSuccess;
     cudaError_t e;
     if ((e = set_smem(conv1_kernel, kC1Smem))) return e;
-    if ((e = set_smem(conv_tma_kernel<64, kEpiRelu>, conv_tma_smem_bytes<64>()))) return e;
-    if ((e = set_smem(conv_tma_kernel<16, kEpiLogit>, conv_tma_smem_bytes<16>()))) return e;
-    if ((e = set_smem(conv_tma_kernel<64, kEpiMask>, conv_tma_smem_bytes<64>()))) return e;
+    if ((e = set_smem(conv_tma_kernel<64, kEpiRelu>, conv_tma_smem_bytes<64, kEpiRelu>()))) return e;
+    if ((e = set_smem(conv_tma_kernel<64, kEpiMask>, conv_tma_smem_bytes<64, kEpiMask>()))) return e;
     if ((e = set_smem(wgrad_kernel<2>, kWgSmem))) return e;
     if ((e = set_smem(wgrad_kernel<64>, kWgSmem))) return e;
     done = true;
@@ -1143,13 +1266,13 @@ cudaError_t launch_conv_tma(const CnnNet* net, const ConvTmaArgs& a, cudaStream_
     const long long tiles = (a.M + 127) / 128;
     if (tiles == 0) return cudaSuccess;
     const int grid = (int)(tiles < net->sms ? tiles : net->sms);
-    conv_tma_kernel<NP, EPI><<<grid, kTmaThreads, conv_tma_smem_bytes<NP>(), s>>>(a);
+    conv_tma_kernel<NP, EPI><<<grid, kTmaThreads, conv_tma_smem_bytes<NP, EPI>(), s>>>(a);
     return cudaGetLastError();
 }
 
-// TMA map of a [rows][64] bf16 tensor: boxes of 128 rows x 64 channels
-// (128 bytes, the 128-byte swizzle), rows outside read as zero.
-cudaError_t make_map(CUtensorMap* map, void* base, long long rows) {
+// TMA map of a [rows][64] bf16 tensor: boxes of box_rows rows x 64
+// channels (128 bytes, the 128-byte swizzle), rows outside read as zero.
+cudaError_t make_map(CUtensorMap* map, void* base, long long rows, int box_rows) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -1161,7 +1284,7 @@ cudaError_t make_map(CUtensorMap* map, void* base, long long rows) {
     }
     const cuuint64_t dims[2] = {64, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {128};
-    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1242,23 +1365,18 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
     memset(&a, 0, sizeof a);
     a.M = M;
     a.L = L;
+    a.halo_rows = halo_tile_rows(L);
     a.err = net->err;
     for (int l = 1; l < 4; ++l) {
         a.map = net->map_act[l - 1];
+        a.out_map = net->tile_act[l];
         a.wmat = net->fwd[l];
         a.bias = net->theta + layer_boff(l);
-        a.out_bf16 = net->act[l];
         if ((e = launch_conv_tma<64, kEpiRelu>(net, a, s))) return e;
     }
-    a.map = net->map_act[3];
-    a.wmat = net->fwd[4];
-    a.bias = net->theta + layer_boff(4);
-    a.out_bf16 = nullptr;
-    a.out_f32 = net->z5;
-    if ((e = launch_conv_tma<16, kEpiLogit>(net, a, s))) return e;
     if (targets && (e = cudaMemsetAsync(net->dz5, 0, (size_t)M * 8, s))) return e;
-    readout_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(net->z5, syn, n, L, targets, logprob, net->dz5,
-                                                           net->loss_item);
+    readout_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(net->fwd[4], net->theta + layer_boff(4), net->act[3], syn,
+                                                           n, L, targets, logprob, net->dz5, net->loss_item);
     return cudaGetLastError();
 }
 
@@ -1285,14 +1403,15 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
     memset(&a, 0, sizeof a);
     a.M = M;
     a.L = L;
+    a.halo_rows = halo_tile_rows(L);
     a.err = net->err;
     int cur = 0;
     for (int l = 3; l >= 1; --l) {
         if ((e = launch_wgrad<64>(net, net->act[l - 1], net->dz[cur], M, l, s))) return e;
         a.map = net->map_dz[cur];
+        a.out_map = net->tile_dz[cur ^ 1];
+        a.mask_map = net->tile_act[l - 1];
         a.wmat = net->bwd[l - 1];
-        a.mask = net->act[l - 1];
-        a.out_bf16 = net->dz[cur ^ 1];
         if ((e = launch_conv_tma<64, kEpiMask>(net, a, s))) return e;
         cur ^= 1;
     }
@@ -1413,7 +1532,6 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     na(&net->targets, (size_t)max_batch * 16);
     na(&net->x0, (size_t)M * 4);
     for (int l = 0; l < 4; ++l) na(&net->act[l], (size_t)M * 128);
-    na(&net->z5, (size_t)M * 8);
     na(&net->dz5, (size_t)M * 8);
     na(&net->dz[0], (size_t)M * 128);
     na(&net->dz[1], (size_t)M * 128);
@@ -1424,8 +1542,11 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     na(&net->Sb5, (size_t)max_batch * 2 * 4);
     na(&net->partial, (size_t)kMaxSplits * 640 * 64 * 4);
     na(&net->err, 4);
-    for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->map_act[l], net->act[l], M);
-    for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->map_dz[l], net->dz[l], M);
+    const int halo = halo_tile_rows(L);
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->map_act[l], net->act[l], M, halo);
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->map_dz[l], net->dz[l], M, halo);
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->tile_act[l], net->act[l], M, 128);
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->tile_dz[l], net->dz[l], M, 128);
     if (e == cudaSuccess) e = cudaMemset(net->err, 0, 4);
     if (e == cudaSuccess) e = cudaMemset(net->theta, 0, P);
     if (e == cudaSuccess) e = cudaMemset(net->m1, 0, P);
