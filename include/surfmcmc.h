@@ -222,7 +222,8 @@ int surfmcmc_decode(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int3
                     uint64_t* out_class_sum, double* out_log_ratio, void* stream);
 
 /* surfmcmc_decode with per-chain state in and out, for resuming a run and for
- * checking single chains.  Runs sweeps sweep_begin .. opts->n_sweeps-1.
+ * checking single chains (Sec. IV: the chain of each class, its sampled n
+ * and its accepted moves).  Runs sweeps sweep_begin .. opts->n_sweeps-1.
  *   init_frames     [n][C][2][W] uint32 in (may be NULL): chain states at
  *                   sweep_begin; NULL starts from the start frames (then
  *                   sweep_begin must be 0).  C = 4 * chains_per_class; chain
@@ -231,6 +232,10 @@ int surfmcmc_decode(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int3
  *   out_chain_sum   [n][C] uint64 out (may be NULL).
  *   out_chain_n     [n][C] int32 out (may be NULL): final n of every chain.
  *   out_chain_frames[n][C][2][W] uint32 out (may be NULL): final states.
+ *   out_chain_accepts [n][C] uint64 out (may be NULL): accepted proposals
+ *                   of every chain in the sweeps run by this call (annealing
+ *                   sweeps included); counting them costs 4.6 KB of shared
+ *                   memory per block and a few operations per proposal.
  * The per-chain uniform: G = min(32, smallest power of two >= C) is the plane
  * width, chain c has group w = c/G and lane b = c%G.  For the proposal of
  * the m-th generator of colour col (row-major order within the colour) in
@@ -242,7 +247,8 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
                        const surfmcmc_opts* opts, uint64_t seed, uint32_t id0, uint32_t sweep_begin,
                        const uint32_t* init_frames, const uint64_t* init_chain_sum, int32_t* out_class,
                        uint64_t* out_class_sum, double* out_log_ratio, uint64_t* out_chain_sum,
-                       int32_t* out_chain_n, uint32_t* out_chain_frames, void* stream);
+                       int32_t* out_chain_n, uint32_t* out_chain_frames, uint64_t* out_chain_accepts,
+                       void* stream);
 
 /* Ragged batches: syndromes of different code sizes (and sweep counts) in one
  * call, with the algorithm of surfmcmc_decode applied to every item; item i

@@ -103,7 +103,7 @@ def lib():
         L.surfmcmc_start_frames.argtypes = [vp, vp, i64, i32, vp, vp, vp]
         L.surfmcmc_decode.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
         L.surfmcmc_decode_ex.argtypes = [vp, vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, u32, vp, vp, vp, vp,
-                                         vp, vp, vp, vp, vp]
+                                         vp, vp, vp, vp, vp, vp]
         L.surfmcmc_noalloc_scratch_needed.argtypes = [i64, i32, i32]
         L.surfmcmc_noalloc_scratch_needed.restype = C.c_size_t
         L.surfmcmc_decode_noalloc.argtypes = [vp, i64, i32, dbl, C.POINTER(_Opts), u64, u32, vp, vp, vp, vp]
@@ -282,7 +282,7 @@ class Context:
 
     def decode_ex(self, syndromes, L, p, opts: Opts | None = None, seed=0, id0=0, sweep_begin=0,
                   init_frames=None, init_chain_sum=None, chain_sum=True, chain_n=True, chain_frames=True,
-                  stream=None):
+                  accepts=False, stream=None):
         """surfmcmc_decode_ex; returns a dict of the outputs (per-chain ones on request)."""
         opts = opts or Opts()
         n = syndromes.shape[0]
@@ -294,12 +294,13 @@ class Context:
         out["chain_n"] = _empty(syndromes, (n, Cn), np.int32) if chain_n else None
         W = (2 * L * L + 31) // 32 if K == 16 else n_words(L)    # toric code: 2 L^2 qubits
         out["chain_frames"] = _empty(syndromes, (n, Cn, 2, W), np.uint32) if chain_frames else None
+        out["accepts"] = _empty(syndromes, (n, Cn), np.uint64) if accepts else None
         st = stream if stream is not None else _stream_of(syndromes, out["cls"])
         o = opts.c()
         self._check(lib().surfmcmc_decode_ex(
             self._h, _ptr(syndromes), n, L, p, C.byref(o), seed, id0, sweep_begin, _ptr(init_frames),
             _ptr(init_chain_sum), _ptr(out["cls"]), _ptr(out["class_sum"]), _ptr(out["log_ratio"]),
-            _ptr(out["chain_sum"]), _ptr(out["chain_n"]), _ptr(out["chain_frames"]), st))
+            _ptr(out["chain_sum"]), _ptr(out["chain_n"]), _ptr(out["chain_frames"]), _ptr(out["accepts"]), st))
         return out
 
     def decode_ti(self, syndromes, L, p, opts: Opts | None = None, n_beta=21, seed=0, id0=0, stream=None):

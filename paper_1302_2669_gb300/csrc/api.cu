@@ -879,7 +879,8 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
                        const surfmcmc_opts* opts_in, uint64_t seed, uint32_t id0, uint32_t sweep_begin,
                        const uint32_t* init_frames, const uint64_t* init_chain_sum, int32_t* out_class,
                        uint64_t* out_class_sum, double* out_log_ratio, uint64_t* out_chain_sum,
-                       int32_t* out_chain_n, uint32_t* out_chain_frames, void* stream) {
+                       int32_t* out_chain_n, uint32_t* out_chain_frames, uint64_t* out_chain_accepts,
+                       void* stream) {
     int rc = check_common(ctx, n, L, id0);
     if (rc) return rc;
     surfmcmc_opts o;
@@ -895,7 +896,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     int lam = 0;
     if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class, toric))
         return fail(ctx, SURFMCMC_EINVAL, "lanes_per_bundle=%d unsupported for L=%d", o.lanes_per_bundle, L);
-    if (o.scan) lam = 32;
+    if (o.scan || out_chain_accepts) lam = 32;   // counting accepts: the LAM = 32 kernels (same results)
     if (n == 0) return SURFMCMC_OK;
     ctx->last_error.clear();
     DeviceGuard g(ctx->device);
@@ -929,6 +930,9 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     // per-chain sums: the caller's device buffer, else scratch
     const bool chs_scratch = !out_chain_sum || !is_device_ptr(out_chain_sum);
     const size_t off_chs = chs_scratch ? cv.reserve((size_t)n * Cn * 8) : 0;
+    // accept counts: the caller's device buffer, else scratch (when asked for)
+    const bool acc_scratch = out_chain_accepts && !is_device_ptr(out_chain_accepts);
+    const size_t off_acc = acc_scratch ? cv.reserve((size_t)n * Cn * 8) : 0;
     const size_t off_e0 = init_frames ? 0 : cv.reserve((size_t)n * 2 * W * 4);
     const size_t off_code = init_frames ? 0 : cv.reserve((size_t)n * 4);
     const std::vector<Segment> segs = plan_segments(o, o.beta_scale, sweep_begin);
@@ -939,6 +943,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     for (Buf* b : all) bind(*b, ctx);
     char* base = (char*)ctx->arena;
     uint64_t* chain_sum = chs_scratch ? (uint64_t*)(base + off_chs) : out_chain_sum;
+    uint64_t* accepts = acc_scratch ? (uint64_t*)(base + off_acc) : out_chain_accepts;
     uint32_t* e0 = init_frames ? nullptr : (uint32_t*)(base + off_e0);
     int32_t* code = init_frames ? nullptr : (int32_t*)(base + off_code);
     uint32_t* state = segs.size() > 1 ? (uint32_t*)(base + off_state) : nullptr;
@@ -946,6 +951,8 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
 
     if ((rc = copy_in(ctx, b_syn, s)) || (rc = copy_in(ctx, b_if, s)) || (rc = copy_in(ctx, b_is, s))) return rc;
     if (!init_frames) CK(launch_start_frames((const uint8_t*)b_syn.dev, n, L, e0, code, s, toric));
+    if (accepts) CK(cudaMemsetAsync(accepts, 0, (size_t)n * Cn * 8, s));
+    sp.accepts = accepts;   // every launch adds to the counts
 
     SweepIO io;
     io.e0 = e0;
@@ -984,6 +991,10 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     }
     if (out_chain_sum && chs_scratch) {
         CK(cudaMemcpyAsync(out_chain_sum, chain_sum, (size_t)n * Cn * 8, cudaMemcpyDeviceToHost, s));
+        any_host = true;
+    }
+    if (acc_scratch) {
+        CK(cudaMemcpyAsync(out_chain_accepts, accepts, (size_t)n * Cn * 8, cudaMemcpyDeviceToHost, s));
         any_host = true;
     }
     if (!stream || any_host) CK(cudaStreamSynchronize(s));
@@ -1448,7 +1459,7 @@ int surfmcmc_decode(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, int3
                     const surfmcmc_opts* opts, uint64_t seed, uint32_t id0, int32_t* out_class,
                     uint64_t* out_class_sum, double* out_log_ratio, void* stream) {
     return surfmcmc_decode_ex(ctx, syndromes, n, L, p, opts, seed, id0, 0, nullptr, nullptr, out_class,
-                              out_class_sum, out_log_ratio, nullptr, nullptr, nullptr, stream);
+                              out_class_sum, out_log_ratio, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
 }  // extern "C"

@@ -190,6 +190,7 @@ struct SweepParams {
     uint64_t* chain_sum;       // [items][C] out, or NULL
     int32_t* chain_n;          // [items][C] out or NULL
     uint32_t* chain_frames;    // per-chain final frames or NULL
+    uint64_t* accepts;         // [items][C] accepted proposals, added to by every launch, or NULL
     int n_groups;
     int grp_nq_max, grp_nc_max;   // largest group (shared-memory layout)
     long long total_units;

@@ -337,7 +337,58 @@ __device__ __forceinline__ int generator_support(int L, int g, int q[4]) {
 // colour sweeps, on the same bit-sliced frames.  IND: independent bit and
 // phase flips (n = |x| + |z|, every real qubit movable) instead of
 // depolarizing noise (n = |x or z|, a qubit movable when its other part is 0).
-template <int G, int LAM, bool SCAN, bool IND>
+// Per-lane count of the accepted proposals of its bundle's chains (bit b =
+// chain b), bit-sliced over kAcptPlanes planes, kept in shared memory after
+// the block's other data; only the instantiations with ACPT = true (one lane
+// split, LAM = 32) count, so the common path carries none of it: word k of lane l of warp w at
+// base + (w (kAcptPlanes + 1) + k) 32 + l, the lane's increment count at
+// k = kAcptPlanes.  Added into the chains' 64-bit counts (atomically: the
+// bundle's LAM lanes share them) before it could overflow and at the end.
+constexpr int kAcptPlanes = 8;
+constexpr uint32_t kAcptCapacity = (1u << kAcptPlanes) - 1u;
+constexpr int kAcptWordsPerWarp = (kAcptPlanes + 1) * 32;
+
+__device__ __forceinline__ uint32_t* acpt_words(uint32_t* smem, const SweepParams& p, int lam) {
+    const int B = 32 / lam;
+    const int warps = blockDim.x >> 5;
+    uint32_t* base = smem + 8 * p.grp_nc_max + warps * (B * bundle_stride(p.grp_nq_max) + warp_aux_words(B));
+    return base + (threadIdx.x >> 5) * kAcptWordsPerWarp + (threadIdx.x & 31);
+}
+
+__device__ __forceinline__ void acpt_clear(uint32_t* a) {
+#pragma unroll
+    for (int k = 0; k <= kAcptPlanes; ++k) a[32 * k] = 0;
+}
+
+template <typename ChainIndex>
+__device__ __forceinline__ void acpt_flush(uint32_t* a, uint32_t valid, uint64_t* accepts, ChainIndex ci_of) {
+    uint32_t pl[kAcptPlanes];
+#pragma unroll
+    for (int k = 0; k < kAcptPlanes; ++k) pl[k] = a[32 * k];
+    for (int b = 0; b < 32; ++b) {
+        if (!((valid >> b) & 1u)) continue;
+        unsigned long long v = 0;
+#pragma unroll
+        for (int k = 0; k < kAcptPlanes; ++k) v |= (unsigned long long)((pl[k] >> b) & 1u) << k;
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(accepts + ci_of(b)), v);
+    }
+    acpt_clear(a);
+}
+
+template <typename ChainIndex>
+__device__ __forceinline__ void acpt_add(uint32_t* a, uint32_t acc, uint32_t valid, uint64_t* accepts,
+                                         ChainIndex ci_of) {
+#pragma unroll
+    for (int k = 0; k < kAcptPlanes; ++k) {
+        if (!acc) break;
+        const uint32_t c = a[32 * k] & acc;
+        a[32 * k] ^= acc;
+        acc = c;
+    }
+    if (++a[32 * kAcptPlanes] == kAcptCapacity) acpt_flush(a, valid, accepts, ci_of);
+}
+
+template <int G, int LAM, bool SCAN, bool IND, bool ACPT>
 __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& gd, long long unit,
                                          uint32_t* smem, const ushort4* tab) {
     constexpr int B = 32 / LAM;                       // bundles per warp
@@ -465,6 +516,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
     }
     OccAcc occ;
     occ.clear();
+    if constexpr (ACPT) acpt_clear(acpt_words(smem, p, LAM));
     const uint32_t qpl = (IND ? 2u : 1u) * (uint32_t)((nq + LAM - 1) / LAM);  // counts per lane and phase
     const uint32_t flush_every = kAccCapacity / qpl;       // phases before the accumulator could overflow
     uint32_t since_flush = 0;
@@ -489,7 +541,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
         auto energy = [&](uint32_t x, uint32_t z) { return x ? (z ? E3 : E1) : (z ? E2 : E0); };
         int n = 0;
         for (int q = 0; q < nq; ++q) n += energy((X[q] >> b) & 1u, (Z[q] >> b) & 1u);
-        uint64_t sum = 0;
+        uint64_t sum = 0, n_acc = 0;
         for (uint32_t t = gd.t_begin; t < gd.t_end; ++t) {
             const bool sample = t >= gd.burn_in;
             for (int step = 0; step < ns; ++step) {
@@ -510,11 +562,13 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
 #pragma unroll
                     for (int k = 0; k < 4; ++k) atomicXor(&own[q[k]], bit);
                     n += dn;
+                    ++n_acc;
                 }
                 if (sample) sum += (uint64_t)n;
             }
         }
         if (mine && p.chain_sum) p.chain_sum[ci_of(b)] += sum;
+        if (mine && p.accepts) p.accepts[ci_of(b)] += n_acc;   // one lane per chain
         scan_n = n;
         __syncwarp();
     } else
@@ -577,6 +631,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                             }
                         }
                     }
+                    if constexpr (ACPT) acpt_add(acpt_words(smem, p, LAM), acc, valid, p.accepts, ci_of);
                     own[sp.x] = o0 ^ acc;
                     own[sp.y] = o1 ^ acc;
                     own[sp.z] = o2 ^ acc;
@@ -588,7 +643,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                 // Finish the queued proposals, one per lane.
                 const uint32_t n_items = min(*q_cnt, (uint32_t)kQueueCap);
                 for (uint32_t i = lane; i < n_items; i += 32) {
-                    const uint32_t* it = q_items + kQueueItem * i;
+                    uint32_t* it = q_items + kQueueItem * i;
                     const int qm = (int)(it[0] & 0xFFFFu), qs = (int)(it[0] >> 16);
                     uint32_t U = it[1];
                     uint32_t acc = it[4];
@@ -598,6 +653,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                     for (int s = 0; s < SLOTS; ++s) qsid[s] = info[1 + s];
                     acc |= bernoulli_range<G, HEAD, NBATCH>(p, U, it[2], it[3], qsid, info[0], t,
                                                             colm | (uint32_t)qm);
+                    if constexpr (ACPT) it[4] = acc;
                     if (acc) {
                         uint32_t* qx = frames + (warp * B + qs) * stride;
                         uint32_t* qown = col < 2 ? qx : qx + nq + 2;
@@ -609,6 +665,16 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                     }
                 }
                 __syncwarp();
+                if constexpr (ACPT) {
+                    // queued proposals of this bundle: counted by its first lane
+                    if (sub == 0 && active)
+                        for (uint32_t i = 0; i < n_items; ++i) {
+                            const uint32_t* it = q_items + kQueueItem * i;
+                            if ((int)(it[0] >> 16) == slot)
+                                acpt_add(acpt_words(smem, p, LAM), it[4], valid, p.accepts, ci_of);
+                        }
+                    __syncwarp();
+                }
             }
             if (t >= gd.burn_in) {
                 accumulate_phase<LAM, IND>(occ, X, Z, nq, sub);
@@ -622,6 +688,9 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
     }
 
     flush_acc<LAM>(occ, sub, valid, p.chain_sum, ci_of);
+    if constexpr (ACPT) {
+        if (active) acpt_flush(acpt_words(smem, p, LAM), valid, p.accepts, ci_of);
+    }
     if (p.state_out && active) {
         uint32_t* st = p.state_out + gd.state_off + (size_t)bid * 2 * nq;
         for (int q = sub; q < nq; q += LAM) {
@@ -659,7 +728,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
 // fill its warps) first by its index, then from a queue counter, in the order
 // the host arranged (largest work first), and rebuilds the support table in
 // shared memory when the group's code size changes.
-template <int G, int LAM, bool SCAN, bool IND>
+template <int G, int LAM, bool SCAN, bool IND, bool ACPT>
 __global__ void __launch_bounds__(128, (G >= 16 ? 6 : 3)) sweep_kernel(const __grid_constant__ SweepParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ long long s_unit;
@@ -687,7 +756,7 @@ __global__ void __launch_bounds__(128, (G >= 16 ? 6 : 3)) sweep_kernel(const __g
             cur = g;
             __syncthreads();
         }
-        run_unit<G, LAM, SCAN, IND>(p, gd, u - gd.unit_base, smem, tab);
+        run_unit<G, LAM, SCAN, IND, ACPT>(p, gd, u - gd.unit_base, smem, tab);
         __syncthreads();
         if (!p.unit_counter) break;
     }
@@ -695,12 +764,13 @@ __global__ void __launch_bounds__(128, (G >= 16 ? 6 : 3)) sweep_kernel(const __g
 
 constexpr int kWarps = 4;
 
-template <int G, int LAM, bool SCAN, bool IND>
+template <int G, int LAM, bool SCAN, bool IND, bool ACPT = false>
 static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
-    const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM);
+    const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM) +
+                        (ACPT ? (size_t)kWarps * kAcptWordsPerWarp * 4 : 0);
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM, SCAN, IND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM, SCAN, IND, ACPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
@@ -713,7 +783,7 @@ static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM, SCAN, IND>, 32 * kWarps,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM, SCAN, IND, ACPT>, 32 * kWarps,
                                                               smem);
         if (e != cudaSuccess) return e;
         const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
@@ -721,14 +791,15 @@ static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
         e = cudaMemsetAsync(p.unit_counter, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return e;
     }
-    sweep_kernel<G, LAM, SCAN, IND><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
+    sweep_kernel<G, LAM, SCAN, IND, ACPT><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int G, int LAM, bool SCAN, bool IND>
 static cudaError_t prepare_t(const SweepParams& p) {
     const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM);
-    return cudaFuncSetAttribute(sweep_kernel<G, LAM, SCAN, IND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(sweep_kernel<G, LAM, SCAN, IND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
 }
 
 template <int G, bool IND>
@@ -758,6 +829,8 @@ static cudaError_t prepare_noise(const SweepParams& p, int lam) {
 template <int G, bool IND>
 static cudaError_t launch_g(const SweepParams& p, int lam, cudaStream_t s) {
     if (p.scan) return lam == 32 ? launch_t<G, 32, true, IND>(p, s) : cudaErrorInvalidValue;
+    // colour sweeps that count accepted proposals: one lane split only
+    if (p.accepts) return lam == 32 ? launch_t<G, 32, false, IND, true>(p, s) : cudaErrorInvalidValue;
     switch (lam) {
         case 2: return launch_t<G, 2, false, IND>(p, s);
         case 4: return launch_t<G, 4, false, IND>(p, s);
