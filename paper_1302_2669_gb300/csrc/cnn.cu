@@ -31,9 +31,11 @@
 //     accumulators (bias + ReLU, logits, or the ReLU gate of the layer
 //     below).  The first layer (2 input channels, K = 18 padded to
 //     32) gathers its operand with producer warps;
-//   weight gradient: D[(tap, ci)][co] = sum_p X[p + tap][ci] dZ[p][co], a
-//     GEMM over positions split across blocks, with a row of ones that yields
-//     the bias gradient; partial sums are added in a fixed order.
+//   weight gradient of the 64-channel layers: D[(tap, ci)][co] =
+//     sum_p X[p + tap][ci] dZ[p][co], a GEMM over positions split across
+//     blocks, with a row of ones that yields the bias gradient; partial sums
+//     are added in a fixed order.  The first layer's (2 input channels, 19
+//     rows) runs on the CUDA cores.
 // The last layer (2 outputs, read and differentiated on the middle lines
 // only: forward fused into the readout, backward), the readout, loss and
 // Adam steps run on the CUDA cores.
@@ -60,10 +62,8 @@ constexpr int kHid = 64;          // hidden channels
 constexpr int kOut = 2;           // flip logits per position (last layer)
 constexpr float kClip = 1e-6f;    // |M| <= 1 - kClip
 constexpr int kConvProd = 8;      // gather warps of the first layer's conv kernel
-constexpr int kWgProd = 8;        // gather warps of the weight-gradient kernel
 constexpr int kEpiWarps = 4;      // accumulator-draining warps
 constexpr int kConvThreads = (kConvProd + kEpiWarps + 1) * 32;
-constexpr int kWgThreads = (kWgProd + kEpiWarps + 1) * 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWaitTimeout = 1;   // error codes written to the device flag
 constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
@@ -679,233 +679,262 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient on tcgen05: D[R][co] = sum_p A[R][p] dZ[p][co] with
-// A[(tap, ci)][p] = X[p + offset(tap)][ci] (zero outside the map) and row
-// R = 9 CIN all ones (bias gradient).  Grid (slices, row tiles); each block
-// sums one slice of the positions into partial[slice][R][co].
+// Weight gradient of the 64-channel layers on tcgen05: D[(tap, ci)][co] =
+// sum_p X[p + shift(tap)][ci] dZ[p][co], and the bias gradient sum_p dZ[p][co].
+// A GEMM with K = positions whose operands are taken MN-major straight from
+// the [position][channel] tensors: per chunk of 64 positions one TMA copy
+// brings X's rows with a halo of P + 1 on each side, another dZ's 64 rows
+// (128-byte swizzle).  Tap t's operand is the 64 rows starting at halo row
+// P + 1 + shift(t): for every position (K) its 64 channels (M) are one
+// 128-byte row.  Two taps side by side along M make M = 128 (the step between
+// the two 64-channel atoms is the descriptor's leading byte offset), so five
+// MMA groups cover taps (0,1) .. (6,7), (8, ones); the ones atom is a constant
+// tile whose channel 0 is 1.0, giving the bias gradient in row 576.  D of
+// pair j is accumulated in tensor-memory columns 64 j .. 64 j + 63 over the
+// block's chunks; row 128 j + r of the block's partial sums is R = 64 tap + ci.
+// Each block takes a contiguous range of chunks; the partial sums are added
+// over the blocks in order.
 // ---------------------------------------------------------------------------
 struct WgradArgs {
-    const bf16* x;      // [M][CIN] input of the layer
-    const bf16* dz;     // [M][64] gradient of the layer's pre-activation
-    float* partial;     // [slices][row_tiles * 128][64]
+    CUtensorMap xmap;   // X [M_alloc][64] bf16, box 64 x wg_halo_rows(L), 128-byte swizzle
+    CUtensorMap dzmap;  // dZ [M_alloc][64] bf16, box 64 x 64, 128-byte swizzle
+    float* partial;     // [slices][640][64]
     long long M;
     int L;
+    int halo_rows;
     int* err;
 };
 
-constexpr int kWgS = 4;                         // pipeline depth
-constexpr int kWgAStage = 128 * 64 * 2;         // 128 rows x 64 positions
-constexpr int kWgBStage = 64 * 64 * 2;          // 64 channels x 64 positions
-constexpr size_t kWgSmem = (size_t)kWgS * (kWgAStage + kWgBStage) + 1024;
+constexpr int kWgS = 4;                          // pipeline depth
+__host__ __device__ constexpr int wg_halo_rows(int L) { return (64 + 2 * (L + 3) + 7) / 8 * 8; }
+constexpr int kWgXStage = wg_halo_rows(SURFMCMC_MAX_L) * 128;   // 17 KB at L = 31
+constexpr int kWgDStage = 64 * 128;
+constexpr int kWgStage = kWgXStage + kWgDStage;
+static_assert(kWgXStage % 1024 == 0 && wg_halo_rows(SURFMCMC_MAX_L) <= 256, "halo tile");
+// stages + the ones tile; requested as 120 KB so that one block holds an SM
+// (its 512 tensor-memory columns would stall a second block's allocation)
+constexpr size_t kWgSmemNeed = (size_t)kWgS * kWgStage + kWgDStage + 1024;
+constexpr size_t kWgSmem = 120 * 1024;
+static_assert(kWgSmemNeed <= kWgSmem, "weight-gradient shared memory");
+constexpr int kWgPairs = 5;
+constexpr int kWgTmaThreads = 6 * 32;            // TMA warp, MMA warp, 4 accumulator warps
+constexpr int kWgRows = 128 * kWgPairs;          // 640 rows of partial sums per block
 
-// 8 x 8 transpose of 16-bit elements across each group of 8 lanes: lane i
-// holds row i (8 elements in 4 words, element j at half j%2 of word j/2) and
-// receives column i.  Three xor-butterfly stages (4, 2, 1 lanes apart) swap
-// the off-diagonal blocks of 4, 2 and 1 columns.
-__device__ __forceinline__ uint4 transpose8(uint4 v, int l8) {
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    {
-        const bool up = l8 & 4;
-        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, up ? w[0] : w[2], 4);
-        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, up ? w[1] : w[3], 4);
-        if (up) {
-            w[0] = r0;
-            w[1] = r1;
-        } else {
-            w[2] = r0;
-            w[3] = r1;
-        }
-    }
-    {
-        const bool up = l8 & 2;
-        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, up ? w[0] : w[1], 2);
-        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, up ? w[2] : w[3], 2);
-        if (up) {
-            w[0] = r0;
-            w[2] = r1;
-        } else {
-            w[1] = r0;
-            w[3] = r1;
-        }
-    }
-    {
-        const bool up = l8 & 1;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t r = __shfl_xor_sync(0xffffffffu, w[k], 1);
-            w[k] = up ? __byte_perm(r, w[k], 0x7632) : __byte_perm(w[k], r, 0x5410);
-        }
-    }
-    return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-template <int CIN>
-__global__ void __launch_bounds__(kWgThreads, 2) wgrad_kernel(WgradArgs a) {
-    constexpr uint32_t IDESC = idesc_bf16(128, 64);
+__global__ void __launch_bounds__(kWgTmaThreads, 1) wgrad_kernel(const __grid_constant__ WgradArgs a) {
+    constexpr uint32_t IDESC = idesc_bf16(128, 64) | (1u << 15) | (1u << 16);   // A, B MN-major
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + kWgS * kWgAStage;
+    uint8_t* sOnes = smem + kWgS * kWgStage;     // 64 rows: channel 0 = 1.0
     __shared__ __align__(8) uint64_t full[kWgS], empty[kWgS], accf;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
-    const int L = a.L;
+    const int L = a.L, P1 = L + 3;
     const long long n_chunks = (M + 63) / 64;
-    const int slice = blockIdx.x, n_slices = gridDim.x, mt = blockIdx.y;
-    const long long c_begin = n_chunks * slice / n_slices, c_end = n_chunks * (slice + 1) / n_slices;
+    const long long c_begin = n_chunks * blockIdx.x / gridDim.x, c_end = n_chunks * (blockIdx.x + 1) / gridDim.x;
 
+    for (int i = tid; i < kWgDStage / 16; i += blockDim.x) {
+        // row r, 16-byte chunk c (stored at chunk c ^ (r & 7)): channel 0 is chunk 0
+        const int r = i >> 3, c = i & 7;
+        reinterpret_cast<uint4*>(sOnes)[i] = make_uint4((c ^ (r & 7)) == 0 ? 0x3F80u : 0u, 0u, 0u, 0u);
+    }
     if (tid == 0) {
         for (int s = 0; s < kWgS; ++s) {
-            mbar_init(&full[s], kWgProd * 32);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(&accf, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kWgProd + kEpiWarps) tmem_alloc(&tmem_slot, 64);
+    fence_async_smem();
+    if (warp == 1) tmem_alloc(&tmem_slot, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp < kWgProd) {
-        // Blocks of 8 rows x 8 positions (one core matrix) per group of 8
-        // lanes: lane l8 loads position 8 pg + l8 (8 channels, 16 bytes), the
-        // group transposes, lane l8 stores row 8 rg + l8.
-        constexpr int kGroups = kWgProd * 4;
-        const int grp = tid >> 3, l8 = tid & 7;
-        const uint16_t* xs = reinterpret_cast<const uint16_t*>(a.x);
-        uint32_t q = 0;
-        for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
-            const uint32_t stage = q % kWgS, use = q / kWgS;
-            if (use > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)))
-                break;  // warp-uniform: the loop below has warp-wide shuffles
-            uint8_t* stA = sA + stage * kWgAStage;
-            uint8_t* stB = sB + stage * kWgBStage;
-            if constexpr (CIN == 64) {
-#pragma unroll
-                for (int pass = 0; pass < 128 / kGroups; ++pass) {
-                    const int b = grp + kGroups * pass, rg = b >> 3, pg = b & 7;
-                    const int R0 = mt * 128 + rg * 8, j = pg * 8 + l8;
-                    const long long pos = ch * 64 + j;
-                    uint4 v = make_uint4(0, 0, 0, 0);
-                    if (R0 < 9 * CIN) {
-                        const int tap = R0 / CIN, ci0 = R0 % CIN;
-                        const long long src = pos + tap_shift(tap, L);
-                        if (pos < M && src >= 0 && src < M)
-                            v = __ldg(reinterpret_cast<const uint4*>(a.x + src * CIN + ci0));
-                    } else if (R0 == 9 * CIN && pos < M) {
-                        v.x = 0x3F80u;  // row 9 CIN: 1.0 (bias gradient)
-                    }
-                    v = transpose8(v, l8);
-                    *reinterpret_cast<uint4*>(stA + core_off(rg * 8 + l8, pg, 8)) = v;
-                }
-            } else {
-                // 2 input channels: row R = tid holds tap R/2, channel R%2;
-                // row 18 is the row of ones, rows above are zero
-                const int R = tid;
-                for (int g = 0; g < 8 && tid < 128; ++g) {
-                    uint32_t w[4] = {0u, 0u, 0u, 0u};
-                    if (R <= 9 * CIN) {
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            uint32_t e[2];
-#pragma unroll
-                            for (int k = 0; k < 2; ++k) {
-                                const long long pos = ch * 64 + g * 8 + h * 2 + k;
-                                uint32_t val = 0;
-                                if (pos < M) {
-                                    if (R < 9 * CIN) {
-                                        const int tap = R / CIN, ci = R % CIN;
-                                        const long long src = pos + tap_shift(tap, L);
-                                        if (src >= 0 && src < M) val = __ldg(xs + src * CIN + ci);
-                                    } else {
-                                        val = 0x3F80u;
-                                    }
-                                }
-                                e[k] = val;
-                            }
-                            w[h] = e[0] | (e[1] << 16);
-                        }
-                    }
-                    *reinterpret_cast<uint4*>(stA + core_off(R, g, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
-                }
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)a.halo_rows * 128 + kWgDStage;
+            uint32_t q = 0;
+            for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
+                const uint32_t stage = q % kWgS, use = q / kWgS;
+                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                uint8_t* st = smem + stage * kWgStage;
+                mbar_expect_tx(&full[stage], bytes);
+                tma_load_2d(st, &a.xmap, 0, (int)(ch * 64 - P1), &full[stage]);
+                tma_load_2d(st + kWgXStage, &a.dzmap, 0, (int)(ch * 64), &full[stage]);
             }
-#pragma unroll
-            for (int pass = 0; pass < 64 / kGroups; ++pass) {
-                const int b = grp + kGroups * pass, cg = b >> 3, pg = b & 7;
-                const long long pos = ch * 64 + pg * 8 + l8;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (pos < M) v = __ldg(reinterpret_cast<const uint4*>(a.dz + pos * 64 + cg * 8));
-                v = transpose8(v, l8);
-                *reinterpret_cast<uint4*>(stB + core_off(cg * 8 + l8, pg, 8)) = v;
-            }
-            fence_async_smem();
-            mbar_arrive(&full[stage]);
+            for (uint32_t k = q > (uint32_t)kWgS ? q - kWgS : 0; k < q; ++k)
+                mbar_drain(&full[k % kWgS], (k / kWgS) & 1, a.err);
         }
-    } else if (warp < kWgProd + kEpiWarps) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // descriptors as 32-bit halves: start / 16 in bits 0-13, the leading
+            // byte offset / 16 (the second M atom) in bits 16-29 of the low half
+            const uint32_t base = smem_u32(smem), ones = smem_u32(sOnes);
+            const uint64_t d0 = smem_desc_sw128(base);
+            const uint32_t a_hi = (uint32_t)(d0 >> 32);
+            const uint32_t lo0 = (uint32_t)d0 & 0xFFFFu;   // start field of the smem base, no offset
+            uint32_t a_off[kWgPairs];   // start of tap 2j's window relative to its stage / 16, with the pair's offset
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t1 = 2 * j, t2 = 2 * j + 1;
+                a_off[j] = (uint32_t)((P1 + tap_shift(t1, L)) * 8) |
+                           ((uint32_t)((tap_shift(t2, L) - tap_shift(t1, L)) * 8) << 16);
+            }
+            a_off[4] = (uint32_t)((P1 + tap_shift(8, L)) * 8);
+            uint32_t q = 0;
+            bool ok = true;
+            for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
+                const uint32_t stage = q % kWgS, use = q / kWgS;
+                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = lo0 + stage * (kWgStage / 16);
+                // pair 4: the ones atom lies ones - window bytes after tap 8's window
+                const uint32_t w8 = base + stage * kWgStage + (P1 + tap_shift(8, L)) * 128;
+                const uint32_t off4 = a_off[4] | (((ones - w8) >> 4) << 16);
+                const uint32_t b_lo = st + (uint32_t)(kWgXStage / 16) | ((uint32_t)(kWgDStage >> 4) << 16);
+#pragma unroll
+                for (int j = 0; j < kWgPairs; ++j) {
+                    const uint32_t a_lo = st + (j < 4 ? a_off[j] : off4);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        mma_bf16_lh(tmem + 64 * j, a_lo + ks * 128, a_hi, b_lo + ks * 128, a_hi, IDESC,
+                                    (ch > c_begin || ks > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[stage]);
+            }
+            // completes after every MMA of the block (also on the abort path)
+            mma_commit(&accf);
+            if (!ok || c_end == c_begin) mbar_drain(&accf, 0, a.err);
+        }
+    } else {
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
-        float* out = a.partial + (((long long)slice * gridDim.y + mt) * 128 + row) * 64;
-        if (c_end > c_begin) {
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err));
-            if (ok) {
-                tc_fence_after();
+        float* out = a.partial + ((long long)blockIdx.x * kWgRows + row) * 64;
+        bool ok = c_end > c_begin;
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err));
+        if (ok) tc_fence_after();
+#pragma unroll 1
+        for (int j = 0; j < kWgPairs; ++j) {
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + cc * 16, v);
+            for (int cc = 0; cc < 4; ++cc) {
+                float v[16];
+                if (ok) {
+                    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 64 * j + cc * 16, v);
+                } else {
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4*>(out + cc * 16 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    for (int i = 0; i < 16; ++i) v[i] = 0.0f;
                 }
-            }
-        } else {
-            for (int j = 0; j < 64; j += 4) *reinterpret_cast<float4*>(out + j) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    } else if (lane == 0) {
-        uint32_t q = 0;
-        bool ok = true;
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
-            const uint32_t stage = q % kWgS, use = q / kWgS;
-            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t ad = smem_desc(a0 + stage * kWgAStage + ks * 256, 128, 8 * 128);
-                const uint64_t bd = smem_desc(b0 + stage * kWgBStage + ks * 256, 128, 8 * 128);
-                mma_bf16(tmem, ad, bd, IDESC, (ch > c_begin || ks > 0) ? 1u : 0u);
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(out + (long long)j * 128 * 64 + cc * 16 + i) =
+                        make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
             }
-            mma_commit(&empty[stage]);
         }
-        // completes after every MMA of the block (also on the abort path)
-        mma_commit(&accf);
-        if (!ok || c_end == c_begin) mbar_drain(&accf, 0, a.err);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kWgProd + kEpiWarps) tmem_dealloc(tmem, 64);
+    if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-// partial[s][R][co] summed over s in order -> flat gradient of layer l.
-__global__ void wgrad_reduce_kernel(const float* partial, int n_slices, int rows_pad, int cin, float* grad_w,
-                                    float* grad_b) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // R * 64 + co
+// The first layer's weight and bias gradients on the CUDA cores (2 input
+// channels: 18 weights and a bias per output channel, too thin a GEMM for the
+// tensor cores): partial[s][R][co] = sum over the slice's positions p of
+// X[p + shift(tap)][ci] dZ[p][co] (R = 2 tap + ci), R = 18: sum of dZ[p][co].
+// Block s walks its slice in tiles of kWg0Tile positions; the tile's inputs
+// and their halo are staged in shared memory as float pairs (zero outside the
+// batch), its dZ rows with 16-byte loads.  Threads: 4 position groups x 64 output channels; group g takes the
+// tile's positions g, g + 4, ..; the groups are added in order.  dZ is zero
+// on the map borders, so the sums run over the padded positions as they are.
+constexpr int kWg0Threads = 256;
+constexpr int kWg0Rows = 19;
+constexpr int kWg0Tile = 128;
+
+__global__ void __launch_bounds__(kWg0Threads, 3) wgrad0_kernel(const bf16* x, const bf16* dz, long long M, int L,
+                                                            float* partial) {
+    __shared__ float2 sx[kWg0Tile + 2 * (SURFMCMC_MAX_L + 3)];
+    __shared__ __align__(16) uint16_t sdz[kWg0Tile][64];
+    __shared__ float red[4][kWg0Rows][64];
+    const int co = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int P1 = L + 3;
+    const long long begin = M * blockIdx.x / gridDim.x, end = M * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t* xw = reinterpret_cast<const uint32_t*>(x);   // both channels of a position
+    int sh[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) sh[t] = P1 + tap_shift(t, L);
+    float acc[kWg0Rows];
+#pragma unroll
+    for (int r = 0; r < kWg0Rows; ++r) acc[r] = 0.0f;
+    for (long long t0 = begin; t0 < end; t0 += kWg0Tile) {
+        const int n = (int)(end - t0 < kWg0Tile ? end - t0 : kWg0Tile);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n + 2 * P1; i += blockDim.x) {
+            const long long src = t0 - P1 + i;
+            const uint32_t v = src >= 0 && src < M ? __ldg(xw + src) : 0u;
+            sx[i] = make_float2(bf16_lo(v), bf16_hi(v));
+        }
+#pragma unroll
+        for (int k = 0; k < kWg0Tile * 8 / kWg0Threads; ++k) {
+            const int i = threadIdx.x + k * kWg0Threads, r = i >> 3, c = i & 7;
+            const uint4 v = r < n ? __ldg(reinterpret_cast<const uint4*>(dz + (t0 + r) * 64) + c) : make_uint4(0, 0, 0, 0);
+            reinterpret_cast<uint4*>(&sdz[r][0])[c] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int j = g; j < n; j += 4) {
+            const float d = __uint_as_float((uint32_t)sdz[j][co] << 16);
+            acc[18] += d;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float2 v = sx[j + sh[t]];
+                acc[2 * t] = fmaf(v.x, d, acc[2 * t]);
+                acc[2 * t + 1] = fmaf(v.y, d, acc[2 * t + 1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kWg0Rows; ++r) red[g][r][co] = acc[r];
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWg0Rows * 64; i += blockDim.x) {
+        const int r = i >> 6, c = i & 63;
+        partial[((long long)blockIdx.x * kWg0Rows + r) * 64 + c] =
+            ((red[0][r][c] + red[1][r][c]) + red[2][r][c]) + red[3][r][c];
+    }
+}
+
+// partial[s][R][co] summed over s -> flat gradient of layer l.  A block of 8
+// warps takes 32 consecutive outputs (R, co); warp w adds the slices w, w + 8,
+// .. in order and the 8 warp sums are added in order.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* partial, int n_slices, int rows_pad, int cin,
+                                                           float* grad_w, float* grad_b) {
+    __shared__ float part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;  // R * 64 + co
     const int R = i >> 6, co = i & 63;
-    if (R > 9 * cin) return;
+    const bool valid = R <= 9 * cin;
     float s = 0.0f;
-    for (int k = 0; k < n_slices; ++k) s += partial[((long long)k * rows_pad + R) * 64 + co];
-    if (R < 9 * cin) grad_w[(long long)co * 9 * cin + R] = s;
-    else grad_b[co] = s;
+    if (valid) {
+#pragma unroll 4
+        for (int k = w; k < n_slices; k += 8) s += partial[((long long)k * rows_pad + R) * 64 + co];
+    }
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && valid) {
+        float t = part[0][lane];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) t += part[j][lane];
+        if (R < 9 * cin) grad_w[(long long)co * 9 * cin + R] = t;
+        else grad_b[co] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1154,20 +1183,34 @@ __global__ void conv5_wgrad_item_kernel(const float* dz5, const bf16* a4, int L,
     }
 }
 
-// Sum over the items in order: dW5[co][j] = sum_item S[item][co][j],
-// db5[co] = sum_item Sb[item][co].
-__global__ void conv5_wgrad_kernel(const float* S, const float* Sb, long long n, float* grad_w, float* grad_b) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kOut * 576) {
-        const int co = i / 576, j = i - co * 576;
-        float s = 0.0f;
-        for (long long k = 0; k < n; ++k) s += S[(k * 2 + co) * 576 + j];
-        grad_w[i] = s;
-    } else if (i < kOut * 576 + kOut) {
+// Sum over the items: dW5[co][j] = sum_item S[item][co][j], db5[co] =
+// sum_item Sb[item][co].  A block of 8 warps takes 32 consecutive outputs;
+// warp w adds the items w, w + 8, .. in order and the 8 warp sums are added
+// in order.
+__global__ void __launch_bounds__(256) conv5_wgrad_kernel(const float* S, const float* Sb, long long n, float* grad_w,
+                                                          float* grad_b) {
+    __shared__ float part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const bool is_w = i < kOut * 576, valid = i < kOut * 576 + kOut;
+    float s = 0.0f;
+    if (is_w) {
+        const int co = i / 576, jj = i - co * 576;
+#pragma unroll 4
+        for (long long k = w; k < n; k += 8) s += S[(k * 2 + co) * 576 + jj];
+    } else if (valid) {
         const int co = i - kOut * 576;
-        float s = 0.0f;
-        for (long long k = 0; k < n; ++k) s += Sb[k * 2 + co];
-        grad_b[co] = s;
+#pragma unroll 4
+        for (long long k = w; k < n; k += 8) s += Sb[k * 2 + co];
+    }
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && valid) {
+        float t = part[0][lane];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) t += part[k][lane];
+        if (is_w) grad_w[i] = t;
+        else grad_b[i - kOut * 576] = t;
     }
 }
 
@@ -1229,6 +1272,8 @@ struct CnnNet {
     CUtensorMap map_act[4], map_dz[2];
     // the same tensors in boxes of 128 rows (output tiles, ReLU gates)
     CUtensorMap tile_act[4], tile_dz[2];
+    // weight gradient: layer inputs act[0..2] with its halo, dz in 64-row boxes
+    CUtensorMap wg_act[3], wg_dz[2];
     std::vector<void*> allocs;
 };
 
@@ -1247,8 +1292,7 @@ cudaError_t prepare_kernels() {
     if ((e = set_smem(conv1_kernel, kC1Smem))) return e;
     if ((e = set_smem(conv_tma_kernel<64, kEpiRelu>, conv_tma_smem_bytes<64, kEpiRelu>()))) return e;
     if ((e = set_smem(conv_tma_kernel<64, kEpiMask>, conv_tma_smem_bytes<64, kEpiMask>()))) return e;
-    if ((e = set_smem(wgrad_kernel<2>, kWgSmem))) return e;
-    if ((e = set_smem(wgrad_kernel<64>, kWgSmem))) return e;
+    if ((e = set_smem(wgrad_kernel, kWgSmem))) return e;
     done = true;
     return cudaSuccess;
 }
@@ -1292,33 +1336,47 @@ cudaError_t make_map(CUtensorMap* map, void* base, long long rows, int box_rows)
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int wgrad_slices(long long M, int row_tiles, int sms) {
-    const long long chunks = (M + 63) / 64;
-    long long k = (2LL * sms + row_tiles - 1) / row_tiles;
-    if (k > kMaxSplits) k = kMaxSplits;
-    if (k > chunks) k = (int)chunks;
-    return (int)(k < 1 ? 1 : k);
+// First layer: CUDA cores, then the in-order sum over the slices.
+cudaError_t launch_wgrad0(const CnnNet* net, const bf16* x, const bf16* dz, long long M, cudaStream_t s) {
+    long long slices = 2LL * net->sms;
+    const long long max_slices = (long long)kMaxSplits * kWgRows / kWg0Rows;   // the partial buffer
+    if (slices > max_slices) slices = max_slices;
+    if (slices > M) slices = M;
+    if (slices < 1) slices = 1;
+    wgrad0_kernel<<<(unsigned)slices, kWg0Threads, 0, s>>>(x, dz, M, net->L, net->partial);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    wgrad_reduce_kernel<<<(kWg0Rows * 64 + 31) / 32, 256, 0, s>>>(net->partial, (int)slices, kWg0Rows, 2,
+                                                                     net->grad + layer_woff(0),
+                                                                     net->grad + layer_boff(0));
+    return cudaGetLastError();
 }
 
-template <int CIN>
-cudaError_t launch_wgrad(const CnnNet* net, const bf16* x, const bf16* dz, long long M, int layer,
-                         cudaStream_t s) {
-    const int row_tiles = (9 * CIN + 1 + 127) / 128;
-    const int slices = wgrad_slices(M, row_tiles, net->sms);
+// Weight gradient of layer l (1..3): X = its input, dZ = the gradient of its
+// pre-activation; rows of dZ past the batch in the last 64-position chunk
+// are zeroed first (the tensor map spans the whole buffer).
+cudaError_t launch_wgrad(const CnnNet* net, int xi, int dzi, long long M, int layer, cudaStream_t s) {
+    const long long chunks = (M + 63) / 64;
+    if (chunks == 0) return cudaSuccess;
+    const long long m_alloc = net->max_batch * net->P * net->P;
+    const long long tail_end = chunks * 64 < m_alloc ? chunks * 64 : m_alloc;
+    cudaError_t e;
+    if (tail_end > M && (e = cudaMemsetAsync(net->dz[dzi] + M * 64, 0, (size_t)(tail_end - M) * 128, s))) return e;
+    const int slices = (int)(chunks < net->sms ? chunks : net->sms);
     WgradArgs a;
-    a.x = x;
-    a.dz = dz;
+    memset(&a, 0, sizeof a);
+    a.xmap = net->wg_act[xi];
+    a.dzmap = net->wg_dz[dzi];
     a.partial = net->partial;
     a.M = M;
     a.L = net->L;
+    a.halo_rows = wg_halo_rows(net->L);
     a.err = net->err;
-    wgrad_kernel<CIN><<<dim3(slices, row_tiles), kWgThreads, kWgSmem, s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e) return e;
-    const int outs = (9 * CIN + 1) * 64;
-    wgrad_reduce_kernel<<<(outs + 255) / 256, 256, 0, s>>>(net->partial, slices, row_tiles * 128, CIN,
-                                                           net->grad + layer_woff(layer),
-                                                           net->grad + layer_boff(layer));
+    wgrad_kernel<<<slices, kWgTmaThreads, kWgSmem, s>>>(a);
+    if ((e = cudaGetLastError())) return e;
+    wgrad_reduce_kernel<<<(577 * 64 + 31) / 32, 256, 0, s>>>(net->partial, slices, kWgRows, 64,
+                                                               net->grad + layer_woff(layer),
+                                                               net->grad + layer_boff(layer));
     return cudaGetLastError();
 }
 
@@ -1391,7 +1449,7 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
     // last layer (CUDA cores)
     conv5_wgrad_item_kernel<<<(unsigned)n, 576, 0, s>>>(net->dz5, net->act[3], L, net->S5, net->Sb5);
     if ((e = cudaGetLastError())) return e;
-    conv5_wgrad_kernel<<<(kOut * 576 + kOut + 255) / 256, 256, 0, s>>>(net->S5, net->Sb5, n,
+    conv5_wgrad_kernel<<<(kOut * 576 + kOut + 31) / 32, 256, 0, s>>>(net->S5, net->Sb5, n,
                                                                         net->grad + layer_woff(4),
                                                                         net->grad + layer_boff(4));
     if ((e = cudaGetLastError())) return e;
@@ -1407,7 +1465,7 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
     a.err = net->err;
     int cur = 0;
     for (int l = 3; l >= 1; --l) {
-        if ((e = launch_wgrad<64>(net, net->act[l - 1], net->dz[cur], M, l, s))) return e;
+        if ((e = launch_wgrad(net, l - 1, cur, M, l, s))) return e;
         a.map = net->map_dz[cur];
         a.out_map = net->tile_dz[cur ^ 1];
         a.mask_map = net->tile_act[l - 1];
@@ -1415,7 +1473,7 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
         if ((e = launch_conv_tma<64, kEpiMask>(net, a, s))) return e;
         cur ^= 1;
     }
-    return launch_wgrad<2>(net, net->x0, net->dz[cur], M, 0, s);
+    return launch_wgrad0(net, net->x0, net->dz[cur], M, s);
 }
 
 cudaError_t cnn_adam_dev(CnnNet* net, float lr, cudaStream_t s) {
@@ -1540,13 +1598,15 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     na(&net->loss, 4);
     na(&net->S5, (size_t)max_batch * 2 * 576 * 4);
     na(&net->Sb5, (size_t)max_batch * 2 * 4);
-    na(&net->partial, (size_t)kMaxSplits * 640 * 64 * 4);
+    na(&net->partial, (size_t)(net->sms > kMaxSplits ? net->sms : kMaxSplits) * kWgRows * 64 * 4);
     na(&net->err, 4);
     const int halo = halo_tile_rows(L);
     for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->map_act[l], net->act[l], M, halo);
     for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->map_dz[l], net->dz[l], M, halo);
     for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->tile_act[l], net->act[l], M, 128);
     for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->tile_dz[l], net->dz[l], M, 128);
+    for (int l = 0; l < 3 && e == cudaSuccess; ++l) e = make_map(&net->wg_act[l], net->act[l], M, wg_halo_rows(L));
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->wg_dz[l], net->dz[l], M, 64);
     if (e == cudaSuccess) e = cudaMemset(net->err, 0, 4);
     if (e == cudaSuccess) e = cudaMemset(net->theta, 0, P);
     if (e == cudaSuccess) e = cudaMemset(net->m1, 0, P);
