@@ -52,7 +52,7 @@ INT_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) of one sampled sweep launch per syndrome of the
 # L = 13, 4 x 16-chain workload, from one ncu capture at 8,192 syndromes
-# (41,096,960 B read + 1,280 B written: the bit-sliced chain state handed
+# (41,100,032 B read + 57,856 B written: the bit-sliced chain state handed
 # over from the annealing launch, proportional to the syndromes).
 SWEEP_DRAM_BYTES_PER_SYNDROME = (41100032 + 57856) / 8192
 
