@@ -91,16 +91,16 @@ def test_decode_chain_counts(ctx, pkg, R):
         _compare_decode(out, ref, i, 4 * R, L)
 
 
-def test_config1_subset(ctx, pkg):
-    """L=5 (41 qubits), p=0.15, 4 classes x 4 chains, 2000 sweeps: 40 of the
-    200 syndromes against the oracle (ragged bundle tail: 40 is not a
-    multiple of 2 syndromes per bundle plus one extra)."""
+def test_config1_all_200(ctx, pkg):
+    """The small workload in full: L=5 (41 qubits), p=0.15, 4 classes x 4
+    chains, 2000 sweeps, all 200 syndromes (syndrome seed 1001, decoder seed
+    1101) against the oracle."""
     L, p, R, sweeps = 5, 0.15, 4, 2000
     syn, _ = _oracle_syndromes(1001, 200, L, p)
     opts = pkg.Opts(chains_per_class=R, n_sweeps=sweeps)
     out = ctx.decode_ex(torch.from_numpy(syn).cuda(), L, p, opts, seed=1101, id0=0)
     torch.cuda.synchronize()
-    idx = list(range(0, 200, 5))
+    idx = list(range(200))
     refs = O.decode_batch(L, p, 4, R, sweeps, 1101, idx, syn[idx])
     for i, ref in zip(idx, refs):
         _compare_decode(out, ref, i, 4 * R, L)
