@@ -417,7 +417,8 @@ int surfmcmc_decode_noalloc(const uint8_t* syndromes, int64_t n, int32_t L, doub
  *   Network: five 3x3 convolutions with zero padding, 2 -> 64 -> 64 -> 64 ->
  *   64 -> 2 channels, bias, ReLU after the first four.  Weights and
  *   activations are bfloat16 (round to nearest even), sums float32 (tensor
- *   cores).
+ *   cores; the last layer only at the 2L outputs the readout reads, on the
+ *   CUDA cores).
  *   Readout: class k = a + 2b, a (b) the parity of an error's sigma_x
  *   (sigma_z) part on qubit column (row) 0.  With e0 the decoder's pure error
  *   (surfmcmc_start_frames) of class code a0 + 2 b0 and m = (L-1) div 2, the
