@@ -476,6 +476,16 @@ int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream);
  * a, and a equals that decision.  The others continue; at n_sweeps every
  * syndrome stops.  A syndrome that never stops early gets exactly the
  * results of surfmcmc_decode; tau = +infinity reproduces surfmcmc_decode.
+ *   reorder 1 (budget reordering): at the first checkpoint every syndrome
+ *   that goes on has the chains of the network's two least likely classes
+ *   continue as further replicas of its two most likely ones (classes
+ *   ranked by log p, ties to the lower class: a, b, c, d; slot c R + r takes
+ *   the state of slot a R + r, slot d R + r that of b R + r, and keeps its
+ *   own random stream); the sums of c and d are frozen there.  From then on
+ *   the decision is the class with the smallest mean: a and b over their own
+ *   chains since the burn-in plus their replicas since that checkpoint, c
+ *   and d over the frozen sums (exact comparison, lowest class on ties), and
+ *   out_class_sum holds those sums.  reorder 0: no reordering.
  *   out_class [n] int32: the decision at the syndrome's stop.
  *   out_class_sum [n][4] uint64 (may be NULL): the class sums at the stop.
  *   out_sweeps [n] uint32 (may be NULL): the sweeps run (the stop).
@@ -483,7 +493,8 @@ int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream);
  * every checkpoint (to size the next chunk).  EINVAL: bad arguments, a net
  * for another L, chunk_sweeps 0, tau NaN. */
 int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* syndromes, int64_t n, int32_t L,
-                          double p, const surfmcmc_opts* opts, uint32_t chunk_sweeps, float tau, uint64_t seed,
+                          double p, const surfmcmc_opts* opts, uint32_t chunk_sweeps, float tau, int32_t reorder,
+                          uint64_t seed,
                           uint32_t id0, int32_t* out_class, uint64_t* out_class_sum, uint32_t* out_sweeps,
                           void* stream);
 

@@ -135,8 +135,8 @@ def lib():
         L.surfmcmc_cnn_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
         L.surfmcmc_cnn_status.argtypes = [vp, vp]
         L.surfmcmc_cnn_soft_targets.argtypes = [vp, i64, vp, vp]
-        L.surfmcmc_decode_early.argtypes = [vp, vp, vp, i64, i32, dbl, C.POINTER(_Opts), u32, C.c_float, u64, u32, vp,
-                                            vp, vp, vp]
+        L.surfmcmc_decode_early.argtypes = [vp, vp, vp, i64, i32, dbl, C.POINTER(_Opts), u32, C.c_float, i32, u64, u32,
+                                            vp, vp, vp, vp]
         L.surfmcmc_set_timing.argtypes = [vp, C.c_int]
         L.surfmcmc_sweep_time.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         _lib = L
@@ -332,7 +332,7 @@ class Context:
         return cls, csum, lr
 
     def decode_early(self, net, syndromes, L, p, opts: Opts | None = None, chunk_sweeps=64, tau=float("inf"), seed=0,
-                     id0=0, stream=None):
+                     id0=0, reorder=False, stream=None):
         """surfmcmc_decode_early; returns (class [n], class_sum [n][4], sweeps [n])."""
         opts = opts or Opts()
         n = syndromes.shape[0]
@@ -342,7 +342,8 @@ class Context:
         st = stream if stream is not None else _stream_of(syndromes, cls)
         o = opts.c()
         self._check(lib().surfmcmc_decode_early(self._h, net._h, _ptr(syndromes), n, L, p, C.byref(o), chunk_sweeps,
-                                                tau, seed, id0, _ptr(cls), _ptr(csum), _ptr(sw), st))
+                                                tau, 1 if reorder else 0, seed, id0, _ptr(cls), _ptr(csum), _ptr(sw),
+                                                st))
         return cls, csum, sw
 
     def autotune(self, L, chains_per_class, p, n_probe=4096, sweeps=20):

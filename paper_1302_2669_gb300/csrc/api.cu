@@ -1301,9 +1301,9 @@ int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, do
 }
 
 int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* syndromes, int64_t n, int32_t L,
-                          double p, const surfmcmc_opts* opts_in, uint32_t chunk_sweeps, float tau, uint64_t seed,
-                          uint32_t id0, int32_t* out_class, uint64_t* out_class_sum, uint32_t* out_sweeps,
-                          void* stream) {
+                          double p, const surfmcmc_opts* opts_in, uint32_t chunk_sweeps, float tau, int32_t reorder,
+                          uint64_t seed, uint32_t id0, int32_t* out_class, uint64_t* out_class_sum,
+                          uint32_t* out_sweeps, void* stream) {
     int rc = check_common(ctx, n, L, id0);
     if (rc) return rc;
     surfmcmc_opts o;
@@ -1314,6 +1314,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
     if (!net || cnn_code_size(net) != L) return fail(ctx, SURFMCMC_EINVAL, "network missing or built for another L");
     if (chunk_sweeps == 0) return fail(ctx, SURFMCMC_EINVAL, "chunk_sweeps must be > 0");
     if (tau != tau) return fail(ctx, SURFMCMC_EINVAL, "tau is NaN");
+    if (reorder != 0 && reorder != 1) return fail(ctx, SURFMCMC_EINVAL, "reorder must be 0 or 1");
     if (n > 0 && (!syndromes || !out_class)) return fail(ctx, SURFMCMC_EINVAL, "NULL syndromes or out_class");
     int lam = 0;
     if (pick_lanes(L, o.lanes_per_bundle, &lam, ctx, o.chains_per_class))
@@ -1359,6 +1360,8 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
     const size_t off_code = cv.reserve((size_t)n * 4);
     const size_t off_state = cv.reserve((size_t)nb_max * 2 * nq * 4);
     const size_t off_ctr = cv.reserve(sizeof(unsigned int));
+    const size_t off_rank = reorder ? cv.reserve((size_t)n) : 0;
+    const size_t off_frozen = reorder ? cv.reserve((size_t)n * 16) : 0;
     if ((rc = ensure_arena(ctx, cv.off))) return rc;
     Buf* all[] = {&b_syn, &b_cls, &b_csum, &b_sw};
     for (Buf* b : all) bind(*b, ctx);
@@ -1387,6 +1390,8 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
     long long n_act = n;
     uint32_t t = 0;
     int cur = 0;  // pair holding the active items' caller indices and ids
+    uint32_t t_reorder = 0;   // the checkpoint at which the budget was reordered (0: not yet)
+    const uint64_t spp_r = (uint64_t)samples_per_sweep(o, L) * R;   // samples of one class per sweep
     for (size_t k = 0; k < marks.size() && n_act > 0; ++k) {
         const uint32_t tk = marks[k];
         const bool final_chunk = k + 1 == marks.size();
@@ -1420,17 +1425,26 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
         if ((rc = run_segments(ctx, sp, segs, o.burn_in, p, lam_k, io, s))) return rc;
 
         // decision so far, then retire the items that may stop here
-        DecideParams dp;
-        memset(&dp, 0, sizeof dp);
-        dp.n = n_act;
-        dp.K = K;
-        dp.R = R;
-        dp.samples = tk > o.burn_in ? samples_per_sweep(o, L) * R * (tk - o.burn_in) : 0;
-        dp.beta_bar = beta_bar;
-        dp.chain_sum = s_out;
-        dp.out_class = tcls;
-        dp.out_class_sum = tsum;
-        CK(launch_decide(dp, s));
+        if (t_reorder) {
+            // reordered items: the top classes have their own chains (sampled
+            // since the burn-in) and further replicas (since t_reorder)
+            const uint64_t n_top = spp_r * ((uint64_t)(tk - o.burn_in) + (uint64_t)(tk - t_reorder));
+            const uint64_t n_low = spp_r * (uint64_t)(t_reorder - o.burn_in);
+            CK(launch_decide_reorder(n_act, (const long long*)at(off_perm[cur]), (const uint8_t*)at(off_rank),
+                                     (const uint64_t*)at(off_frozen), R, s_out, n_top, n_low, tcls, tsum, s));
+        } else {
+            DecideParams dp;
+            memset(&dp, 0, sizeof dp);
+            dp.n = n_act;
+            dp.K = K;
+            dp.R = R;
+            dp.samples = tk > o.burn_in ? samples_per_sweep(o, L) * R * (tk - o.burn_in) : 0;
+            dp.beta_bar = beta_bar;
+            dp.chain_sum = s_out;
+            dp.out_class = tcls;
+            dp.out_class_sum = tsum;
+            CK(launch_decide(dp, s));
+        }
         CK(launch_retire(n_act, (const long long*)at(off_perm[cur]), logprob, tcls, tsum, tau, tk,
                          final_chunk ? 1 : 0, (int32_t*)b_cls.dev, (uint64_t*)b_csum.dev, (uint32_t*)b_sw.dev, keep,
                          s));
@@ -1445,6 +1459,13 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
         CK(cudaStreamSynchronize(s));
         n_act = h_cnt;
         cur ^= 1;
+        if (reorder && !t_reorder) {
+            // the chains of the survivors' two least likely classes continue
+            // as replicas of the two most likely ones
+            CK(launch_reorder(n_act, (const long long*)at(off_perm[cur]), logprob, R, 2 * W, f_in, s_in,
+                              (uint8_t*)at(off_rank), (uint64_t*)at(off_frozen), s));
+            t_reorder = tk;
+        }
     }
     bool any_host = false;
     for (Buf* b : {&b_cls, &b_csum, &b_sw}) {

@@ -368,6 +368,90 @@ __global__ void compact_kernel(long long n, const int32_t* keep, const long long
     for (int c = threadIdx.x; c < chains; c += blockDim.x) sums_out[j * chains + c] = sums[i * chains + c];
 }
 
+// Budget reordering of an early-stopped decode (at its first checkpoint):
+// for active item i (caller's index perm[i]) the network's classes ranked by
+// log-probability, highest first, ties to the lower class: a, b, c, d.  The
+// chains of c and d continue as further replicas of a and b: slot c R + r
+// takes the frame of slot a R + r and slot d R + r that of b R + r, their
+// sums restart from 0, and the class sums of c and d so far are frozen.
+// rank[o] = a | b << 2 | c << 4 | d << 6, frozen[o] = (S_c, S_d).  One warp
+// per item.
+__global__ void reorder_kernel(long long n, const long long* perm, const float* logprob, int R, int chain_words,
+                               uint32_t* frames, uint64_t* sums, uint8_t* rank, uint64_t* frozen) {
+    const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const long long o = perm[i];
+    int ord[4] = {0, 1, 2, 3};
+    float lp[4];
+    for (int k = 0; k < 4; ++k) lp[k] = logprob[o * 4 + k];
+    for (int x = 1; x < 4; ++x)          // insertion sort, stable: ties keep the lower class first
+        for (int y = x; y > 0 && lp[ord[y]] > lp[ord[y - 1]]; --y) {
+            const int t = ord[y];
+            ord[y] = ord[y - 1];
+            ord[y - 1] = t;
+        }
+    const int C = 4 * R;
+    uint64_t* cs = sums + i * C;
+    uint32_t* fr = frames + i * (long long)C * chain_words;
+    if (lane == 0) {
+        uint64_t sc = 0, sd = 0;
+        for (int r = 0; r < R; ++r) {
+            sc += cs[ord[2] * R + r];
+            sd += cs[ord[3] * R + r];
+        }
+        frozen[o * 2 + 0] = sc;
+        frozen[o * 2 + 1] = sd;
+        rank[o] = (uint8_t)(ord[0] | ord[1] << 2 | ord[2] << 4 | ord[3] << 6);
+    }
+    __syncwarp();
+    for (int r = 0; r < R; ++r)
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t* src = fr + (long long)(ord[h] * R + r) * chain_words;
+            uint32_t* dst = fr + (long long)(ord[h + 2] * R + r) * chain_words;
+            for (int w = lane; w < chain_words; w += 32) dst[w] = src[w];
+        }
+    __syncwarp();
+    for (int j = lane; j < 2 * R; j += 32) cs[ord[2 + j / R] * R + j % R] = 0;
+}
+
+// a * b < c * d for 64-bit unsigned operands (128-bit products).
+__device__ __forceinline__ bool prod_less(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    const uint64_t h1 = __umul64hi(a, b), h2 = __umul64hi(c, d);
+    return h1 < h2 || (h1 == h2 && a * b < c * d);
+}
+
+// Decision of a reordered item: class sums S_a, S_b over the class's own and
+// its further replicas' chains (n_top samples each), S_c, S_d the frozen sums
+// (n_low samples each); the class with the smallest mean S_k / N_k wins,
+// compared exactly (S_k N_j < S_j N_k), lowest class on ties.
+__global__ void decide_reorder_kernel(long long n, const long long* perm, const uint8_t* rank, const uint64_t* frozen,
+                                      int R, const uint64_t* chain_sum, uint64_t n_top, uint64_t n_low,
+                                      int32_t* out_class, uint64_t* out_class_sum) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long o = perm[i];
+    const int rk = rank[o];
+    const int a = rk & 3, b = (rk >> 2) & 3, c = (rk >> 4) & 3, d = (rk >> 6) & 3;
+    const uint64_t* cs = chain_sum + i * 4 * R;
+    uint64_t S[4], N[4];
+    S[a] = 0;
+    S[b] = 0;
+    for (int r = 0; r < R; ++r) {
+        S[a] += cs[a * R + r] + cs[c * R + r];
+        S[b] += cs[b * R + r] + cs[d * R + r];
+    }
+    S[c] = frozen[o * 2 + 0];
+    S[d] = frozen[o * 2 + 1];
+    N[a] = N[b] = n_top;
+    N[c] = N[d] = n_low;
+    int best = 0;
+    for (int k = 1; k < 4; ++k)
+        if (prod_less(S[k], N[best], S[best], N[k])) best = k;
+    out_class[i] = best;
+    for (int k = 0; k < 4; ++k) out_class_sum[i * 4 + k] = S[k];
+}
+
 __global__ void iota_kernel(long long n, long long* perm) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) perm[i] = i;
@@ -459,6 +543,23 @@ cudaError_t launch_start_frames(const uint8_t* syn, long long n, int L, uint32_t
         start_frames_toric_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(syn, n, L, frames, code);
     else
         start_frames_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(syn, n, L, frames, code);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(long long n, const long long* perm, const float* logprob, int R, int chain_words,
+                           uint32_t* frames, uint64_t* sums, uint8_t* rank, uint64_t* frozen, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    reorder_kernel<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(n, perm, logprob, R, chain_words, frames, sums, rank,
+                                                           frozen);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decide_reorder(long long n, const long long* perm, const uint8_t* rank, const uint64_t* frozen,
+                                  int R, const uint64_t* chain_sum, uint64_t n_top, uint64_t n_low, int32_t* out_class,
+                                  uint64_t* out_class_sum, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    decide_reorder_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, perm, rank, frozen, R, chain_sum, n_top,
+                                                                      n_low, out_class, out_class_sum);
     return cudaGetLastError();
 }
 

@@ -242,6 +242,11 @@ cudaError_t launch_compact(long long n, const int32_t* keep, long long* pos, lon
                            uint32_t id0, int frame_words, int chains, const uint32_t* frames, const uint64_t* sums,
                            long long* perm_out, uint32_t* ids_out, uint32_t* frames_out, uint64_t* sums_out,
                            cudaStream_t s);
+cudaError_t launch_reorder(long long n, const long long* perm, const float* logprob, int R, int chain_words,
+                           uint32_t* frames, uint64_t* sums, uint8_t* rank, uint64_t* frozen, cudaStream_t s);
+cudaError_t launch_decide_reorder(long long n, const long long* perm, const uint8_t* rank, const uint64_t* frozen,
+                                  int R, const uint64_t* chain_sum, uint64_t n_top, uint64_t n_low, int32_t* out_class,
+                                  uint64_t* out_class_sum, cudaStream_t s);
 cudaError_t launch_iota(long long n, long long* perm, cudaStream_t s);
 
 // Context services shared with the network code (api.cu).

@@ -18,7 +18,10 @@ buffers and keeps counts):
    sigma of the long-chain rate is kept.
 4. Test at p: the long-chain decoder and the early-stop decoder on a fresh
    test set (one call each), both timed on the device; error rates against
-   the true classes.
+   the true classes.  With --reorder, also the early stop with budget
+   reordering (the chains of the network's two least likely classes become
+   replicas of its two most likely ones at the first checkpoint) at the same
+   tau.
 """
 from __future__ import annotations
 
@@ -166,9 +169,11 @@ def timed(fn, reps=1):
     return r, a.elapsed_time(b) / reps / 1000.0
 
 
-def evaluate_p(ctx, fwd_net, L, p, long_opts, chunk, n_val, n_test, seed, log=None):
+def evaluate_p(ctx, fwd_net, L, p, long_opts, chunk, n_val, n_test, seed, log=None, reorder=False):
     """Calibrate tau on a validation set at error rate p, then time the
-    long-chain and early-stop decoders on a test set at p (one call each)."""
+    long-chain and early-stop decoders on a test set at p (one call each);
+    with reorder, also the early stop with budget reordering at the same
+    tau."""
     import torch
     va = make_set(ctx, L, n_val, seed + 1, p, p, 1)
     lp_va = fwd_net.forward(va["syn"]).cpu().numpy()
@@ -186,6 +191,16 @@ def evaluate_p(ctx, fwd_net, L, p, long_opts, chunk, n_val, n_test, seed, log=No
     run_early()
     _, t_long = timed(run_long)
     (cls_early, _, sw), t_early = timed(run_early)
+    extra = {}
+    if reorder:
+        run_re = lambda: ctx.decode_early(fwd_net, te["syn"], L, p, long_opts, chunk_sweeps=chunk, tau=tau,
+                                          seed=seed + 102, reorder=True)
+        run_re()
+        (cls_re, _, sw_re), t_re = timed(run_re)
+        cls_re = cls_re.cpu().numpy()
+        sw_re = sw_re.view(torch.int32).cpu().numpy()
+        extra = {"ler_reorder": float((cls_re != true).mean()), "mean_sweeps_reorder": float(sw_re.mean()),
+                 "syn_per_s_reorder": n_test / t_re, "gain_reorder": t_long / t_re}
     cls_long = out_long.cpu().numpy()
     cls_early = cls_early.cpu().numpy()
     sw = sw.view(torch.int32).cpu().numpy()
@@ -196,10 +211,11 @@ def evaluate_p(ctx, fwd_net, L, p, long_opts, chunk, n_val, n_test, seed, log=No
            "within_1sigma": ler_early <= ler_long + sigma, "mean_sweeps_early": float(sw.mean()),
            "stopped_at_first_checkpoint": float((sw == marks[0]).mean()),
            "syn_per_s_long": n_test / t_long, "syn_per_s_early": n_test / t_early, "gain": t_long / t_early,
-           "val_ler_long": ler_long_va, "calibration": rows}
+           "val_ler_long": ler_long_va, "calibration": rows, **extra}
     if log:
         log(f"p={p:.3f}: tau {tau} LER long {ler_long:.5f} early {ler_early:.5f} (sigma {sigma:.5f}) "
-            f"sweeps {row['mean_sweeps_early']:.1f}/{long_opts.n_sweeps} gain {row['gain']:.2f}")
+            f"sweeps {row['mean_sweeps_early']:.1f}/{long_opts.n_sweeps} gain {row['gain']:.2f}"
+            + (f" | reorder LER {extra['ler_reorder']:.5f} gain {extra['gain_reorder']:.2f}" if extra else ""))
     return row
 
 
@@ -224,11 +240,14 @@ def run(args, log=print):
     fwd_net = P.Network(ctx, L, max_batch=8192)
     fwd_net.set_params(net.get_params())
     net.close()
-    rows = [evaluate_p(ctx, fwd_net, L, p, long_opts, args.chunk, args.val, args.test, args.seed + 10 * i, log=log)
+    rows = [evaluate_p(ctx, fwd_net, L, p, long_opts, args.chunk, args.val, args.test, args.seed + 10 * i, log=log,
+                       reorder=args.reorder)
             for i, p in enumerate(args.eval_ps)]
     te = make_set(ctx, L, args.test, args.seed + 7, args.p_lo, args.p_hi, args.n_p)
     _, t_fwd = timed(lambda: fwd_net.forward(te["syn"]), reps=3)
-    flops = 2.0 * L * L * sum(ci * 9 * co for ci, co in zip([2, 64, 64, 64, 64], [64, 64, 64, 64, 2]))
+    # tensor-core work of the forward: conv1..conv4 on the L x L maps (the
+    # last layer runs on the CUDA cores at the middle-line outputs only)
+    flops = 2.0 * L * L * sum(ci * 9 * co for ci, co in zip([2, 64, 64, 64], [64, 64, 64, 64]))
     res = {
         "metric": "early-stop decoding throughput at matched logical error rate",
         "L": L, "train_p_range": [args.p_lo, args.p_hi], "strata": args.n_p,
@@ -278,6 +297,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=4001)
     ap.add_argument("--eval-ps", default="0.08,0.10,0.12,0.14,0.16")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--reorder", action="store_true",
+                    help="also decode each test set with budget reordering at the calibrated tau")
     args = ap.parse_args(argv)
     args.eval_ps = [float(x) for x in args.eval_ps.split(",")]
     res = run(args, log=lambda m: print(m, flush=True))

@@ -146,3 +146,86 @@ def test_trained_network_gain(pkg, ctx):
     assert row["ler_early"] <= row["ler_long"] + 2 * row["sigma"], row
     assert row["mean_sweeps_early"] < 0.75 * ns.sweeps, row
     assert row["gain"] > 1.2, row
+
+
+def _reorder_reference(L, p, R, o, chunk, tau, seed, id0, syn, lp):
+    """Early stop with budget reordering, composed from the oracle's chain
+    runs: the stop rule at every checkpoint; at the first checkpoint a
+    survivor's chains of its two least likely classes (network ranking,
+    ties to the lower class) take the states of the two most likely classes'
+    chains and restart their sums, the classes' sums so far being frozen;
+    later decisions compare class means exactly."""
+    burn, T = o.burn_in, o.n_sweeps
+    marks = list(range(burn + chunk, T, chunk)) + [T]
+    kw = dict(burn_in=burn, anneal_stages=o.anneal_stages, anneal_beta0=o.anneal_beta0)
+    spp = 4
+    res = []
+    for i in range(len(syn)):
+        am = int(np.argmax(lp[i]))
+        margin = lp[i][am] - max(lp[i][k] for k in range(4) if k != am)
+        rank = sorted(range(4), key=lambda k: (-float(lp[i][k]), k))
+        a, b, c, d = rank
+        out = O.run_chains(L, 4, R, p, seed, id0 + i, syn[i], 0, marks[0], **kw)
+        fx, fz, cs = out["frames_x"].copy(), out["frames_z"].copy(), out["chain_sum"].copy()
+        frozen = None
+        for k, tk in enumerate(marks):
+            if k > 0:
+                out = O.run_chains(L, 4, R, p, seed, id0 + i, syn[i], marks[k - 1], tk, frames=(fx, fz),
+                                   chain_sum=cs, **kw)
+                fx, fz, cs = out["frames_x"].copy(), out["frames_z"].copy(), out["chain_sum"].copy()
+            S = [int(cs[q * R:(q + 1) * R].sum()) for q in range(4)]
+            if frozen is None:
+                N = [1, 1, 1, 1]
+            else:
+                S[a] += S[c]
+                S[b] += S[d]
+                S[c], S[d] = frozen
+                n_top = spp * R * ((tk - burn) + (tk - marks[0]))
+                n_low = spp * R * (marks[0] - burn)
+                N = [0, 0, 0, 0]
+                N[a] = N[b] = n_top
+                N[c] = N[d] = n_low
+            best = 0
+            for q in range(1, 4):
+                if S[q] * N[best] < S[best] * N[q]:
+                    best = q
+            final = k + 1 == len(marks)
+            if final or (margin > np.float32(tau) and am == best):
+                res.append((best, S, tk))
+                break
+            if frozen is None:
+                frozen = (S[c], S[d])
+                for r in range(R):
+                    for src, dst in ((a, c), (b, d)):
+                        fx[dst * R + r] = fx[src * R + r]
+                        fz[dst * R + r] = fz[src * R + r]
+                        cs[dst * R + r] = 0
+    return res
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_budget_reordering_bit_exact(pkg, ctx, device):
+    L, n, p, chunk, R = 5, 400, 0.13, 40, 4
+    syn, _ = O.gen_syndromes(6010, 0, n, L, p)
+    net = _net(pkg, ctx, L, 5)
+    o = _opts(pkg, sweeps=240, burn=40, R=R)
+    lp = net.forward(syn).astype(np.float32)
+    am = lp.argmax(1)
+    masked = lp.copy()
+    masked[np.arange(n), am] = -np.inf
+    tau = float(np.quantile(lp[np.arange(n), am] - masked.max(1), 0.25))
+    x = torch.from_numpy(syn).cuda() if device else syn
+    cls, csum, sw = ctx.decode_early(net, x, L, p, o, chunk_sweeps=chunk, tau=tau, seed=81, id0=3, reorder=True)
+    if device:
+        cls, csum, sw = cls.cpu().numpy(), csum.cpu().numpy(), sw.cpu().numpy()
+    ref = _reorder_reference(L, p, R, o, chunk, tau, 81, 3, syn, lp)
+    first = o.burn_in + chunk
+    for i, (c, S, tk) in enumerate(ref):
+        assert cls[i] == c and [int(v) for v in csum[i]] == S and sw[i] == tk, i
+    # items stop at the first checkpoint, later after reordering, and at the end
+    assert (sw == first).sum() > 10 and ((sw > first) & (sw < o.n_sweeps)).sum() > 5
+    assert (sw == o.n_sweeps).sum() > 10
+    # without reordering the same call is the plain early stop
+    c0, s0, w0 = ctx.decode_early(net, syn, L, p, o, chunk_sweeps=chunk, tau=tau, seed=81, id0=3)
+    assert (w0[sw == first] == first).all() and (c0[sw == first] == cls[sw == first]).all()
+    net.close()
