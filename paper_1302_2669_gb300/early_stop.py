@@ -241,7 +241,7 @@ def run(args, log=print):
     fwd_net.set_params(net.get_params())
     net.close()
     rows = [evaluate_p(ctx, fwd_net, L, p, long_opts, args.chunk, args.val, args.test, args.seed + 10 * i, log=log,
-                       reorder=args.reorder)
+                       reorder=getattr(args, "reorder", False))
             for i, p in enumerate(args.eval_ps)]
     te = make_set(ctx, L, args.test, args.seed + 7, args.p_lo, args.p_hi, args.n_p)
     _, t_fwd = timed(lambda: fwd_net.forward(te["syn"]), reps=3)
