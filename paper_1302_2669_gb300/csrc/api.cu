@@ -259,7 +259,7 @@ int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nul
 int widen_lanes(const surfmcmc_ctx* ctx, int L, int requested, int lam, long long n_bundles, int G, int code = 0) {
     if (requested || !ctx || ctx->sms <= 0) return lam;
     const int nq = geo_nq(code, L), nc = geo_nc(code, L);
-    const long long capacity = (long long)ctx->sms * (G >= 16 ? 5 : 3);
+    const long long capacity = (long long)ctx->sms * sweep_blocks_per_sm(G);
     while (lam < 32 && sweep_units(n_bundles, lam) < capacity &&
            sweep_smem_bytes(nq, nc, 2 * lam) <= 200 * 1024)
         lam *= 2;
@@ -1033,6 +1033,9 @@ int surfmcmc_decode_ti(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     sp.scan = o.scan;
     sp.noise = o.noise;
     energy_table(o, sp.energy);
+    // a batch too small to fill the device gets more lanes per bundle (the
+    // results do not depend on the lane split)
+    lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G, toric);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
     const std::vector<Segment> segs0 = plan_segments(o, o.beta_scale, 0);
     const int W = geo_words(toric, L), nq = geo_nq(toric, L);

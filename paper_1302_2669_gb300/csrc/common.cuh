@@ -142,6 +142,10 @@ __host__ __device__ __forceinline__ int geo_nc(int code, int L) { return code ? 
 // of opposite parity: same-colour generators in a row are two qubits apart.
 __host__ __device__ __forceinline__ int bundle_stride(int nq) { return 2 * (nq + 2) + 1; }
 
+// Blocks per SM the sweep kernel is compiled for (its register bound): 6
+// with plane widths of 16 or 32 chains, 3 with narrower planes.
+__host__ __device__ constexpr int sweep_blocks_per_sm(int G) { return G >= 16 ? 6 : 3; }
+
 // ---------------------------------------------------------------------------
 // Sweep kernel parameters.  One launch runs the chains of up to kMaxGroups
 // groups of syndromes; a group has one code size and one sweep range.  Items

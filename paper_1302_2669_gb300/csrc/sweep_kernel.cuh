@@ -729,7 +729,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
 // the host arranged (largest work first), and rebuilds the support table in
 // shared memory when the group's code size changes.
 template <int G, int LAM, bool SCAN, bool IND, bool ACPT>
-__global__ void __launch_bounds__(128, (G >= 16 ? 6 : 3)) sweep_kernel(const __grid_constant__ SweepParams p) {
+__global__ void __launch_bounds__(128, sweep_blocks_per_sm(G)) sweep_kernel(const __grid_constant__ SweepParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ long long s_unit;
     ushort4* tab = reinterpret_cast<ushort4*>(smem);
