@@ -542,13 +542,15 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
         int n = 0;
         for (int q = 0; q < nq; ++q) n += energy((X[q] >> b) & 1u, (Z[q] >> b) & 1u);
         uint64_t sum = 0, n_acc = 0;
+        const int n_x = p.code ? L * L : L * (L - 1);   // sigma_x generators come first
         for (uint32_t t = gd.t_begin; t < gd.t_end; ++t) {
             const bool sample = t >= gd.burn_in;
             for (int step = 0; step < ns; ++step) {
                 const uint4 r = philox10(make_uint4(my_sid, chain, t, (uint32_t)step), p.rk);
                 const int g = (int)__umulhi(r.x, (uint32_t)ns);
-                int q[4];
-                const int type = p.code ? toric_generator_support(L, g, q) : generator_support(L, g, q);
+                const ushort4 sp = tab[g];
+                const int q[4] = {sp.x, sp.y, sp.z, sp.w};
+                const int type = g >= n_x;
                 uint32_t* own = type == 0 ? X : Z;
                 const uint32_t* oth = type == 0 ? Z : X;
                 int dn = 0;
@@ -745,11 +747,18 @@ __global__ void __launch_bounds__(128, sweep_blocks_per_sm(G)) sweep_kernel(cons
         while (g + 1 < p.n_groups && u >= p.grp[g + 1].unit_base) ++g;
         const GroupDesc& gd = p.grp[g];
         if (g != cur) {
+            // support table: colour-major for sweeps, syndrome order for
+            // random scan (4 nc = n_stab entries either way)
             for (int idx = threadIdx.x; idx < 4 * gd.nc; idx += blockDim.x) {
-                const int col = idx / gd.nc, m = idx - col * gd.nc;
                 int q[4];
-                if (p.code) toric_colour_support(gd.L, col, m, q);
-                else colour_support(gd.L, col, m, q);
+                if constexpr (SCAN) {
+                    if (p.code) toric_generator_support(gd.L, idx, q);
+                    else generator_support(gd.L, idx, q);
+                } else {
+                    const int col = idx / gd.nc, m = idx - col * gd.nc;
+                    if (p.code) toric_colour_support(gd.L, col, m, q);
+                    else colour_support(gd.L, col, m, q);
+                }
                 tab[idx] = make_ushort4((unsigned short)q[0], (unsigned short)q[1], (unsigned short)q[2],
                                         (unsigned short)q[3]);
             }
