@@ -27,15 +27,19 @@
 //     128 rows starting at row P + 1 + shift(t) of that halo tile, so each
 //     input row crosses from L2 once per tile instead of once per tap.  The
 //     weight operand stays in shared memory for the whole persistent block;
-//     one thread issues the MMAs, four warps drain the two tensor-memory
-//     accumulators (bias + ReLU, logits, or the ReLU gate of the layer
-//     below).  The first layer (2 input channels, K = 18 padded to
-//     32) gathers its operand with producer warps;
+//     two threads issue the MMAs (alternate tiles), four warps drain the
+//     four tensor-memory accumulators (bias + ReLU, or the ReLU gate of the
+//     layer below) and store each tile with a TMA copy.  The first layer
+//     (2 input channels, K = 18 padded to 32) gathers its operand with
+//     producer warps;
 //   weight gradient of the 64-channel layers: D[(tap, ci)][co] =
-//     sum_p X[p + tap][ci] dZ[p][co], a GEMM over positions split across
-//     blocks, with a row of ones that yields the bias gradient; partial sums
-//     are added in a fixed order.  The first layer's (2 input channels, 19
-//     rows) runs on the CUDA cores.
+//     sum_p X[p + tap][ci] dZ[p][co], a GEMM over positions whose operands
+//     are read MN-major by TMA straight from the [position][channel]
+//     tensors (tap windows are row offsets of a halo tile, two taps make
+//     M = 128, a constant ones tile gives the bias row); one block per SM
+//     over a contiguous range of positions, partial sums added in a fixed
+//     order.  The first layer's (2 input channels, 19 rows) runs on the
+//     CUDA cores.
 // The last layer (2 outputs, read and differentiated on the middle lines
 // only: forward fused into the readout, backward), the readout, loss and
 // Adam steps run on the CUDA cores.
@@ -68,7 +72,7 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWaitTimeout = 1;   // error codes written to the device flag
 constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
 constexpr int kTmaStages = 4;     // halo tiles in flight in the TMA conv kernel
-constexpr int kTmaThreads = 6 * 32;  // TMA warp, MMA warp, 4 accumulator warps
+constexpr int kTmaThreads = 7 * 32;  // TMA warp, MMA warps 1 and 6, 4 accumulator warps
 
 // Channels of the five layers and the offsets of their weights and biases in
 // the flat parameter vector.
@@ -498,9 +502,11 @@ constexpr size_t conv_tma_smem_bytes() {
 }
 
 // Warp 0 (one thread) loads the halo tile of each position tile by TMA into
-// a ring of stages; warp 1 (one thread) issues 4 MMAs per tap (K = 16 each),
-// 36 per tile, into one of four accumulators; warps 2-5 drain the
-// accumulators.  A tap's operand starts at a 128-byte row inside the
+// a ring of stages; warps 1 and 6 (one thread each) issue 4 MMAs per tap
+// (K = 16 each), 36 per tile, into one of four accumulators, taking the
+// block's tiles alternately (one thread cannot issue 128 x 64 x 16 MMAs as
+// fast as the tensor pipe runs them; every accumulator still gets its MMAs
+// from one thread in order); warps 2-5 drain the accumulators.  A tap's operand starts at a 128-byte row inside the
 // 1024-byte-aligned halo tile: the 128-byte swizzle is a function of the
 // shared-memory address bits, so the descriptor keeps a zero base offset.
 // The bf16 epilogues write their tile into one of two output buffers in the
@@ -517,9 +523,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
     uint8_t* sA = smem;                      // S halo tiles, 1024-byte aligned
     uint8_t* sB = smem + S * kTmaStage;
     uint8_t* sOut = sB + NP * 576 * 2;       // 2 output tiles (bf16 epilogues), 1024-byte aligned
-    __shared__ __align__(8) uint64_t full[S], empty[S], accf[NACC], acce[NACC], maskf[2], fin;
+    __shared__ __align__(8) uint64_t full[S], empty[S], accf[NACC], acce[NACC], maskf[2], fin[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    static_assert(NACC % 2 == 0 && S % 2 == 0, "alternating issuers need even rings");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
@@ -542,7 +549,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
         }
         mbar_init(&maskf[0], 1);
         mbar_init(&maskf[1], 1);
-        mbar_init(&fin, 1);
+        mbar_init(&fin[0], 1);
+        mbar_init(&fin[1], 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -567,9 +575,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             // are unconsumed only after an abort)
             for (uint32_t k = q > (uint32_t)S ? q - S : 0; k < q; ++k) mbar_drain(&full[k % S], (k / S) & 1, a.err);
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 || warp == 6) {
         if (lane == 0) {
-            uint32_t it = 0;
+            const uint32_t who = warp == 1 ? 0u : 1u;   // tiles it = who, who + 2, ...
+            uint32_t it = who;
             // descriptors as 32-bit halves: the high halves are fixed, the
             // low halves are the start address / 16 plus the operand's offset
             const uint64_t a_desc = smem_desc_sw128(smem_u32(sA) + P1 * 128);
@@ -579,7 +588,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             uint32_t tap_lo[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) tap_lo[c] = (uint32_t)(tap_shift(c, L) * 8);   // 128 B rows / 16
-            for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            for (long long tile = blockIdx.x + (long long)who * gridDim.x; tile < n_tiles;
+                 tile += 2LL * gridDim.x, it += 2) {
                 const uint32_t b = it % NACC, u = it / NACC;
                 const uint32_t stage = it % S, use = it / S;
                 if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
@@ -598,8 +608,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
                 mma_commit(&empty[stage]);
                 mma_commit(&accf[b]);
             }
-            mma_commit(&fin);
-            mbar_drain(&fin, 0, a.err);
+            mma_commit(&fin[who]);
+            mbar_drain(&fin[who], 0, a.err);
         }
     } else {
         const int quarter = warp & 3;
