@@ -65,9 +65,9 @@ typedef __nv_bfloat16 bf16;
 constexpr int kHid = 64;          // hidden channels
 constexpr int kOut = 2;           // flip logits per position (last layer)
 constexpr float kClip = 1e-6f;    // |M| <= 1 - kClip
-constexpr int kConvProd = 8;      // gather warps of the first layer's conv kernel
 constexpr int kEpiWarps = 4;      // accumulator-draining warps
-constexpr int kConvThreads = (kConvProd + kEpiWarps + 1) * 32;
+constexpr int kOutTile = 128 * 128;   // one 128 x 64 bf16 output tile
+constexpr int kConvAcc = 4;       // tensor-memory accumulators of the conv kernels
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWaitTimeout = 1;   // error codes written to the device flag
 constexpr int kMaxSplits = 64;    // position slices of the weight-gradient GEMM
@@ -255,14 +255,14 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Barrier 1 over the 128 accumulator-draining threads; the second form
-// returns whether the predicate held in all of them.
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-__device__ __forceinline__ bool epi_all(bool v) {
+// Named barrier id (1 by default) over 128 accumulator-draining threads;
+// the second form returns whether the predicate held in all of them.
+__device__ __forceinline__ void epi_sync(uint32_t id = 1) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ bool epi_all(bool v, uint32_t id = 1) {
     uint32_t r;
-    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
                  : "=r"(r)
-                 : "r"((uint32_t)v)
+                 : "r"((uint32_t)v), "r"(id)
                  : "memory");
     return r != 0;
 }
@@ -283,6 +283,20 @@ __device__ __forceinline__ bool interior_rem(int rem, int L) {
 
 // Position shift of tap t = 3 kh + kw: (kh - 1) P + (kw - 1).
 __device__ __forceinline__ int tap_shift(int t, int L) { return (t / 3 - 1) * (L + 2) + (t % 3 - 1); }
+
+// 64 consecutive f32 columns of this warp's 32 tensor-memory lanes, one
+// load and one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 // 16 consecutive f32 columns of this warp's 32 tensor-memory lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
@@ -309,51 +323,78 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 // ---------------------------------------------------------------------------
 // Implicit-GEMM 3x3 conv of the first layer on tcgen05.
 // ---------------------------------------------------------------------------
-struct ConvArgs {
-    const bf16* act;     // [M][2] input maps (padded)
-    const bf16* wmat;    // [64][32] operand B (k = tap * 2 + ci, zero from k = 18)
-    const float* bias;   // [64]
-    bf16* out_bf16;      // [M][64]
-    long long M;         // positions n P^2
+struct Conv1Args {
+    CUtensorMap in_map;   // input [M][2] bf16 viewed as [ceil(M/4)][8], box 8 x c1_strip_rows(L), no swizzle
+    CUtensorMap out_map;  // output [M_alloc][64] bf16, box 64 x 128, 128-byte swizzle
+    const bf16* wmat;     // [64][32] operand B (k = tap * 2 + ci, zero from k = 18)
+    const float* bias;    // [64]
+    long long M;          // positions n P^2
     int L;
     int* err;
 };
 
-constexpr int kC1KP = 32;                      // K of the first layer: 9 taps x 2 channels, padded
-constexpr int kC1Stage = 128 * kC1KP * 2;      // one tile's operand
-constexpr int kC1S = 4;                        // pipeline depth
-constexpr size_t kC1Smem = (size_t)64 * kC1KP * 2 + kC1S * kC1Stage + 1024;
+constexpr int kC1KP = 32;                       // K of the first layer: 9 taps x 2 channels, padded
+constexpr int kC1Stage = 128 * kC1KP * 2;       // one tile's A operand
+constexpr int kC1S = 4;                         // pipeline depth
+constexpr int kC1StripStage = 1024;             // one tile's input strip
+constexpr int kC1Threads = 14 * 32;             // TMA warp, MMA warp, 2 x 4 accumulator warps, 4 operand warps
 
-// First layer (2 input channels): producer warps gather the 18 values of a
-// position's 3x3 neighbourhood (one 32-bit pair per tap) into the operand.
-__global__ void __launch_bounds__(kConvThreads, 1) conv1_kernel(ConvArgs a) {
-    constexpr int S = kC1S, KGS = kC1KP / 8, NP = 64;
-    constexpr uint32_t NCOLS = 2 * NP;
+// 16-byte rows (4 positions) of the input strip of a 128-position tile: the
+// taps reach P + 1 = L + 3 positions either way and the strip starts up to 3
+// positions before the first one it needs (row-aligned).
+__host__ __device__ constexpr int c1_strip_rows(int L) { return (128 + 2 * (L + 3) + 3 + 3) / 4; }
+static_assert(c1_strip_rows(SURFMCMC_MAX_L) * 16 <= kC1StripStage, "input strip");
+constexpr size_t kC1Smem = 4 * (size_t)kOutTile + kC1S * kC1Stage + 64 * kC1KP * 2 + kC1S * kC1StripStage + 1024;
+
+// floor(v / 4) for any sign
+__device__ __forceinline__ long long floor_div4(long long v) { return v >= 0 ? v / 4 : -((-v + 3) / 4); }
+
+// First layer (2 input channels, K = 18 padded to 32).  Warp 0 (one thread)
+// loads by TMA the strip of input positions a tile's taps read (4 B per
+// position); warps 10-13 build the tile's operand rows from it in shared
+// memory (row r, group g = taps 4g .. 4g+3; group 3 stays zero); warp 1 (one
+// thread) issues the two K = 16 MMAs into one of four accumulators; two
+// groups of four warps (2-5 and 6-9) drain alternate tiles (bias + ReLU, zero
+// border) into 128-byte-swizzled staging buffers that one thread of the
+// group stores with a TMA copy.  With K this small the MMAs are short and
+// the drain is the longest step of a tile, so two tiles drain at once.
+__global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_constant__ Conv1Args a) {
+    constexpr int S = kC1S, KGS = kC1KP / 8, NP = 64, NACC = kConvAcc;
+    constexpr uint32_t NCOLS = NACC * NP;
     constexpr uint32_t IDESC = idesc_bf16(128, NP);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sB = smem;
-    uint8_t* sA = smem + NP * kC1KP * 2;
-    __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], fin;
+    uint8_t* sOut = smem;                         // 2 output tiles per drain group, 1024-byte aligned
+    uint8_t* sA = sOut + 4 * kOutTile;            // S operand tiles
+    uint8_t* sB = sA + S * kC1Stage;              // weights
+    uint8_t* sStrip = sB + NP * kC1KP * 2;        // S input strips, 1024-byte aligned
+    __shared__ __align__(8) uint64_t full[S], sfree[S], afull[S], aempty[S], accf[NACC], acce[NACC], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    __shared__ __align__(16) float sBias[NP];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
-    const int L = a.L;
+    const int L = a.L, P1 = L + 3;
     const long long n_tiles = (M + 127) / 128;
 
-    for (int idx = tid; idx < NP * KGS; idx += kConvThreads) {
+    for (int idx = tid; idx < NP * KGS; idx += kC1Threads) {
         const int r = idx / KGS, g = idx - r * KGS;
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.wmat + (size_t)r * kC1KP) + g);
         *reinterpret_cast<uint4*>(sB + core_off(r, g, KGS)) = v;
     }
+    if (tid < NP) sBias[tid] = __ldg(a.bias + tid);
+    // operand group 3 (k = 24 .. 31) is never written again
+    for (int idx = tid; idx < S * kC1Stage / 16; idx += kC1Threads)
+        reinterpret_cast<uint4*>(sA)[idx] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], kConvProd * 32);
-            mbar_init(&empty[s], 1);
+            mbar_init(&full[s], 1);
+            mbar_init(&sfree[s], 128);
+            mbar_init(&afull[s], 128);
+            mbar_init(&aempty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&accf[b], 1);
             mbar_init(&acce[b], kEpiWarps * 32);
         }
@@ -362,109 +403,125 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv1_kernel(ConvArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_async_smem();
-    if (warp == kConvProd + kEpiWarps) tmem_alloc(&tmem_slot, NCOLS);
+    if (warp == 1) tmem_alloc(&tmem_slot, NCOLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp < kConvProd) {
-        // warp w covers rows 32 (w mod 4) .. +31; a thread loads group g =
-        // taps 4g .. 4g+3 of rows 2 half, 2 half + 1 of its 8-row blocks
-        const int rowblock = warp & 3, half = warp >> 2, g = lane >> 3;
-        uint32_t q = 0;
-        bool ok = true;
-        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++q) {
-            const uint32_t stage = q % S, use = q / S;
-            uint4 v[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const long long m = tile * 128 + rowblock * 32 + (lane & 7) + 8 * (2 * half + k);
-                uint32_t w[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int t = 4 * g + j;
-                    const long long src = m + tap_shift(t, L);
-                    w[j] = (t < 9 && m < M && src >= 0 && src < M)
-                               ? __ldg(reinterpret_cast<const uint32_t*>(a.act) + src) : 0u;
-                }
-                v[k] = make_uint4(w[0], w[1], w[2], w[3]);
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)c1_strip_rows(L) * 16;
+            uint32_t q = 0;
+            for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++q) {
+                const uint32_t stage = q % S, use = q / S;
+                if (use > 0 && !mbar_wait(&sfree[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                mbar_expect_tx(&full[stage], bytes);
+                tma_load_2d(sStrip + stage * kC1StripStage, &a.in_map, 0, (int)floor_div4(tile * 128 - P1),
+                            &full[stage]);
             }
-            if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) {
-                ok = false;
-                break;
-            }
-            uint8_t* st = sA + stage * kC1Stage;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int r = rowblock * 32 + (lane & 7) + 8 * (2 * half + k);
-                *reinterpret_cast<uint4*>(st + core_off(r, g, KGS)) = v[k];
-            }
-            fence_async_smem();
-            mbar_arrive(&full[stage]);
+            for (uint32_t k = q > (uint32_t)S ? q - S : 0; k < q; ++k) mbar_drain(&full[k % S], (k / S) & 1, a.err);
         }
-    } else if (warp < kConvProd + kEpiWarps) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+                const uint32_t b = it % NACC, u = it / NACC;
+                const uint32_t stage = it % S, use = it / S;
+                if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
+                if (!mbar_wait(&afull[stage], use & 1, &abort_flag, a.err)) break;
+                tc_fence_after();
+#pragma unroll
+                for (int ks = 0; ks < kC1KP / 16; ++ks) {
+                    const uint64_t ad = smem_desc(a0 + stage * kC1Stage + ks * 256, 128, KGS * 128);
+                    const uint64_t bd = smem_desc(b0 + ks * 256, 128, KGS * 128);
+                    mma_bf16(tmem + b * NP, ad, bd, IDESC, ks > 0 ? 1u : 0u);
+                }
+                mma_commit(&aempty[stage]);
+                mma_commit(&accf[b]);
+            }
+            mma_commit(&fin);
+            mbar_drain(&fin, 0, a.err);
+        }
+    } else if (warp >= 10) {
+        // operand rows: thread r builds row r of every tile
+        const int r = 32 * (warp - 10) + lane;
+        int sh[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) sh[t] = tap_shift(t, L);
+        uint32_t q = 0;
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++q) {
+            const uint32_t stage = q % S, use = q / S;
+            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) break;
+            const long long s0 = tile * 128 - P1;
+            const int base = r + P1 + (int)(s0 - 4 * floor_div4(s0));   // strip index of position tile*128 + r
+            const uint32_t* strip = reinterpret_cast<const uint32_t*>(sStrip + stage * kC1StripStage);
+            uint32_t w[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) w[t] = strip[base + sh[t]];
+            mbar_arrive(&sfree[stage]);
+            if (use > 0 && !mbar_wait(&aempty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+            uint8_t* st = sA + stage * kC1Stage;
+            *reinterpret_cast<uint4*>(st + core_off(r, 0, KGS)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(st + core_off(r, 1, KGS)) = make_uint4(w[4], w[5], w[6], w[7]);
+            *reinterpret_cast<uint4*>(st + core_off(r, 2, KGS)) = make_uint4(w[8], 0u, 0u, 0u);
+            fence_async_smem();
+            mbar_arrive(&afull[stage]);
+        }
+    } else {
+        // drain group grp takes tiles it = grp, grp + 2, ... (accumulators
+        // grp, grp + 2), its own named barrier and staging buffers
+        const uint32_t grp = warp < 6 ? 0u : 1u, bar_id = 1 + grp;
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
-        uint32_t it = 0;
-        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-            const uint32_t b = it & 1, u = it >> 1;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[b], u & 1, &abort_flag, a.err));
-            if (!ok) break;
+        const bool elected = (warp == 2 || warp == 6) && lane == 0;
+        const int PP = (L + 2) * (L + 2);
+        uint32_t it = grp, k = 0;
+        for (long long tile = blockIdx.x + (long long)grp * gridDim.x; tile < n_tiles;
+             tile += 2LL * gridDim.x, it += 2, ++k) {
+            const uint32_t b = it % NACC, u = it / NACC;
+            uint8_t* out = sOut + (2 * grp + (k & 1)) * kOutTile;
+            if (elected) bulk_wait_read<1>();   // the group's store of two tiles back has left this buffer
+            const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err);
+            if (!epi_all(ok, bar_id)) break;
             tc_fence_after();
             const long long m = tile * 128 + row;
-            const bool keep = m < M && interior(m, L);
+            const int rem = (int)((tile * 128) % PP + row) % PP;
+            const bool keep = m < M && interior_rem(rem, L);
             const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
-#pragma unroll
-            for (int cc = 0; cc < NP / 16; ++cc) {
-                float v[16];
-                tmem_ld16(taddr + cc * 16, v);
-                if (m < M) {
-                    uint32_t w[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float x0 = keep ? fmaxf(v[2 * j] + __ldg(a.bias + cc * 16 + 2 * j), 0.0f) : 0.0f;
-                        const float x1 = keep ? fmaxf(v[2 * j + 1] + __ldg(a.bias + cc * 16 + 2 * j + 1), 0.0f) : 0.0f;
-                        w[j] = pack_bf16(x0, x1);
-                    }
-                    uint4* op = reinterpret_cast<uint4*>(a.out_bf16 + m * 64 + cc * 16);
-                    op[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                    op[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                }
-            }
+            float v[NP];
+            tmem_ld64(taddr, v);
             tc_fence_before();
             mbar_arrive(&acce[b]);
-        }
-    } else if (lane == 0) {
-        uint32_t it = 0;
-        bool ok = true;
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
-            const uint32_t b = it & 1, u = it >> 1;
-            if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
-            tc_fence_after();
-            const uint32_t stage = it % S, use = it / S;
-            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
+            uint8_t* orow = out + row * 128;
+            const int sw = row & 7;
 #pragma unroll
-            for (int ks = 0; ks < kC1KP / 16; ++ks) {
-                const uint64_t ad = smem_desc(a0 + stage * kC1Stage + ks * 256, 128, KGS * 128);
-                const uint64_t bd = smem_desc(b0 + ks * 256, 128, KGS * 128);
-                mma_bf16(tmem + b * NP, ad, bd, IDESC, ks > 0 ? 1u : 0u);
+            for (int j = 0; j < NP / 8; ++j) {
+                const float4 b0 = *reinterpret_cast<const float4*>(sBias + 8 * j);
+                const float4 b1 = *reinterpret_cast<const float4*>(sBias + 8 * j + 4);
+                const float bj[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int c = 8 * j + 2 * h;
+                    w[h] = keep ? pack_bf16(fmaxf(v[c] + bj[2 * h], 0.0f), fmaxf(v[c + 1] + bj[2 * h + 1], 0.0f)) : 0u;
+                }
+                *reinterpret_cast<uint4*>(orow + ((j ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            mma_commit(&empty[stage]);
-            mma_commit(&accf[b]);
+            fence_async_smem();
+            epi_sync(bar_id);
+            if (elected) {
+                tma_store_2d(&a.out_map, out, 0, (int)(tile * 128));
+                bulk_commit();
+            }
         }
-        mma_commit(&fin);
-        mbar_drain(&fin, 0, a.err);
+        if (elected) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kConvProd + kEpiWarps) tmem_dealloc(tmem, NCOLS);
+    if (warp == 1) tmem_dealloc(tmem, NCOLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -493,8 +550,6 @@ constexpr int kHaloRowsMax = halo_tile_rows(SURFMCMC_MAX_L);
 constexpr int kTmaStage = kHaloRowsMax * 128;   // stage stride in bytes
 static_assert(kHaloRowsMax <= 256 && kTmaStage % 1024 == 0, "halo tile");
 
-constexpr int kOutTile = 128 * 128;   // one 128 x 64 bf16 output tile
-constexpr int kConvAcc = 4;           // tensor-memory accumulators of the conv kernel
 
 template <int NP, int EPI>
 constexpr size_t conv_tma_smem_bytes() {
@@ -527,6 +582,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     static_assert(NACC % 2 == 0 && S % 2 == 0, "alternating issuers need even rings");
+    static_assert(NP == 64, "the epilogue drains 64 accumulator columns");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
@@ -638,8 +694,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             const bool keep = m < M && interior_rem(rem, L);
             const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
             float v[NP];
-#pragma unroll
-            for (int cc = 0; cc < NP / 16; ++cc) tmem_ld16(taddr + cc * 16, v + cc * 16);
+            tmem_ld64(taddr, v);
             tc_fence_before();
             mbar_arrive(&acce[b]);
             uint8_t* orow = out + row * 128;
@@ -1278,6 +1333,8 @@ struct CnnNet {
     float *logprob = nullptr, *dz5 = nullptr, *loss_item = nullptr, *loss = nullptr, *S5 = nullptr, *Sb5 = nullptr;
     float* partial = nullptr;
     int* err = nullptr;
+    // TMA map of the first layer's input x0 (16-byte rows of 4 positions)
+    CUtensorMap map_x0;
     // TMA maps of the 64-channel tensors that convs read: act[0..3], dz[0..1]
     CUtensorMap map_act[4], map_dz[2];
     // the same tensors in boxes of 128 rows (output tiles, ReLU gates)
@@ -1307,11 +1364,11 @@ cudaError_t prepare_kernels() {
     return cudaSuccess;
 }
 
-cudaError_t launch_conv1(const CnnNet* net, const ConvArgs& a, cudaStream_t s) {
+cudaError_t launch_conv1(const CnnNet* net, const Conv1Args& a, cudaStream_t s) {
     const long long tiles = (a.M + 127) / 128;
     if (tiles == 0) return cudaSuccess;
     const int grid = (int)(tiles < net->sms ? tiles : net->sms);
-    conv1_kernel<<<grid, kConvThreads, kC1Smem, s>>>(a);
+    conv1_kernel<<<grid, kC1Threads, kC1Smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1324,9 +1381,10 @@ cudaError_t launch_conv_tma(const CnnNet* net, const ConvTmaArgs& a, cudaStream_
     return cudaGetLastError();
 }
 
-// TMA map of a [rows][64] bf16 tensor: boxes of box_rows rows x 64
-// channels (128 bytes, the 128-byte swizzle), rows outside read as zero.
-cudaError_t make_map(CUtensorMap* map, void* base, long long rows, int box_rows) {
+// TMA map of a [rows][width] bf16 tensor in boxes of box_rows rows x width
+// (width 64: 128-byte rows with the 128-byte swizzle; width 8: 16-byte rows,
+// no swizzle); rows outside the tensor read as zero.
+cudaError_t make_map_w(CUtensorMap* map, void* base, long long rows, int box_rows, int width) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -1336,14 +1394,19 @@ cudaError_t make_map(CUtensorMap* map, void* base, long long rows, int box_rows)
         if (qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    const cuuint64_t dims[2] = {64, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {128};
-    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)width * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)width, (cuuint32_t)box_rows};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              width == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_map(CUtensorMap* map, void* base, long long rows, int box_rows) {
+    return make_map_w(map, base, rows, box_rows, 64);
 }
 
 // First layer: CUDA cores, then the in-order sum over the slices.
@@ -1419,12 +1482,12 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
     if ((e = prepare_kernels())) return e;
     input_maps_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(syn, n, L, net->x0);
     if ((e = cudaGetLastError())) return e;
-    ConvArgs c1;
+    Conv1Args c1;
     memset(&c1, 0, sizeof c1);
-    c1.act = net->x0;
+    c1.in_map = net->map_x0;
+    c1.out_map = net->tile_act[0];
     c1.wmat = net->fwd[0];
     c1.bias = net->theta + layer_boff(0);
-    c1.out_bf16 = net->act[0];
     c1.M = M;
     c1.L = L;
     c1.err = net->err;
@@ -1598,7 +1661,7 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     for (int l = 0; l < 3; ++l) na(&net->bwd[l], (size_t)64 * 576 * 2);
     na(&net->syn, (size_t)max_batch * 2 * L * (L - 1));
     na(&net->targets, (size_t)max_batch * 16);
-    na(&net->x0, (size_t)M * 4);
+    na(&net->x0, (size_t)(M + 3) / 4 * 16);   // whole 16-byte rows for the first layer's TMA map
     for (int l = 0; l < 4; ++l) na(&net->act[l], (size_t)M * 128);
     na(&net->dz5, (size_t)M * 8);
     na(&net->dz[0], (size_t)M * 128);
@@ -1611,6 +1674,8 @@ int surfmcmc_cnn_create(surfmcmc_ctx* ctx, int32_t L, int64_t max_batch, surfmcm
     na(&net->partial, (size_t)(net->sms > kMaxSplits ? net->sms : kMaxSplits) * kWgRows * 64 * 4);
     na(&net->err, 4);
     const int halo = halo_tile_rows(L);
+    if (e == cudaSuccess) e = make_map_w(&net->map_x0, net->x0, (M + 3) / 4, c1_strip_rows(L), 8);
+    if (e == cudaSuccess) e = cudaMemset(net->x0, 0, (size_t)(M + 3) / 4 * 16);
     for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->map_act[l], net->act[l], M, halo);
     for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = make_map(&net->map_dz[l], net->dz[l], M, halo);
     for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = make_map(&net->tile_act[l], net->act[l], M, 128);
