@@ -317,6 +317,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// The same after max(x, 0), in one conversion (round to nearest even).
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));   // b: high half
+    return d;
+}
+
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
@@ -326,8 +333,7 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 struct Conv1Args {
     CUtensorMap in_map;   // input [M][2] bf16 viewed as [ceil(M/4)][8], box 8 x c1_strip_rows(L), no swizzle
     CUtensorMap out_map;  // output [M_alloc][64] bf16, box 64 x 128, 128-byte swizzle
-    const bf16* wmat;     // [64][32] operand B (k = tap * 2 + ci, zero from k = 18)
-    const float* bias;    // [64]
+    const bf16* wmat;     // [64][32] operand B (k = tap * 2 + ci; k = 18..20: the bias in three parts)
     long long M;          // positions n P^2
     int L;
     int* err;
@@ -352,12 +358,15 @@ __device__ __forceinline__ long long floor_div4(long long v) { return v >= 0 ? v
 // First layer (2 input channels, K = 18 padded to 32).  Warp 0 (one thread)
 // loads by TMA the strip of input positions a tile's taps read (4 B per
 // position); warps 10-13 build the tile's operand rows from it in shared
-// memory (row r, group g = taps 4g .. 4g+3; group 3 stays zero); warp 1 (one
-// thread) issues the two K = 16 MMAs into one of four accumulators; two
-// groups of four warps (2-5 and 6-9) drain alternate tiles (bias + ReLU, zero
-// border) into 128-byte-swizzled staging buffers that one thread of the
-// group stores with a TMA copy.  With K this small the MMAs are short and
-// the drain is the longest step of a tile, so two tiles drain at once.
+// memory (row r, group g = taps 4g .. 4g+3, then three constant-one columns
+// k = 18..20 that multiply the bias's three bf16 parts in the weight operand;
+// rows of border positions are all zero, so their outputs are zero; group 3
+// stays zero); warp 1 (one thread) issues the two K = 16 MMAs into one of
+// four accumulators; two groups of four warps (2-5 and 6-9) drain alternate
+// tiles (ReLU and rounding in one conversion) into 128-byte-swizzled staging
+// buffers that one thread of the group stores with a TMA copy.  With K this
+// small the MMAs are short and the drain is the longest step of a tile, so
+// two tiles drain at once.
 __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_constant__ Conv1Args a) {
     constexpr int S = kC1S, KGS = kC1KP / 8, NP = 64, NACC = kConvAcc;
     constexpr uint32_t NCOLS = NACC * NP;
@@ -371,7 +380,6 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
     __shared__ __align__(8) uint64_t full[S], sfree[S], afull[S], aempty[S], accf[NACC], acce[NACC], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ __align__(16) float sBias[NP];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = a.M;
@@ -383,7 +391,6 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.wmat + (size_t)r * kC1KP) + g);
         *reinterpret_cast<uint4*>(sB + core_off(r, g, KGS)) = v;
     }
-    if (tid < NP) sBias[tid] = __ldg(a.bias + tid);
     // operand group 3 (k = 24 .. 31) is never written again
     for (int idx = tid; idx < S * kC1Stage / 16; idx += kC1Threads)
         reinterpret_cast<uint4*>(sA)[idx] = make_uint4(0u, 0u, 0u, 0u);
@@ -447,6 +454,7 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
     } else if (warp >= 10) {
         // operand rows: thread r builds row r of every tile
         const int r = 32 * (warp - 10) + lane;
+        const int PP = (L + 2) * (L + 2);
         int sh[9];
 #pragma unroll
         for (int t = 0; t < 9; ++t) sh[t] = tap_shift(t, L);
@@ -457,15 +465,18 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
             const long long s0 = tile * 128 - P1;
             const int base = r + P1 + (int)(s0 - 4 * floor_div4(s0));   // strip index of position tile*128 + r
             const uint32_t* strip = reinterpret_cast<const uint32_t*>(sStrip + stage * kC1StripStage);
+            const int rem = (int)((tile * 128) % PP + r) % PP;
+            const bool keep = tile * 128 + r < M && interior_rem(rem, L);
             uint32_t w[9];
 #pragma unroll
-            for (int t = 0; t < 9; ++t) w[t] = strip[base + sh[t]];
+            for (int t = 0; t < 9; ++t) w[t] = keep ? strip[base + sh[t]] : 0u;
+            const uint32_t one2 = keep ? 0x3F803F80u : 0u;   // bf16 1.0 at k = 18, 19 (and k = 20)
             mbar_arrive(&sfree[stage]);
             if (use > 0 && !mbar_wait(&aempty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
             uint8_t* st = sA + stage * kC1Stage;
             *reinterpret_cast<uint4*>(st + core_off(r, 0, KGS)) = make_uint4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<uint4*>(st + core_off(r, 1, KGS)) = make_uint4(w[4], w[5], w[6], w[7]);
-            *reinterpret_cast<uint4*>(st + core_off(r, 2, KGS)) = make_uint4(w[8], 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(st + core_off(r, 2, KGS)) = make_uint4(w[8], one2, one2 & 0xFFFFu, 0u);
             fence_async_smem();
             mbar_arrive(&afull[stage]);
         }
@@ -476,7 +487,6 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
         const bool elected = (warp == 2 || warp == 6) && lane == 0;
-        const int PP = (L + 2) * (L + 2);
         uint32_t it = grp, k = 0;
         for (long long tile = blockIdx.x + (long long)grp * gridDim.x; tile < n_tiles;
              tile += 2LL * gridDim.x, it += 2, ++k) {
@@ -486,9 +496,6 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
             const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err);
             if (!epi_all(ok, bar_id)) break;
             tc_fence_after();
-            const long long m = tile * 128 + row;
-            const int rem = (int)((tile * 128) % PP + row) % PP;
-            const bool keep = m < M && interior_rem(rem, L);
             const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
             float v[NP];
             tmem_ld64(taddr, v);
@@ -498,15 +505,9 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
             const int sw = row & 7;
 #pragma unroll
             for (int j = 0; j < NP / 8; ++j) {
-                const float4 b0 = *reinterpret_cast<const float4*>(sBias + 8 * j);
-                const float4 b1 = *reinterpret_cast<const float4*>(sBias + 8 * j + 4);
-                const float bj[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                 uint32_t w[4];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int c = 8 * j + 2 * h;
-                    w[h] = keep ? pack_bf16(fmaxf(v[c] + bj[2 * h], 0.0f), fmaxf(v[c + 1] + bj[2 * h + 1], 0.0f)) : 0u;
-                }
+                for (int h = 0; h < 4; ++h) w[h] = pack_bf16_relu(v[8 * j + 2 * h], v[8 * j + 2 * h + 1]);
                 *reinterpret_cast<uint4*>(orow + ((j ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
             fence_async_smem();
@@ -1048,6 +1049,14 @@ __global__ void pack_kernel(PackArgs a) {
         const int co = (int)(j / kp), k = (int)(j - (long long)co * kp);
         float v = 0.0f;
         if (co < layer_cout(l) && k < 9 * cin) v = a.theta[layer_woff(l) + (long long)co * 9 * cin + k];
+        if (l == 0 && k >= 18 && k < 21) {
+            // the bias as the exact sum of three bf16 parts (8 significant
+            // bits each), multiplied by constant-one operand columns
+            const float b = a.theta[layer_boff(0) + co];
+            const float b1 = __bfloat162float(__float2bfloat16_rn(b));
+            const float b2 = __bfloat162float(__float2bfloat16_rn(b - b1));
+            v = k == 18 ? b1 : k == 19 ? b2 : b - b1 - b2;
+        }
         a.fwd[l][j] = __float2bfloat16_rn(v);
     } else {
         const long long j = i - a.fwd_begin[5];
@@ -1487,7 +1496,6 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
     c1.in_map = net->map_x0;
     c1.out_map = net->tile_act[0];
     c1.wmat = net->fwd[0];
-    c1.bias = net->theta + layer_boff(0);
     c1.M = M;
     c1.L = L;
     c1.err = net->err;
