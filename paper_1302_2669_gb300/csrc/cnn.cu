@@ -1086,45 +1086,71 @@ __device__ __forceinline__ float warp_prod_except(float t, int skip) {
     return r;
 }
 
-__global__ void readout_kernel(const bf16* w5, const float* b5, const bf16* a4, const uint8_t* syn, long long n,
-                               int L, const float* targets, float* logprob, float* dz5, float* loss_item) {
+// Positions of a middle line evaluated per pass of the readout: their taps
+// share rows, so K positions take (K + 2) x 3 loads per line instead of 9 K.
+constexpr int kReadK = 4;
+
+__global__ void __launch_bounds__(256, 4) readout_kernel(const bf16* w5, const float* b5, const bf16* a4,
+                                                      const uint8_t* syn, long long n, int L, const float* targets,
+                                                      float* logprob, float* dz5, float* loss_item) {
+    // last-layer weights of channels 2 lane, 2 lane + 1 for (output, tap)
+    __shared__ float2 sw[2][9][32];
+    for (int idx = threadIdx.x; idx < 2 * 9 * 32; idx += blockDim.x) {
+        const int co = idx / 288, t = (idx / 32) % 9, ln = idx % 32;
+        const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(w5 + co * 576 + t * 64) + ln);
+        sw[co][t][ln] = make_float2(bf16_lo(v), bf16_hi(v));
+    }
+    __syncthreads();
     const long long item = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (item >= n) return;
     const int m = (L - 1) / 2, P = L + 2;
     const long long base = item * P * P + P + 1;   // map (0, 0)
-    float w[2][9][2];
-#pragma unroll
-    for (int co = 0; co < 2; ++co)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(w5 + co * 576 + t * 64) + lane);
-            w[co][t][0] = bf16_lo(v);
-            w[co][t][1] = bf16_hi(v);
-        }
     const uint32_t* a = reinterpret_cast<const uint32_t*>(a4) + lane;   // 32 words per position
     float sa = 0.0f, sb = 0.0f;
-    for (int i = 0; i < L; ++i) {
-        const long long qa = base + (long long)i * P + m, qb = base + (long long)m * P + i;
-        float acc0 = 0.0f, acc1 = 0.0f;
+    for (int i = 0; i < L; i += kReadK) {
+        // line a: positions (i + k, m), rows i - 1 .. i + K, columns m - 1 .. m + 1;
+        // line b: positions (m, i + k), columns i - 1 .. i + K, rows m - 1 .. m + 1
+        uint32_t la[kReadK + 2][3], lb[kReadK + 2][3];
+#pragma unroll
+        for (int r = 0; r < kReadK + 2; ++r) {
+            const int y = i - 1 + r;             // <= L: the bottom (right) border at most
+            const bool ok = y <= L;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                la[r][c] = ok ? __ldg(a + (base + (long long)y * P + (m - 1 + c)) * 32) : 0u;
+                lb[r][c] = ok ? __ldg(a + (base + (long long)(m - 1 + c) * P + y) * 32) : 0u;
+            }
+        }
+        float acc[2][kReadK];
+#pragma unroll
+        for (int k = 0; k < kReadK; ++k) acc[0][k] = acc[1][k] = 0.0f;
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-            const int sh = (t / 3 - 1) * P + (t % 3 - 1);
-            const uint32_t x0 = __ldg(a + (qa + sh) * 32), x1 = __ldg(a + (qb + sh) * 32);
-            acc0 = fmaf(bf16_lo(x0), w[0][t][0], acc0);
-            acc0 = fmaf(bf16_hi(x0), w[0][t][1], acc0);
-            acc1 = fmaf(bf16_lo(x1), w[1][t][0], acc1);
-            acc1 = fmaf(bf16_hi(x1), w[1][t][1], acc1);
+            const float2 wa = sw[0][t][lane], wb = sw[1][t][lane];
+            const int dy = t / 3, dx = t % 3;
+#pragma unroll
+            for (int k = 0; k < kReadK; ++k) {
+                const uint32_t xa = la[k + dy][dx], xb = lb[k + dx][dy];
+                acc[0][k] = fmaf(bf16_lo(xa), wa.x, acc[0][k]);
+                acc[0][k] = fmaf(bf16_hi(xa), wa.y, acc[0][k]);
+                acc[1][k] = fmaf(bf16_lo(xb), wb.x, acc[1][k]);
+                acc[1][k] = fmaf(bf16_hi(xb), wb.y, acc[1][k]);
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
-            acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
-        }
-        if (lane == i) {
-            sa = acc0 + __ldg(b5 + 0);
-            sb = acc1 + __ldg(b5 + 1);
-        }
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < kReadK; ++k) {
+                acc[0][k] += __shfl_xor_sync(0xffffffffu, acc[0][k], o);
+                acc[1][k] += __shfl_xor_sync(0xffffffffu, acc[1][k], o);
+            }
+#pragma unroll
+        for (int k = 0; k < kReadK; ++k)
+            if (lane == i + k && i + k < L) {
+                sa = acc[0][k] + __ldg(b5 + 0);
+                sb = acc[1][k] + __ldg(b5 + 1);
+            }
     }
     float ta = 1.0f, tb = 1.0f;
     if (lane < L) {
