@@ -552,9 +552,14 @@ constexpr int kTmaStage = kHaloRowsMax * 128;   // stage stride in bytes
 static_assert(kHaloRowsMax <= 256 && kTmaStage % 1024 == 0, "halo tile");
 
 
+// Staging buffers of the epilogue: two output tiles, or three for the
+// ReLU-gate epilogue, whose gate tile is loaded two tiles ahead into the
+// buffer that then receives the output in place.
+__host__ __device__ constexpr int conv_out_bufs(int epi) { return epi == kEpiMask ? 3 : 2; }
+
 template <int NP, int EPI>
 constexpr size_t conv_tma_smem_bytes() {
-    return (size_t)kTmaStages * kTmaStage + (size_t)NP * 576 * 2 + 2 * kOutTile + 1024;
+    return (size_t)kTmaStages * kTmaStage + (size_t)NP * 576 * 2 + conv_out_bufs(EPI) * kOutTile + 1024;
 }
 
 // Warp 0 (one thread) loads the halo tile of each position tile by TMA into
@@ -568,7 +573,8 @@ constexpr size_t conv_tma_smem_bytes() {
 // The bf16 epilogues write their tile into one of two output buffers in the
 // 128-byte-swizzled layout (16-byte chunk j of row r at chunk j ^ (r & 7)),
 // which one thread then stores with a single TMA copy; the ReLU gate of the
-// backward pass arrives in that buffer by TMA before the tile is drained.
+// backward pass arrives by TMA in the buffer of its tile two tiles ahead
+// (three buffers) and the gated output overwrites it in place.
 template <int NP, int EPI>
 __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_constant__ ConvTmaArgs a) {
     constexpr int S = kTmaStages, KG = 576 / 8, NACC = kConvAcc;
@@ -578,8 +584,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;                      // S halo tiles, 1024-byte aligned
     uint8_t* sB = smem + S * kTmaStage;
-    uint8_t* sOut = sB + NP * 576 * 2;       // 2 output tiles (bf16 epilogues), 1024-byte aligned
-    __shared__ __align__(8) uint64_t full[S], empty[S], accf[NACC], acce[NACC], maskf[2], fin[2];
+    uint8_t* sOut = sB + NP * 576 * 2;       // output tiles (bf16 epilogues), 1024-byte aligned
+    constexpr int NOB = conv_out_bufs(EPI);
+    __shared__ __align__(8) uint64_t full[S], empty[S], accf[NACC], acce[NACC], maskf[3], fin[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     static_assert(NACC % 2 == 0 && S % 2 == 0, "alternating issuers need even rings");
@@ -604,8 +611,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             mbar_init(&accf[b], 1);
             mbar_init(&acce[b], kEpiWarps * 32);
         }
-        mbar_init(&maskf[0], 1);
-        mbar_init(&maskf[1], 1);
+        for (int k = 0; k < 3; ++k) mbar_init(&maskf[k], 1);
         mbar_init(&fin[0], 1);
         mbar_init(&fin[1], 1);
         abort_flag = 0;
@@ -676,17 +682,22 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
         float bias[EPI == kEpiRelu ? NP : 1];
 #pragma unroll
         for (int j = 0; j < (EPI == kEpiRelu ? NP : 1); ++j) bias[j] = EPI == kEpiRelu ? __ldg(a.bias + j) : 0.0f;
+        // the block's k-th tile is blockIdx.x + k gridDim.x; its gate tile
+        // (ReLU-gate epilogue) goes to buffer k mod 3, two tiles ahead
+        const uint32_t n_mine = (uint32_t)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1);
+        uint32_t issued = 0, gated = 0;   // gate loads issued / seen complete (elected thread)
+        auto issue_gate = [&](uint32_t k) {
+            mbar_expect_tx(&maskf[k % NOB], kOutTile);
+            tma_load_2d(sOut + (k % NOB) * kOutTile, &a.mask_map, 0,
+                        (int)((blockIdx.x + (long long)k * gridDim.x) * 128), &maskf[k % NOB]);
+        };
+        if (EPI == kEpiMask && elected)
+            for (; issued < 2 && issued < n_mine; ++issued) issue_gate(issued);
         uint32_t it = 0;
         for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-            const uint32_t b = it % NACC, u = it / NACC, ob = it & 1;
+            const uint32_t b = it % NACC, u = it / NACC, ob = it % NOB;
             uint8_t* out = sOut + ob * kOutTile;
-            if (elected) {
-                bulk_wait_read<1>();   // the store of two tiles back has left this buffer
-                if (EPI == kEpiMask) {
-                    mbar_expect_tx(&maskf[ob], kOutTile);
-                    tma_load_2d(out, &a.mask_map, 0, (int)(tile * 128), &maskf[ob]);
-                }
-            }
+            if (EPI == kEpiRelu && elected) bulk_wait_read<1>();   // the store of two tiles back has left this buffer
             const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err);
             if (!epi_all(ok)) break;
             tc_fence_after();
@@ -700,7 +711,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             mbar_arrive(&acce[b]);
             uint8_t* orow = out + row * 128;
             const int sw = row & 7;
-            if (EPI == kEpiMask) mbar_wait(&maskf[ob], (it >> 1) & 1, &abort_flag, a.err);
+            if (EPI == kEpiMask && mbar_wait(&maskf[ob], (it / NOB) & 1, &abort_flag, a.err) && elected) ++gated;
 #pragma unroll
             for (int j = 0; j < NP / 8; ++j) {
                 uint4* chunk = reinterpret_cast<uint4*>(orow + ((j ^ sw) << 4));
@@ -729,12 +740,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             if (elected) {
                 tma_store_2d(&a.out_map, out, 0, (int)(tile * 128));
                 bulk_commit();
+                if (EPI == kEpiMask && issued < n_mine) {
+                    bulk_wait_read<1>();   // the previous tile's store has left buffer (it + 2) mod 3
+                    issue_gate(issued++);
+                }
             }
         }
         if (elected) {
-            // after an abort a gate load may still be in flight
-            if (EPI == kEpiMask && it < (uint32_t)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x))
-                mbar_drain(&maskf[it & 1], (it >> 1) & 1, a.err);
+            // after an abort gate loads may still be in flight
+            if (EPI == kEpiMask)
+                for (uint32_t k = gated; k < issued; ++k) mbar_drain(&maskf[k % NOB], (k / NOB) & 1, a.err);
             bulk_wait_all();
         }
     }
