@@ -267,15 +267,9 @@ __device__ __forceinline__ bool epi_all(bool v, uint32_t id = 1) {
     return r != 0;
 }
 
-// Padded maps: P = L + 2, position m of a batch; interior positions are the
-// L x L map, the rest is the zero border.
-__device__ __forceinline__ bool interior(long long m, int L) {
-    const int P = L + 2, PP = P * P;
-    const int rem = (int)(m % PP), y = rem / P, x = rem - (rem / P) * P;
-    return y >= 1 && y <= L && x >= 1 && x <= L;
-}
-
-// The same for position rem = m mod P^2 inside its map.
+// Padded maps: P = L + 2; interior positions are the L x L map, the rest is
+// the zero border.  Whether position rem = m mod P^2 inside its map is
+// interior:
 __device__ __forceinline__ bool interior_rem(int rem, int L) {
     const int P = L + 2, y = rem / P, x = rem - y * P;
     return y >= 1 && y <= L && x >= 1 && x <= L;
@@ -1238,34 +1232,53 @@ __global__ void loss_sum_kernel(const float* loss_item, long long n, float* loss
 // Input gradient of the last layer, gated by the ReLU of layer 4 (padded
 // maps; the border of dz5 is zero): dZ4[q][ci] = [a4[q][ci] > 0] sum over
 // taps t of sum_co W5[co][t][ci] dz5[q - shift(t)][co] for interior q, and 0
-// on the border.
-__global__ void conv5_dgrad_kernel(const bf16* w5, const float* dz5, const bf16* a4, long long M, int L,
+// on the border.  dz5 is nonzero only on channel 0 of the middle column x = m
+// and channel 1 of the middle row y = m, so dZ4 can be nonzero only in the
+// bands y in [m-1, m+1] (3L positions) and x in [m-1, m+1] outside them
+// (3(L-3) at most): the caller zeroes dZ4 and this kernel computes those
+// bands, thread = (item, band slot of 6L, 8-channel group).
+__global__ void conv5_dgrad_kernel(const bf16* w5, const float* dz5, const bf16* a4, long long n, int L,
                                    bf16* dz4) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // m * 8 + ci group
-    if (i >= M * 8) return;
-    const long long m = i >> 3;
-    const int cg = (int)(i & 7) * 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int NB = 6 * L;
+    if (i >= n * NB * 8) return;
+    const long long item = i / (NB * 8);
+    const int j = (int)(i / 8 - item * NB), cg = (int)(i & 7) * 8;
+    const int m = (L - 1) / 2, P = L + 2;
+    int y, x;
+    if (j < 3 * L) {
+        y = m - 1 + j / L;
+        x = j % L;
+    } else {
+        y = (j - 3 * L) / 3;
+        x = m - 1 + (j - 3 * L) % 3;
+        if (y >= m - 1 && y <= m + 1) return;   // in the row band
+    }
+    if (y < 0 || y >= L || x < 0 || x >= L) return;
+    const long long q = item * P * P + (long long)(y + 1) * P + (x + 1);
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const bool in = interior(m, L);
-    for (int t = 0; t < 9 && in; ++t) {
-        const float2 d = *reinterpret_cast<const float2*>(dz5 + (m - tap_shift(t, L)) * 2);
+    bool any = false;
+    for (int t = 0; t < 9; ++t) {
+        const float2 d = *reinterpret_cast<const float2*>(dz5 + (q - tap_shift(t, L)) * 2);
         if (d.x == 0.0f && d.y == 0.0f) continue;
+        any = true;
         const float g[2] = {d.x, d.y};
         for (int co = 0; co < kOut; ++co) {
             const uint4 wv = *reinterpret_cast<const uint4*>(w5 + (long long)co * 576 + t * 64 + cg);
             const uint32_t ww[4] = {wv.x, wv.y, wv.z, wv.w};
-            for (int j = 0; j < 4; ++j) {
-                acc[2 * j] += bf16_lo(ww[j]) * g[co];
-                acc[2 * j + 1] += bf16_hi(ww[j]) * g[co];
+            for (int k = 0; k < 4; ++k) {
+                acc[2 * k] += bf16_lo(ww[k]) * g[co];
+                acc[2 * k + 1] += bf16_hi(ww[k]) * g[co];
             }
         }
     }
-    const uint4 av = *reinterpret_cast<const uint4*>(a4 + m * 64 + cg);
+    if (!any) return;   // stays zero
+    const uint4 av = *reinterpret_cast<const uint4*>(a4 + q * 64 + cg);
     const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
     uint32_t o[4];
-    for (int j = 0; j < 4; ++j)
-        o[j] = pack_bf16(bf16_lo(aw[j]) > 0.0f ? acc[2 * j] : 0.0f, bf16_hi(aw[j]) > 0.0f ? acc[2 * j + 1] : 0.0f);
-    *reinterpret_cast<uint4*>(dz4 + m * 64 + cg) = make_uint4(o[0], o[1], o[2], o[3]);
+    for (int k = 0; k < 4; ++k)
+        o[k] = pack_bf16(bf16_lo(aw[k]) > 0.0f ? acc[2 * k] : 0.0f, bf16_hi(aw[k]) > 0.0f ? acc[2 * k + 1] : 0.0f);
+    *reinterpret_cast<uint4*>(dz4 + q * 64 + cg) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // Last-layer weight and bias gradients of one syndrome (block per item, 576
@@ -1299,12 +1312,13 @@ __global__ void conv5_wgrad_item_kernel(const float* dz5, const bf16* a4, int L,
 }
 
 // Sum over the items: dW5[co][j] = sum_item S[item][co][j], db5[co] =
-// sum_item Sb[item][co].  A block of 8 warps takes 32 consecutive outputs;
-// warp w adds the items w, w + 8, .. in order and the 8 warp sums are added
-// in order.
-__global__ void __launch_bounds__(256) conv5_wgrad_kernel(const float* S, const float* Sb, long long n, float* grad_w,
-                                                          float* grad_b) {
-    __shared__ float part[8][32];
+// sum_item Sb[item][co].  A block of 32 warps takes 32 consecutive outputs;
+// warp w adds the items w, w + 32, .. in order and the 32 warp sums are
+// added in order.
+constexpr int kC5Warps = 32;
+__global__ void __launch_bounds__(kC5Warps * 32) conv5_wgrad_kernel(const float* S, const float* Sb, long long n,
+                                                                    float* grad_w, float* grad_b) {
+    __shared__ float part[kC5Warps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
     const bool is_w = i < kOut * 576, valid = i < kOut * 576 + kOut;
@@ -1312,18 +1326,18 @@ __global__ void __launch_bounds__(256) conv5_wgrad_kernel(const float* S, const 
     if (is_w) {
         const int co = i / 576, jj = i - co * 576;
 #pragma unroll 4
-        for (long long k = w; k < n; k += 8) s += S[(k * 2 + co) * 576 + jj];
+        for (long long k = w; k < n; k += kC5Warps) s += S[(k * 2 + co) * 576 + jj];
     } else if (valid) {
         const int co = i - kOut * 576;
 #pragma unroll 4
-        for (long long k = w; k < n; k += 8) s += Sb[k * 2 + co];
+        for (long long k = w; k < n; k += kC5Warps) s += Sb[k * 2 + co];
     }
     part[w][lane] = s;
     __syncthreads();
     if (w == 0 && valid) {
         float t = part[0][lane];
 #pragma unroll
-        for (int k = 1; k < 8; ++k) t += part[k][lane];
+        for (int k = 1; k < kC5Warps; ++k) t += part[k][lane];
         if (is_w) grad_w[i] = t;
         else grad_b[i - kOut * 576] = t;
     }
@@ -1571,12 +1585,13 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
     // last layer (CUDA cores)
     conv5_wgrad_item_kernel<<<(unsigned)n, 576, 0, s>>>(net->dz5, net->act[3], L, net->S5, net->Sb5);
     if ((e = cudaGetLastError())) return e;
-    conv5_wgrad_kernel<<<(kOut * 576 + kOut + 31) / 32, 256, 0, s>>>(net->S5, net->Sb5, n,
+    conv5_wgrad_kernel<<<(kOut * 576 + kOut + 31) / 32, kC5Warps * 32, 0, s>>>(net->S5, net->Sb5, n,
                                                                         net->grad + layer_woff(4),
                                                                         net->grad + layer_boff(4));
     if ((e = cudaGetLastError())) return e;
-    conv5_dgrad_kernel<<<(unsigned)((M * 8 + 255) / 256), 256, 0, s>>>(net->fwd[4], net->dz5, net->act[3], M, L,
-                                                                        net->dz[0]);
+    if ((e = cudaMemsetAsync(net->dz[0], 0, (size_t)M * 128, s))) return e;
+    conv5_dgrad_kernel<<<(unsigned)((n * 6 * L * 8 + 255) / 256), 256, 0, s>>>(net->fwd[4], net->dz5, net->act[3], n, L,
+                                                                             net->dz[0]);
     if ((e = cudaGetLastError())) return e;
     // layers 4, 3, 2: weight gradient, then input gradient gated by the layer below
     ConvTmaArgs a;
