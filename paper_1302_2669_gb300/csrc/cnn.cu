@@ -29,9 +29,12 @@
 //     weight operand stays in shared memory for the whole persistent block;
 //     two threads issue the MMAs (alternate tiles), four warps drain the
 //     four tensor-memory accumulators (bias + ReLU, or the ReLU gate of the
-//     layer below) and store each tile with a TMA copy.  The first layer
-//     (2 input channels, K = 18 padded to 32) gathers its operand with
-//     producer warps;
+//     layer below) and store each tile with a TMA copy.  The 64-channel
+//     conv is bound by shared-memory bandwidth: an N = 64 MMA reads 6 KB of
+//     operands.  The first layer (2 input channels, K = 18 padded to 32)
+//     builds its operand from a TMA-loaded strip of input positions, adds
+//     the bias through constant-one operand columns and drains alternate
+//     tiles with two groups of warps;
 //   weight gradient of the 64-channel layers: D[(tap, ci)][co] =
 //     sum_p X[p + tap][ci] dZ[p][co], a GEMM over positions whose operands
 //     are read MN-major by TMA straight from the [position][channel]
