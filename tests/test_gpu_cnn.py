@@ -62,7 +62,9 @@ def _forward_check(gpu, ref):
     assert d.mean() < 2e-3, d.mean()
 
 
-@pytest.mark.parametrize("L,n,seed", [(3, 5, 1), (5, 13, 2), (9, 7, 3)])
+# L = 3 (the smallest network size), an even L, and L = 31 (the largest:
+# widest input strips and halo tiles, the longest middle lines)
+@pytest.mark.parametrize("L,n,seed", [(3, 5, 1), (4, 9, 4), (5, 13, 2), (9, 7, 3), (31, 3, 5)])
 def test_forward_parity_small(pkg, ctx, L, n, seed):
     syn, _ = O.gen_syndromes(700 + seed, 0, n, L, 0.15)
     p = _params(seed)
@@ -112,7 +114,7 @@ def test_forward_batching_and_buffers(pkg, ctx):
     b.close()
 
 
-@pytest.mark.parametrize("L,n,seed", [(5, 7, 21), (9, 37, 22), (17, 64, 23)])
+@pytest.mark.parametrize("L,n,seed", [(5, 7, 21), (6, 11, 25), (9, 37, 22), (17, 64, 23), (31, 4, 24)])
 def test_gradient_parity(pkg, ctx, L, n, seed):
     rng = np.random.default_rng(seed)
     syn, _ = O.gen_syndromes(800 + seed, 0, n, L, 0.14)
