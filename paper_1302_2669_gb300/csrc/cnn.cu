@@ -41,8 +41,9 @@
 //     tensors (tap windows are row offsets of a halo tile, two taps make
 //     M = 128, a constant ones tile gives the bias row); one block per SM
 //     over a contiguous range of positions, partial sums added in a fixed
-//     order.  The first layer's (2 input channels, 19 rows) runs on the
-//     CUDA cores.
+//     order.  The first layer's (2 input channels, 19 rows) is the same
+//     GEMM with its operand rows built from an input strip, M padded to
+//     128 by the dZ tile.
 // The last layer (2 outputs, read and differentiated on the middle lines
 // only: forward fused into the readout, backward), the readout, loss and
 // Adam steps run on the CUDA cores.
@@ -924,69 +925,167 @@ __global__ void __launch_bounds__(kWgTmaThreads, 1) wgrad_kernel(const __grid_co
     if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-// The first layer's weight and bias gradients on the CUDA cores (2 input
-// channels: 18 weights and a bias per output channel, too thin a GEMM for the
-// tensor cores): partial[s][R][co] = sum over the slice's positions p of
-// X[p + shift(tap)][ci] dZ[p][co] (R = 2 tap + ci), R = 18: sum of dZ[p][co].
-// Block s walks its slice in tiles of kWg0Tile positions; the tile's inputs
-// and their halo are staged in shared memory as float pairs (zero outside the
-// batch), its dZ rows with 16-byte loads.  Threads: 4 position groups x 64 output channels; group g takes the
-// tile's positions g, g + 4, ..; the groups are added in order.  dZ is zero
-// on the map borders, so the sums run over the padded positions as they are.
-constexpr int kWg0Threads = 256;
+// ---------------------------------------------------------------------------
+// The first layer's weight and bias gradients on tcgen05: D[R][co] = sum_p
+// A0[p][R] dZ[p][co] with A0[p][2 tap + ci] = X[p + shift(tap)][ci] and
+// A0[p][18] = 1 (the bias row), a GEMM over positions (K) whose operands are
+// both MN-major under the 128-byte swizzle.  Per chunk of 128 positions one
+// TMA copy brings the strip of input positions its taps read (as for the
+// first layer's conv) and another the chunk's 128 dZ rows; four warps write
+// the chunk's A0 rows (128 bytes each: values 0..18, then zeros) into a
+// swizzled tile; one thread issues eight K = 16 MMAs of M = 128 whose first
+// 64-row atom is A0 and whose second is the chunk's dZ tile (the leading
+// byte offset is the step from one tile to the other; rows 64..127 of D are
+// never read).  D accumulates over the block's contiguous range of chunks in
+// 64 tensor-memory columns, and rows 0..18 become the block's partial sums.
+// dZ is zero on the map borders and past the batch (the caller zeroes the
+// tail of the last chunk), so every position can enter the sums.
+// ---------------------------------------------------------------------------
 constexpr int kWg0Rows = 19;
-constexpr int kWg0Tile = 128;
+struct Wgrad0Args {
+    CUtensorMap in_map;   // X: [M][2] bf16 as [ceil(M/4)][8], box 8 x c1_strip_rows(L)
+    CUtensorMap dzmap;    // dZ [M_alloc][64] bf16, box 64 x 128, 128-byte swizzle
+    float* partial;       // [slices][19][64]
+    long long M;
+    int L;
+    int* err;
+};
 
-__global__ void __launch_bounds__(kWg0Threads, 3) wgrad0_kernel(const bf16* x, const bf16* dz, long long M, int L,
-                                                            float* partial) {
-    __shared__ float2 sx[kWg0Tile + 2 * (SURFMCMC_MAX_L + 3)];
-    __shared__ __align__(16) uint16_t sdz[kWg0Tile][64];
-    __shared__ float red[4][kWg0Rows][64];
-    const int co = threadIdx.x & 63, g = threadIdx.x >> 6;
-    const int P1 = L + 3;
-    const long long begin = M * blockIdx.x / gridDim.x, end = M * (blockIdx.x + 1) / gridDim.x;
-    const uint32_t* xw = reinterpret_cast<const uint32_t*>(x);   // both channels of a position
-    int sh[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) sh[t] = P1 + tap_shift(t, L);
-    float acc[kWg0Rows];
-#pragma unroll
-    for (int r = 0; r < kWg0Rows; ++r) acc[r] = 0.0f;
-    for (long long t0 = begin; t0 < end; t0 += kWg0Tile) {
-        const int n = (int)(end - t0 < kWg0Tile ? end - t0 : kWg0Tile);
-        __syncthreads();
-        for (int i = threadIdx.x; i < n + 2 * P1; i += blockDim.x) {
-            const long long src = t0 - P1 + i;
-            const uint32_t v = src >= 0 && src < M ? __ldg(xw + src) : 0u;
-            sx[i] = make_float2(bf16_lo(v), bf16_hi(v));
+constexpr int kW0S = 4;                              // pipeline depth
+constexpr int kW0Tile = 128 * 128;                   // one A0 or dZ tile of 128 rows
+constexpr int kW0Stage = 2 * kW0Tile;                // A0 tile, then the dZ tile
+constexpr int kW0Threads = 6 * 32;                   // TMA warp, MMA warp, 4 operand warps
+constexpr size_t kW0Smem = (size_t)kW0S * kW0Stage + kW0S * kC1StripStage + 1024;
+
+__global__ void __launch_bounds__(kW0Threads, 1) wgrad0_kernel(const __grid_constant__ Wgrad0Args a) {
+    constexpr uint32_t IDESC = idesc_bf16(128, 64) | (1u << 15) | (1u << 16);   // A, B MN-major
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sStrip = smem + kW0S * kW0Stage;
+    __shared__ __align__(8) uint64_t full[kW0S], afull[kW0S], empty[kW0S], accf;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = a.M;
+    const int L = a.L, P1 = L + 3;
+    const long long n_chunks = (M + 127) / 128;
+    const long long c_begin = n_chunks * blockIdx.x / gridDim.x, c_end = n_chunks * (blockIdx.x + 1) / gridDim.x;
+
+    // A0 tiles start zero: 16-byte chunks 3..7 of every row are never written
+    for (int i = tid; i < kW0S * (kW0Tile / 16); i += kW0Threads) {
+        const int st = i / (kW0Tile / 16), j = i - st * (kW0Tile / 16);
+        reinterpret_cast<uint4*>(smem + st * kW0Stage)[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kW0S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&afull[s], 128);
+            mbar_init(&empty[s], 1);
         }
-#pragma unroll
-        for (int k = 0; k < kWg0Tile * 8 / kWg0Threads; ++k) {
-            const int i = threadIdx.x + k * kWg0Threads, r = i >> 3, c = i & 7;
-            const uint4 v = r < n ? __ldg(reinterpret_cast<const uint4*>(dz + (t0 + r) * 64) + c) : make_uint4(0, 0, 0, 0);
-            reinterpret_cast<uint4*>(&sdz[r][0])[c] = v;
+        mbar_init(&accf, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();
+    if (warp == 1) tmem_alloc(&tmem_slot, 64);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)c1_strip_rows(L) * 16 + kW0Tile;
+            uint32_t q = 0;
+            for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
+                const uint32_t stage = q % kW0S, use = q / kW0S;
+                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                mbar_expect_tx(&full[stage], bytes);
+                tma_load_2d(sStrip + stage * kC1StripStage, &a.in_map, 0, (int)floor_div4(ch * 128 - P1),
+                            &full[stage]);
+                tma_load_2d(smem + stage * kW0Stage + kW0Tile, &a.dzmap, 0, (int)(ch * 128), &full[stage]);
+            }
+            for (uint32_t k = q > (uint32_t)kW0S ? q - kW0S : 0; k < q; ++k)
+                mbar_drain(&full[k % kW0S], (k / kW0S) & 1, a.err);
         }
-        __syncthreads();
-#pragma unroll 4
-        for (int j = g; j < n; j += 4) {
-            const float d = __uint_as_float((uint32_t)sdz[j][co] << 16);
-            acc[18] += d;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // descriptors as 32-bit halves: start / 16 in bits 0-13 and the
+            // leading byte offset / 16 (A's second atom: the dZ tile) in bits
+            // 16-29 of the low half
+            const uint64_t d0 = smem_desc_sw128(smem_u32(smem));
+            const uint32_t hi = (uint32_t)(d0 >> 32);
+            const uint32_t lo0 = (uint32_t)d0 & 0xFFFFu;
+            const uint32_t lbo = (uint32_t)(kW0Tile >> 4) << 16;
+            uint32_t q = 0;
+            bool ok = true;
+            for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
+                const uint32_t stage = q % kW0S, use = q / kW0S;
+                if (!mbar_wait(&afull[stage], use & 1, &abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_lo = (lo0 + stage * (kW0Stage / 16)) | lbo;
+                const uint32_t b_lo = (lo0 + stage * (kW0Stage / 16) + kW0Tile / 16) | lbo;
 #pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const float2 v = sx[j + sh[t]];
-                acc[2 * t] = fmaf(v.x, d, acc[2 * t]);
-                acc[2 * t + 1] = fmaf(v.y, d, acc[2 * t + 1]);
+                for (int ks = 0; ks < 8; ++ks)   // 16 positions (2048 bytes) per MMA
+                    mma_bf16_lh(tmem, a_lo + ks * 128, hi, b_lo + ks * 128, hi, IDESC,
+                                (ch > c_begin || ks > 0) ? 1u : 0u);
+                mma_commit(&empty[stage]);
+            }
+            // completes after every MMA of the block (also on the abort path)
+            mma_commit(&accf);
+            if (!ok || c_end == c_begin) mbar_drain(&accf, 0, a.err);
+        }
+    } else {
+        // operand rows: thread r writes row r (position ch * 128 + r) of every chunk
+        const int r = 32 * (warp - 2) + lane, sw = r & 7;
+        int sh[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) sh[t] = tap_shift(t, L);
+        uint32_t q = 0;
+        for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
+            const uint32_t stage = q % kW0S, use = q / kW0S;
+            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) break;
+            const long long s0 = ch * 128 - P1;
+            const int base = r + P1 + (int)(s0 - 4 * floor_div4(s0));   // strip index of position ch*128 + r
+            const uint32_t* strip = reinterpret_cast<const uint32_t*>(sStrip + stage * kC1StripStage);
+            uint32_t w[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) w[t] = strip[base + sh[t]];
+            uint8_t* row = smem + stage * kW0Stage + r * 128;
+            *reinterpret_cast<uint4*>(row + ((0 ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(row + ((1 ^ sw) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
+            *reinterpret_cast<uint4*>(row + ((2 ^ sw) << 4)) = make_uint4(w[8], 0x3F80u, 0u, 0u);   // R = 18: 1.0
+            fence_async_smem();
+            mbar_arrive(&afull[stage]);
+        }
+        if (warp == 4) {
+            // tensor-memory lanes 0..31 (this warp's quarter): rows R = 0..18
+            bool ok = c_end > c_begin;
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err));
+            float v[64];
+            if (ok) {
+                tc_fence_after();
+                tmem_ld64(tmem, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+            }
+            if (lane < kWg0Rows) {
+                float* out = a.partial + ((long long)blockIdx.x * kWg0Rows + lane) * 64;
+#pragma unroll
+                for (int i = 0; i < 64; i += 4)
+                    *reinterpret_cast<float4*>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
             }
         }
     }
-#pragma unroll
-    for (int r = 0; r < kWg0Rows; ++r) red[g][r][co] = acc[r];
+    tc_fence_before();
     __syncthreads();
-    for (int i = threadIdx.x; i < kWg0Rows * 64; i += blockDim.x) {
-        const int r = i >> 6, c = i & 63;
-        partial[((long long)blockIdx.x * kWg0Rows + r) * 64 + c] =
-            ((red[0][r][c] + red[1][r][c]) + red[2][r][c]) + red[3][r][c];
-    }
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, 64);
 }
 
 // partial[s][R][co] summed over s -> flat gradient of layer l.  A block of 8
@@ -1427,6 +1526,7 @@ cudaError_t prepare_kernels() {
     if ((e = set_smem(conv_tma_kernel<64, kEpiRelu>, conv_tma_smem_bytes<64, kEpiRelu>()))) return e;
     if ((e = set_smem(conv_tma_kernel<64, kEpiMask>, conv_tma_smem_bytes<64, kEpiMask>()))) return e;
     if ((e = set_smem(wgrad_kernel, kWgSmem))) return e;
+    if ((e = set_smem(wgrad0_kernel, kW0Smem))) return e;
     done = true;
     return cudaSuccess;
 }
@@ -1476,16 +1576,26 @@ cudaError_t make_map(CUtensorMap* map, void* base, long long rows, int box_rows)
     return make_map_w(map, base, rows, box_rows, 64);
 }
 
-// First layer: CUDA cores, then the in-order sum over the slices.
-cudaError_t launch_wgrad0(const CnnNet* net, const bf16* x, const bf16* dz, long long M, cudaStream_t s) {
-    long long slices = 2LL * net->sms;
-    const long long max_slices = (long long)kMaxSplits * kWgRows / kWg0Rows;   // the partial buffer
-    if (slices > max_slices) slices = max_slices;
-    if (slices > M) slices = M;
-    if (slices < 1) slices = 1;
-    wgrad0_kernel<<<(unsigned)slices, kWg0Threads, 0, s>>>(x, dz, M, net->L, net->partial);
-    cudaError_t e = cudaGetLastError();
-    if (e) return e;
+// First layer: rows of dZ past the batch in the last 128-position chunk are
+// zeroed first, then the in-order sum over the slices.
+cudaError_t launch_wgrad0(const CnnNet* net, int dzi, long long M, cudaStream_t s) {
+    const long long chunks = (M + 127) / 128;
+    if (chunks == 0) return cudaSuccess;
+    const long long m_alloc = net->max_batch * net->P * net->P;
+    const long long tail_end = chunks * 128 < m_alloc ? chunks * 128 : m_alloc;
+    cudaError_t e;
+    if (tail_end > M && (e = cudaMemsetAsync(net->dz[dzi] + M * 64, 0, (size_t)(tail_end - M) * 128, s))) return e;
+    const int slices = (int)(chunks < net->sms ? chunks : net->sms);
+    Wgrad0Args a;
+    memset(&a, 0, sizeof a);
+    a.in_map = net->map_x0;
+    a.dzmap = net->tile_dz[dzi];
+    a.partial = net->partial;
+    a.M = M;
+    a.L = net->L;
+    a.err = net->err;
+    wgrad0_kernel<<<slices, kW0Threads, kW0Smem, s>>>(a);
+    if ((e = cudaGetLastError())) return e;
     wgrad_reduce_kernel<<<(kWg0Rows * 64 + 31) / 32, 256, 0, s>>>(net->partial, (int)slices, kWg0Rows, 2,
                                                                      net->grad + layer_woff(0),
                                                                      net->grad + layer_boff(0));
@@ -1613,7 +1723,7 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
         if ((e = launch_conv_tma<64, kEpiMask>(net, a, s))) return e;
         cur ^= 1;
     }
-    return launch_wgrad0(net, net->x0, net->dz[cur], M, s);
+    return launch_wgrad0(net, cur, M, s);
 }
 
 cudaError_t cnn_adam_dev(CnnNet* net, float lr, cudaStream_t s) {
