@@ -132,21 +132,63 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def cpu_baseline(n_syn=None, p=0.13, seed=SYN_SEEDS[1]):
+def parity_ids(n: int, per_p: int = 4):
+    """Syndrome indices of the batch checked against the oracle: spread over
+    the batch, first and last included."""
+    if n <= per_p:
+        return list(range(n))
+    return sorted({(j * (n - 1)) // (per_p - 1) for j in range(per_p)})
+
+
+def cpu_baseline(ids_per_p, sweeps=SWEEPS, id0=0):
     """The oracle as it stands, one process per syndrome on the host cores,
-    on `n_syn` syndromes of the workload at full length."""
+    on the syndromes `ids_per_p[i]` (batch indices) of p = PS[i], at full
+    length.  Returns the timing record and the oracle's decodes per p."""
+    import multiprocessing as mp
+
     import oracle as O
     cores = os.cpu_count() or 1
-    n_syn = n_syn or cores
-    syn, _ = O.gen_syndromes(seed, 0, n_syn, L, p)
+    jobs, where = [], []
+    for i, (p, s) in enumerate(zip(PS, SYN_SEEDS)):
+        for j in ids_per_p[i]:
+            syn, _ = O.gen_syndromes(s, id0 + j, 1, L, p)
+            jobs.append((p, s, id0 + j, syn[0]))
+            where.append((i, j))
+    burn = min(BURN_IN, sweeps)
+    stages = ANNEAL_STAGES if burn >= ANNEAL_STAGES else 0
+    work = [(L, p, K_CLASSES, R_CHAINS, sweeps, s + 100, ident, syn, burn, 1.0, stages, ANNEAL_BETA0, 0, 0, None)
+            for p, s, ident, syn in jobs]
+    procs = min(cores, len(work))
     t0 = time.perf_counter()
-    O.decode_batch(L, p, K_CLASSES, R_CHAINS, SWEEPS, seed + 100, range(n_syn), syn, processes=min(cores, n_syn),
-                   burn_in=BURN_IN, anneal_stages=ANNEAL_STAGES, anneal_beta0=ANNEAL_BETA0)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(O._decode_worker, work, chunksize=1)
     dt = time.perf_counter() - t0
-    return {"value": n_syn / dt, "unit": "syndromes/s", "cores": min(cores, n_syn), "kind": "oracle",
-            "sample": f"{n_syn} syndromes of the workload at p={p} (L={L}, {K_CLASSES}x{R_CHAINS} chains, "
-                      f"{SWEEPS} sweeps), one process per syndrome",
-            "updates_per_s": n_syn * UPDATES_PER_SYNDROME / dt, "seconds": dt}
+    n_syn = len(jobs)
+    out = {i: {} for i in range(len(PS))}
+    for (i, j), r in zip(where, res):
+        out[i][j] = r
+    rec = {"value": n_syn / dt, "unit": "syndromes/s", "cores": procs,
+           "kind": "oracle",
+           "sample": f"{n_syn} syndromes of the workload ({', '.join(str(len(x)) for x in ids_per_p)} at p = "
+                     f"{', '.join(str(p) for p in PS)}; L={L}, {K_CLASSES}x{R_CHAINS} chains, {sweeps} sweeps), "
+                     "one process per syndrome",
+           "updates_per_s": n_syn * UPDATES_PER_SYNDROME * sweeps / SWEEPS / dt, "seconds": dt}
+    return rec, out
+
+
+def compare_parity(orc, last, ids_per_p):
+    """Element-by-element comparison of the GPU's decisions and class sums
+    with the oracle's on the sampled syndromes of every p."""
+    checked, bad = 0, []
+    for i, p in enumerate(PS):
+        cls, sums = last[i][0].cpu().numpy(), last[i][1].cpu().numpy()
+        for j in ids_per_p[i]:
+            r = orc[i][j]
+            checked += 1
+            if int(cls[j]) != int(r["cls"]) or not (sums[j].astype("uint64") == r["class_sum"]).all():
+                bad.append({"p": p, "index": j})
+    return {"checked": checked, "mismatches": len(bad), "ps": PS, "indices": ids_per_p,
+            "compared": "decided class and the 4 class sums, bit for bit", "bad": bad[:8]}
 
 
 def run_reference(args):
@@ -155,11 +197,14 @@ def run_reference(args):
         return 0
     cores = os.cpu_count() or 1
     times = []
+    per_p = max(1, cores // len(PS))
     for step in range(args.warmup + args.steps):
-        p = PS[step % 4]
-        r = cpu_baseline(n_syn=cores, p=p, seed=SYN_SEEDS[step % 4])
+        # a different sample of the batch every step: ids step*per_p ..
+        ids = [list(range(step * per_p, (step + 1) * per_p)) for _ in PS]
+        r, _ = cpu_baseline(ids)
         if step >= args.warmup:
             times.append(r["seconds"])
+    cores = per_p * len(PS)
     total = sum(times)
     value = cores * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": 0,
@@ -184,20 +229,40 @@ def main():
     ap.add_argument("--sweeps", type=int, default=SWEEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
 
+    from paper_1302_2669_gb300 import shard
+    if "WORLD_SIZE" not in os.environ:
+        import torch
+        have = torch.cuda.device_count()
+        if have < args.gpus:
+            print(f"bench.py: --gpus {args.gpus} needs {args.gpus} GPUs, this machine has {have}", file=sys.stderr)
+            return 2
+        if args.gpus > 1:
+            # one process per GPU: this command again under torch.distributed.run
+            return shard.spawn_ranks(args.gpus, os.path.abspath(__file__), sys.argv[1:])
+
     import torch
     import paper_1302_2669_gb300 as pkg
     from paper_1302_2669_gb300 import build as b
-    from paper_1302_2669_gb300 import shard
 
     rank, world, local = dist_env()
+    if world != args.gpus:
+        print(f"bench.py: WORLD_SIZE={world} but --gpus {args.gpus}", file=sys.stderr)
+        return 2
     if world > 1:
         import torch.distributed as dist
+        # NCCL's initialisation log (communicator size and ranks) on stderr
+        os.environ.setdefault("NCCL_DEBUG", "INFO")
+        os.environ.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
+        os.environ.setdefault("NCCL_DEBUG_FILE", "/dev/stderr")
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        print(f"bench.py: rank {rank} of {dist.get_world_size()} on cuda:{local} ({dist.get_backend()})",
+              file=sys.stderr, flush=True)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     b.build()
@@ -225,8 +290,15 @@ def main():
                    out_class_sum=out_sum, out_log_ratio=out_lr)
         return i
 
+    # the decisions of the last decode of each p (copied after the step's
+    # end event, outside the timed region)
+    last = {}
+
+    def keep(i):
+        last[i] = (out_cls.clone(), out_sum.clone())
+
     for j in range(args.warmup):
-        step(j)
+        keep(step(j))
     torch.cuda.synchronize()
 
     fails = {p: [0, 0] for p in PS}
@@ -248,6 +320,7 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
         fails[PS[i]][0] += int((out_cls != tcls[i]).sum())
         fails[PS[i]][1] += n
+        keep(i)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -257,6 +330,16 @@ def main():
     total_ms = shard.max_value(sum(step_ms), device=dev)
     merged = shard.sum_counts([v for p in PS for v in fails[p]], device=dev)
     fails = {p: merged[2 * i:2 * i + 2] for i, p in enumerate(PS)}
+    for i in range(len(PS)):   # a p that no step reached (fewer than four steps)
+        if i not in last:
+            keep(step(i))
+    # all-gather of the per-syndrome decisions: the job's decisions in id
+    # order on every rank, and their failures recounted from them
+    gathered = {}
+    for i, p in enumerate(PS):
+        dec = shard.all_gather_rows(last[i][0], device=dev)
+        tru = shard.all_gather_rows(tcls[i], device=dev)
+        gathered[p] = {"syndromes": int(dec.numel()), "failures": int((dec != tru).sum())}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -314,8 +397,14 @@ def main():
         "clocks": clk,
         "e2e": e2e,
     }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+    line["decisions"] = {"gathered_over_ranks": world, "per_p": {f"{p:.2f}": v for p, v in gathered.items()}}
+    ids = [parity_ids(n) for _ in PS]
+    if (world == 1 and not args.no_cpu_baseline) or not args.no_parity:
+        rec, orc = cpu_baseline(ids, sweeps=sweeps, id0=id0)
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = rec
+        if not args.no_parity:
+            line["parity"] = compare_parity(orc, last, ids)
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0

@@ -398,7 +398,8 @@ int surfmcmc_sweep_time(surfmcmc_ctx* ctx, double* ms, int64_t* launches);
  *   Set-up: the first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.
- *   Errors: EINVAL for bad arguments, host pointers or an oversized batch,
+ *   Errors: EINVAL for bad arguments, host pointers, buffers of another
+ *   device or an oversized batch,
  *   ECUDA if a CUDA call fails. */
 #define SURFMCMC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 size_t surfmcmc_noalloc_scratch_needed(int64_t n, int32_t L, int32_t chains_per_class);

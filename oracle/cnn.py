@@ -206,3 +206,46 @@ def loss_and_grad(params, syn, L, targets, bf16=False):
         if i > 0:
             dz = dx * (acts[i] > 0)
     return loss, flatten(grads)
+
+
+def grad_magnitude(params, syn, L, targets, bf16=False):
+    """Per parameter, the sum of the absolute values of the terms whose sum
+    is its gradient (flat, like loss_and_grad): the backward pass of
+    loss_and_grad with every factor replaced by its absolute value.  A
+    gradient computed from the same terms with relative errors of at most u
+    in each stored factor differs from the exact one by at most about
+    (stored factors) x u x this magnitude; the GPU's float32 accumulation
+    adds only a few units of 2^-24 relative to it."""
+    layers = unflatten(params)
+    rnd = bf16_round if bf16 else (lambda v: v)
+    _, acts = forward(params, syn, L, bf16=bf16, keep=True)
+    c0 = pure_error_codes(syn, L)
+    n = len(c0)
+    a0, b0 = c0 & 1, c0 >> 1
+    ga = np.zeros((n, 2))
+    gb = np.zeros((n, 2))
+    for k in range(4):
+        ga[np.arange(n), (k & 1) ^ a0] -= targets[:, k] / n
+        gb[np.arange(n), (k >> 1) ^ b0] -= targets[:, k] / n
+    ta, tb, Ma, Mb = _readout(acts[-1], L)
+
+    def d_prod_abs(t, M, g):
+        inside = (M > -1 + CLIP) & (M < 1 - CLIP)
+        dM = np.where(inside, np.abs(g[:, 0] / (1 + M)) + np.abs(g[:, 1] / (1 - M)), 0.0)
+        others = np.empty_like(t)
+        for i in range(t.shape[1]):
+            others[:, i] = np.prod(np.abs(np.delete(t, i, axis=1)), axis=1)
+        return dM[:, None] * others * (1 - t * t) / 2.0
+
+    m = midline(L)
+    dz = np.zeros_like(acts[-1])
+    dz[:, :, m, 0] = d_prod_abs(ta, Ma, ga)
+    dz[:, m, :, 1] = d_prod_abs(tb, Mb, gb)
+    grads = [None] * 5
+    for i in range(4, -1, -1):
+        w, b = layers[i]
+        dx, dw, db = _conv_grad(np.abs(acts[i]), np.abs(rnd(w)), dz)
+        grads[i] = (dw, db)
+        if i > 0:
+            dz = dx * (acts[i] > 0)
+    return flatten(grads)

@@ -13,8 +13,14 @@
 
 #include "surfmcmc.h"
 #include "common.cuh"
+#include "plan.cuh"
 
 using namespace surfmcmc;
+
+// Launch shape of the sweep kernel chosen by surfmcmc_autotune.
+struct Tuned {
+    int lam = 0;             // lanes per bundle
+};
 
 struct surfmcmc_ctx {
     int device = 0;
@@ -23,7 +29,7 @@ struct surfmcmc_ctx {
     size_t arena_bytes = 0;
     std::string last_error;
     bool timing = false;
-    std::map<std::pair<int, int>, int> tuned;  // (L, chains per class) -> lanes per bundle
+    std::map<std::pair<int, int>, Tuned> tuned;  // (L, chains per class) -> launch shape
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // recorded around sweep launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
 };
@@ -135,135 +141,33 @@ int check_common(surfmcmc_ctx* ctx, int64_t n, int32_t L, uint32_t id0) {
     return SURFMCMC_OK;
 }
 
-// Energy of a qubit's Pauli, index x + 2z (I, X, Z, Y), of a noise model:
-// depolarizing {0, 1, 1, 1} (n = qubits in error, Sec. IV), independent
-// flips {0, 1, 1, 2} (Sec. IV.B), general channel {0, eX, eZ, eY}.
-void energy_table(const surfmcmc_opts& o, int E[4]) {
-    E[0] = 0;
-    if (o.noise == 2) {
-        E[1] = o.pauli_energy[0];
-        E[2] = o.pauli_energy[2];
-        E[3] = o.pauli_energy[1];
-    } else {
-        E[1] = 1;
-        E[2] = 1;
-        E[3] = o.noise ? 2 : 1;
-    }
-}
-
-double powi(double r, int e) {
-    double v = 1.0;
-    for (int i = 0; i < e; ++i) v *= r;
-    return v;
-}
-
-// r = e^{-beta_bar}: (p/3)/(1-p) (Eq. 2, depolarizing), p/(1-p)
-// (independent flips), or for the general channel the root r in (0, 1] of
-// (1 - p)(r^eX + r^eY + r^eZ) = p after 100 halvings of [0, 1] (the left end
-// moves when the value at the midpoint is below p).
-double noise_rate(double p, int noise, const int E[4]) {
-    if (noise == 0) return (p / 3.0) / (1.0 - p);
-    if (noise == 1) return p / (1.0 - p);
-    double lo = 0.0, hi = 1.0;
-    for (int it = 0; it < 100; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        const double f = (1.0 - p) * (powi(mid, E[1]) + powi(mid, E[3]) + powi(mid, E[2]));
-        if (f < p) lo = mid; else hi = mid;
-    }
-    return 0.5 * (lo + hi);
-}
-
-// r* = e^{-beta_scale beta_bar}; T[d] = floor(r*^d 2^32), d = 1..32, r*^d by
-// repeated multiplication.
-void acceptance_table(double r, double beta_scale, uint64_t T[33], double* beta_bar) {
-    const double rs = beta_scale == 1.0 ? r : exp(-beta_scale * -log(r));
-    double rd = rs;
-    T[0] = 0;
-    for (int d = 1; d <= 32; ++d) {
-        T[d] = (uint64_t)floor(rd * 4294967296.0);
-        rd = rd * rs;
-    }
-    *beta_bar = -log(r);
-}
-
-// Burn-in stage j of S runs at beta* (a0 + (1 - a0) j / S).
-double anneal_scale(double beta_scale, double a0, int j, int S) {
-    return beta_scale * (a0 + (1.0 - a0) * (double)j / (double)S);
-}
-
-// Acceptance thresholds of one launch as kernel parameters: flags, the
-// number of leading all-zero digit planes, and per plane k the algebraic
-// normal form of d-1 -> bit (31-k) of T[d].
-void set_temperature(SweepParams& sp, double p, double beta_scale) {
-    uint64_t T[33];
-    double beta_bar;
-    acceptance_table(noise_rate(p, sp.noise, sp.energy), beta_scale, T, &beta_bar);
-    for (int d = 0; d < 33; ++d) sp.T[d] = T[d];
-    sp.accept_all = T[1] >= 4294967296ull;
-    sp.reject_all = T[1] == 0;
-    sp.qmodes = 0;
-    for (int q = 0; q < 8 && !sp.accept_all; ++q) {
-        uint32_t any1 = 0, any234 = 0;
-        for (int k = 4 * q; k < 4 * q + 4; ++k) {
-            any1 |= (uint32_t)(T[1] >> (31 - k)) & 1u;
-            for (int d = 2; d <= 4; ++d) any234 |= (uint32_t)(T[d] >> (31 - k)) & 1u;
-        }
-        sp.qmodes |= (any234 ? 2u : any1 ? 1u : 0u) << (2 * q);
-    }
-    for (int k = 0; k < 32; ++k) {
-        uint32_t t[5] = {0, 0, 0, 0, 0};
-        if (!sp.accept_all)
-            for (int d = 1; d <= 4; ++d) t[d] = (uint32_t)((T[d] >> (31 - k)) & 1u);
-        sp.pc[0][k] = t[1] ? ~0u : 0u;
-        sp.pc[1][k] = (t[1] ^ t[2]) ? ~0u : 0u;
-        sp.pc[2][k] = (t[1] ^ t[3]) ? ~0u : 0u;
-        sp.pc[3][k] = (t[1] ^ t[2] ^ t[3] ^ t[4]) ? ~0u : 0u;
-    }
-}
-
+// Lanes per bundle of a run: the caller's choice, else the autotuned value
+// for (L, chains per class), else the rule of heuristic_lanes.
 int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nullptr, int R = 0, int code = 0) {
     const int nq = geo_nq(code, L), nc = geo_nc(code, L);
-    auto smem_ok = [&](int lam) { return sweep_smem_bytes(nq, nc, lam) <= 200 * 1024; };
     if (requested) {
         if (requested != 2 && requested != 4 && requested != 8 && requested != 16 && requested != 32)
             return SURFMCMC_EINVAL;
-        if (!smem_ok(requested)) return SURFMCMC_EINVAL;
+        if (sweep_smem_bytes(nq, nc, requested) > kSweepSmemLimit) return SURFMCMC_EINVAL;
         *lam_out = requested;
         return SURFMCMC_OK;
     }
     if (ctx) {
         auto it = ctx->tuned.find({L, R});
         if (it != ctx->tuned.end()) {
-            *lam_out = it->second;
+            *lam_out = it->second.lam;
             return SURFMCMC_OK;
         }
     }
-    // heuristic: the most lanes that the colour's generators fill to >= 90%
-    int best = 32;
-    double best_eff = -1;
-    for (int lam = 32; lam >= 2; lam /= 2) {
-        if (!smem_ok(lam)) continue;
-        const double eff = (double)nc / (double)(lam * ((nc + lam - 1) / lam));
-        if (eff >= 0.9) { best = lam; break; }
-        if (eff > best_eff + 1e-12) { best_eff = eff; best = lam; }
-    }
-    *lam_out = best;
+    *lam_out = heuristic_lanes(L, code);
     return SURFMCMC_OK;
 }
 
-// Small batches: a persistent block takes work units of 4 warps x 32/lam
-// bundles, so a batch of few bundles leaves most blocks idle and the run
-// time is the latency of one unit.  Unless the caller fixed the lanes, widen
-// (more lanes share a bundle's generators, shorter units) until the units
-// fill the resident blocks once.  The results do not depend on the lanes.
+// Widens the lanes of a small batch (widen_lanes_for) unless the caller
+// fixed them.
 int widen_lanes(const surfmcmc_ctx* ctx, int L, int requested, int lam, long long n_bundles, int G, int code = 0) {
-    if (requested || !ctx || ctx->sms <= 0) return lam;
-    const int nq = geo_nq(code, L), nc = geo_nc(code, L);
-    const long long capacity = (long long)ctx->sms * sweep_blocks_per_sm(G);
-    while (lam < 32 && sweep_units(n_bundles, lam) < capacity &&
-           sweep_smem_bytes(nq, nc, 2 * lam) <= 200 * 1024)
-        lam *= 2;
-    return lam;
+    if (requested || !ctx) return lam;
+    return widen_lanes_for(ctx->sms, L, lam, n_bundles, G, code);
 }
 
 int check_opts(surfmcmc_ctx* ctx, const surfmcmc_opts& o, double p) {
@@ -311,47 +215,6 @@ int check_toric(surfmcmc_ctx* ctx, const surfmcmc_opts& o, int L) {
 int reject_toric(surfmcmc_ctx* ctx, const surfmcmc_opts& o, const char* what) {
     if (o.n_classes == 16) return fail(ctx, SURFMCMC_EINVAL, "%s supports the planar code (4 classes) only", what);
     return SURFMCMC_OK;
-}
-
-// Chain layout of a run: C chains per syndrome, plane width G, bundles of 32
-// chains (G = 32: C/32 bundles per syndrome; G < 32: 32/G syndromes per
-// bundle).
-void init_chains(SweepParams& sp, int Cn, int R, uint32_t id0) {
-    memset(&sp, 0, sizeof sp);
-    int G = 1;
-    while (G < Cn && G < 32) G *= 2;
-    sp.C = Cn;
-    sp.R = R;
-    sp.G = G;
-    sp.bps = G == 32 ? (Cn + 31) / 32 : 1;
-    sp.spb = G == 32 ? 1 : 32 / G;
-    sp.id0 = id0;
-    sp.ids = nullptr;
-}
-
-long long bundles_of(const SweepParams& sp, long long n) {
-    return sp.G == 32 ? n * sp.bps : (n + sp.spb - 1) / sp.spb;
-}
-
-// Appends a group of n syndromes of size L (items item_base ..) whose
-// per-item rows start at the given word offsets.
-void add_group(SweepParams& sp, int L, long long n, long long item_base, long long e0_off, long long frames_off,
-               long long state_off, int lam) {
-    GroupDesc& g = sp.grp[sp.n_groups++];
-    g.L = L;
-    g.nq = geo_nq(sp.code, L);
-    g.W = geo_words(sp.code, L);
-    g.nc = geo_nc(sp.code, L);
-    g.n = n;
-    g.n_bundles = bundles_of(sp, n);
-    g.item_base = item_base;
-    g.e0_off = e0_off;
-    g.frames_off = frames_off;
-    g.state_off = state_off;
-    g.unit_base = sp.total_units;
-    sp.total_units += sweep_units(g.n_bundles, lam);
-    if (g.nq > sp.grp_nq_max) sp.grp_nq_max = g.nq;
-    if (g.nc > sp.grp_nc_max) sp.grp_nc_max = g.nc;
 }
 
 // Launch segments of one run: the S annealing stages of the burn-in (no
@@ -1298,7 +1161,7 @@ int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, do
     cudaEventDestroy(e_b);
     cudaStreamDestroy(s);
     if (!best) return fail(ctx, SURFMCMC_EINVAL, "no lanes_per_bundle fits L=%d", L);
-    ctx->tuned[{L, R}] = best;
+    ctx->tuned[{L, R}].lam = best;
     if (best_out) *best_out = best;
     return SURFMCMC_OK;
 }

@@ -54,6 +54,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -1518,16 +1519,24 @@ cudaError_t net_alloc(CnnNet* net, void** p, size_t bytes) {
     return e;
 }
 
+// Shared-memory limits of the network kernels, set once per device (the
+// attribute belongs to the current device's context), under a lock.
 cudaError_t prepare_kernels() {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e;
+    constexpr int kMaxDevices = 64;
+    static std::mutex m;
+    static bool done[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(m);
+    if (done[dev]) return cudaSuccess;
     if ((e = set_smem(conv1_kernel, kC1Smem))) return e;
     if ((e = set_smem(conv_tma_kernel<64, kEpiRelu>, conv_tma_smem_bytes<64, kEpiRelu>()))) return e;
     if ((e = set_smem(conv_tma_kernel<64, kEpiMask>, conv_tma_smem_bytes<64, kEpiMask>()))) return e;
     if ((e = set_smem(wgrad_kernel, kWgSmem))) return e;
     if ((e = set_smem(wgrad0_kernel, kW0Smem))) return e;
-    done = true;
+    done[dev] = true;
     return cudaSuccess;
 }
 

@@ -23,6 +23,8 @@
 // and a chain is decided at its first digit that differs from T[d]'s.  The
 // warp stops drawing planes once every chain of its proposals is decided.
 #pragma once
+#include <mutex>
+
 #include "common.cuh"
 
 namespace surfmcmc {
@@ -773,24 +775,41 @@ __global__ void __launch_bounds__(128, sweep_blocks_per_sm(G)) sweep_kernel(cons
 
 constexpr int kWarps = 4;
 
+// The dynamic shared-memory limit of one kernel instantiation, raised on
+// demand.  The attribute belongs to the current device's context, so the
+// limit already set is kept per device, under a lock (contexts on several
+// host threads may launch at once).
+struct SmemLimit {
+    static constexpr int kMaxDevices = 64;
+    std::mutex m;
+    size_t bytes[kMaxDevices] = {};
+
+    template <typename Kernel>
+    cudaError_t ensure(Kernel* k, int dev, size_t smem) {
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lock(m);
+        if (smem <= bytes[dev]) return cudaSuccess;
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) bytes[dev] = smem;
+        return e;
+    }
+};
+
 template <int G, int LAM, bool SCAN, bool IND, bool ACPT = false>
 static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
     const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM) +
                         (ACPT ? (size_t)kWarps * kAcptWordsPerWarp * 4 : 0);
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<G, LAM, SCAN, IND, ACPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    static SmemLimit limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = limit.ensure(sweep_kernel<G, LAM, SCAN, IND, ACPT>, dev, smem);
+    if (e != cudaSuccess) return e;
     if (p.total_units == 0) return cudaSuccess;
     long long blocks = p.total_units;
     if (p.unit_counter) {
         // persistent: as many blocks as fit on the device at once
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM, SCAN, IND, ACPT>, 32 * kWarps,
                                                               smem);

@@ -6,8 +6,11 @@ library's continuous-batching server.
 Requests: L uniform over {9, 13, 17, 25}, depolarizing p = 0.12, sweeps = L^2
 (the first quarter annealed from 0.3 beta_bar in 4 stages, not sampled),
 4 classes x 4 chains.  Syndromes are seeded synthetic inputs made by the
-library's generator before the run.  Prints one JSON line with the offered
-and achieved rates, p50/p99/max latency, batches and memory stalls.
+library's generator before the run.  The same arrivals are served twice:
+without a memory budget and with --memory-budget bytes (default 2 MiB,
+about two batches' scratch at this rate), so that admission has to wait
+for memory.  Prints one JSON line with, per run, the offered and achieved
+rates, p50/p99/max latency, batches and memory stalls.
 """
 from __future__ import annotations
 
@@ -28,7 +31,8 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--max-batch", type=int, default=1024)
     ap.add_argument("--max-wait-us", type=float, default=500.0)
-    ap.add_argument("--memory-budget", type=int, default=0)
+    ap.add_argument("--memory-budget", type=int, default=2 * 1024 * 1024,
+                    help="budget of the second run (0: run only without a budget)")
     ap.add_argument("--seed", type=int, default=5001)
     args = ap.parse_args(argv)
 
@@ -49,47 +53,53 @@ def main(argv=None):
         rows[L] = syn.cpu().numpy()
     ctx.close()
     opts = pkg.Opts(chains_per_class=4, n_sweeps=100, burn_in=25, anneal_stages=4, anneal_beta0=0.3)
-    srv = pkg.Server(0, args.p, opts, seed=args.seed + 100, max_batch=args.max_batch, slots=args.slots,
-                     max_L=max(sizes), memory_budget=args.memory_budget, max_wait_us=args.max_wait_us)
-    lat = []
-    done = threading.Event()
 
-    def collect():
-        got = 0
-        while got < n_req:
-            ids, cls, sums, l = srv.poll(max_results=8192, wait_us=20000)
-            lat.extend(l.tolist())
-            got += len(ids)
-        done.set()
+    def serve(budget):
+        srv = pkg.Server(0, args.p, opts, seed=args.seed + 100, max_batch=args.max_batch, slots=args.slots,
+                         max_L=max(sizes), memory_budget=budget, max_wait_us=args.max_wait_us)
+        lat = []
+        done = threading.Event()
 
-    th = threading.Thread(target=collect)
-    th.start()
-    t0 = time.perf_counter()
-    t_next = t0
-    for i in range(n_req):
-        t_next += gaps[i]
-        while True:
-            now = time.perf_counter()
-            if now >= t_next:
-                break
-            if t_next - now > 2e-4:
-                time.sleep(t_next - now - 1e-4)
-        L = int(Ls[i])
-        srv.submit(i, L, L * L, rows[L][i])
-    t_sub = time.perf_counter() - t0
-    done.wait()
-    t_all = time.perf_counter() - t0
-    th.join()
-    st = srv.stats()
-    srv.close()
-    lat_ms = np.array(lat) / 1000.0
-    line = {"metric": "serving latency and throughput", "offered_rps": args.rate,
-            "submitted_rps": n_req / t_sub, "completed_rps": n_req / t_all, "requests": n_req,
-            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "max_ms": float(lat_ms.max()), "batches": st["batches"], "memory_stalls": st["memory_stalls"],
+        def collect():
+            got = 0
+            while got < n_req:
+                ids, cls, sums, l = srv.poll(max_results=8192, wait_us=20000)
+                lat.extend(l.tolist())
+                got += len(ids)
+            done.set()
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(n_req):
+            t_next += gaps[i]
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                if t_next - now > 2e-4:
+                    time.sleep(t_next - now - 1e-4)
+            L = int(Ls[i])
+            srv.submit(i, L, L * L, rows[L][i])
+        t_sub = time.perf_counter() - t0
+        done.wait()
+        t_all = time.perf_counter() - t0
+        th.join()
+        st = srv.stats()
+        srv.close()
+        lat_ms = np.array(lat) / 1000.0
+        return {"memory_budget": budget, "submitted_rps": n_req / t_sub, "completed_rps": n_req / t_all,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "max_ms": float(lat_ms.max()), "batches": st["batches"], "memory_stalls": st["memory_stalls"]}
+
+    runs = [serve(0)] + ([serve(args.memory_budget)] if args.memory_budget > 0 else [])
+    line = {"metric": "serving latency and throughput", "offered_rps": args.rate, "requests": n_req,
+            **{k: v for k, v in runs[0].items() if k != "memory_budget"},
+            "runs": runs,
             "config": {"sizes": sizes, "p": args.p, "sweeps": "L^2 (first quarter annealed, 4 stages from 0.3)",
                        "chains": "4 classes x 4", "slots": args.slots, "max_batch": args.max_batch,
-                       "max_wait_us": args.max_wait_us, "memory_budget": args.memory_budget},
+                       "max_wait_us": args.max_wait_us},
             "updates_per_request_mean": float(np.mean([16 * L * L * 2 * L * (L - 1) for L in Ls]))}
     print(json.dumps(line), flush=True)
     return 0

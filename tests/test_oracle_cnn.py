@@ -74,6 +74,38 @@ def test_gradient_matches_finite_differences():
         assert abs(num - g[i]) < 1e-6 + 1e-4 * abs(num), (i, num, g[i])
 
 
+def test_gradient_magnitude_bounds_the_gradient():
+    """grad_magnitude (the sum of |terms| of every gradient element) is at
+    least |gradient| everywhere (triangle inequality), scales with the
+    targets, and equals |gradient| where no terms cancel: with every flip
+    logit of the last layer negative (its -4 start bias), every term of the
+    last layer's bias gradient of channel 0 has one sign."""
+    L = 5
+    rng = np.random.default_rng(11)
+    syn, _ = O.gen_syndromes(17, 0, 4, L, 0.12)
+    t = rng.dirichlet(np.ones(4), size=4)
+    p = cnn.init_params(4)
+    _, g = cnn.loss_and_grad(p, syn, L, t, bf16=True)
+    A = cnn.grad_magnitude(p, syn, L, t, bf16=True)
+    assert (np.abs(g) <= A * (1 + 1e-12) + 1e-300).all()
+    assert np.allclose(cnn.grad_magnitude(p, syn, L, 2 * t, bf16=True), 2 * A, rtol=1e-12, atol=0)
+    _, acts = cnn.forward(p, syn, L, bf16=True, keep=True)
+    m = cnn.midline(L)
+    assert (acts[-1][:, :, m, 0] < 0).all()
+    t1 = np.eye(4)[[0, 1, 2, 3]]
+    _, g1 = cnn.loss_and_grad(p, syn, L, t1, bf16=True)
+    A1 = cnn.grad_magnitude(p, syn, L, t1, bf16=True)
+    # all four one-hot targets: per syndrome the parity term of channel 0 has
+    # one sign across the middle column's positions; the bias of output
+    # channel 0 is the last-but-one parameter
+    one = np.eye(4)[[0]]
+    for i in range(4):
+        _, gi = cnn.loss_and_grad(p, syn[i:i + 1], L, one, bf16=True)
+        Ai = cnn.grad_magnitude(p, syn[i:i + 1], L, one, bf16=True)
+        assert abs(abs(gi[-2]) - Ai[-2]) <= 1e-12 * Ai[-2], (i, gi[-2], Ai[-2])
+    assert (np.abs(g1) <= A1 * (1 + 1e-12)).all()
+
+
 def test_logprob_normalised():
     L = 5
     syn, _ = O.gen_syndromes(8, 0, 6, L, 0.15)

@@ -1,8 +1,11 @@
 """Sharding of syndromes over two CPU ranks (gloo): the merged failure counts
 of the sharded run equal those of one process decoding every syndrome.  Each
 rank decodes its share with the oracle, keyed by global syndrome id."""
+import json
 import os
 import socket
+import subprocess
+import sys
 
 import pytest
 
@@ -66,3 +69,41 @@ def test_two_rank_gloo_matches_single_process(tmp_path):
     ref = sum(int(O.decode_one(L, P, K, R, SWEEPS, DEC_SEED, i, syn[i], burn_in=BURN, anneal_stages=4,
                                anneal_beta0=0.3)["cls"] != tc[i]) for i in range(N))
     assert int(cnt) == N and int(fails) == ref and float(tmax) == 2.0
+
+
+def test_spawned_ranks_gather_the_decisions_of_one_process(tmp_path):
+    """The rank-spawning path of bench.py (shard.spawn_ranks: two ranks under
+    torch.distributed.run, gloo on CPU): the all-gathered decisions equal one
+    process's decisions for the same ids, and the summed failures match."""
+    pytest.importorskip("torch")
+    import numpy as np
+
+    import oracle as O
+    here = os.path.dirname(os.path.abspath(__file__))
+    sys.path.insert(0, here)
+    import gloo_rank_worker as W
+    out = tmp_path / "gathered.json"
+    env = dict(os.environ, PYTHONPATH=os.path.dirname(here), OMP_NUM_THREADS="1")
+    rc = shard.spawn_ranks(2, os.path.join(here, "gloo_rank_worker.py"), [str(out)], env=env)
+    assert rc == 0
+    got = json.loads(out.read_text())
+    n = 2 * W.N_PER_RANK
+    syn, tc = O.gen_syndromes(W.SYN_SEED, 0, n, W.L, W.P)
+    ref = [O.decode_one(W.L, W.P, W.K, W.R, W.SWEEPS, W.DEC_SEED, i, syn[i], burn_in=W.BURN, anneal_stages=4,
+                        anneal_beta0=0.3)["cls"] for i in range(n)]
+    assert got["world"] == 2 and got["syndromes"] == n
+    assert got["decisions"] == ref
+    assert got["failures"] == int((np.array(ref) != tc).sum())
+
+
+def test_bench_refuses_more_gpus_than_present():
+    """bench.py --gpus N on a machine with fewer than N GPUs exits with a
+    clear error instead of printing a one-rank line."""
+    torch = pytest.importorskip("torch")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    n = torch.cuda.device_count() + 1
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", str(n), "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 2
+    assert f"--gpus {n} needs {n} GPUs" in r.stderr
+    assert not r.stdout.strip()
