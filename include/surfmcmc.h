@@ -468,6 +468,18 @@ int surfmcmc_cnn_train_step(surfmcmc_cnn* net, const uint8_t* syndromes, const f
                             float lr, float* out_loss, void* stream);
 int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream);
 
+/* Bound on every pipeline wait of the network kernels, in polls of the
+ * mbarrier (0 restores the default, 2^22).  A wait that reaches the bound
+ * gives up: the block stops its other roles, waits out the copies and
+ * tensor-core operations it has in flight, frees its tensor memory and
+ * exits; the device error flag then makes the call (or the next
+ * surfmcmc_cnn_status) return ECUDA with "a pipeline wait timed out" in
+ * surfmcmc_last_error, and clears the flag.  Outputs of such a call are
+ * undefined.  Small bounds exist to exercise that path; the default is far
+ * above the duration of any wait of a working pipeline.  EINVAL for a NULL
+ * net. */
+int surfmcmc_cnn_set_wait_limit(surfmcmc_cnn* net, uint32_t polls);
+
 /* Decoding with early stop (the paper has no counterpart).  The same chains
  * as surfmcmc_decode with opts (same seed, ids id0 + i, same sweeps), run in
  * chunks: checkpoints at burn_in + k chunk_sweeps (k = 1, 2, ...) below

@@ -74,7 +74,8 @@ EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surf
            "surfmcmc_server_create", "surfmcmc_server_submit", "surfmcmc_server_poll", "surfmcmc_server_stats",
            "surfmcmc_server_destroy", "surfmcmc_cnn_n_params", "surfmcmc_cnn_create", "surfmcmc_cnn_destroy",
            "surfmcmc_cnn_set_params", "surfmcmc_cnn_get_params", "surfmcmc_cnn_forward", "surfmcmc_cnn_gradient",
-           "surfmcmc_cnn_train_step", "surfmcmc_cnn_status", "surfmcmc_cnn_soft_targets", "surfmcmc_decode_early")
+           "surfmcmc_cnn_train_step", "surfmcmc_cnn_status", "surfmcmc_cnn_set_wait_limit", "surfmcmc_cnn_soft_targets",
+           "surfmcmc_decode_early")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -134,6 +135,7 @@ def lib():
         L.surfmcmc_cnn_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         L.surfmcmc_cnn_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
         L.surfmcmc_cnn_status.argtypes = [vp, vp]
+        L.surfmcmc_cnn_set_wait_limit.argtypes = [vp, u32]
         L.surfmcmc_cnn_soft_targets.argtypes = [vp, i64, vp, vp]
         L.surfmcmc_decode_early.argtypes = [vp, vp, vp, i64, i32, dbl, C.POINTER(_Opts), u32, C.c_float, i32, u64, u32,
                                             vp, vp, vp, vp]
@@ -502,6 +504,11 @@ class Network:
 
     def status(self, stream=None):
         self._ctx._check(lib().surfmcmc_cnn_status(self._h, stream))
+
+    def set_wait_limit(self, polls: int = 0):
+        """surfmcmc_cnn_set_wait_limit: bound on each pipeline wait of the
+        network kernels in polls (0: the default)."""
+        self._ctx._check(lib().surfmcmc_cnn_set_wait_limit(self._h, int(polls)))
 
     @staticmethod
     def soft_targets(log_ratio, out=None, stream=None):

@@ -147,13 +147,27 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
+// Non-blocking test of the same (mbarrier.test_wait never suspends the thread).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Bounded wait for the completion of the phase of the given parity.  Gives up
-// when another role of the block has given up, or after kSpinLimit polls (then
-// records the time-out in the device error flag and raises the block's abort
-// flag so that every other wait of the block returns too).
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
-        if (mbar_try(bar, parity)) return true;
+// when another role of the block has given up, or after `limit` polls (the
+// kernel's spin_limit, kSpinLimit unless set smaller to exercise this path;
+// then it records the time-out in the device error flag and raises the
+// block's abort flag so that every other wait of the block returns too).
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err, uint32_t limit) {
+    // the first poll does not suspend, so that a bound of one poll gives up
+    // whenever the phase is not complete yet
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (it == 0 ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;
         if ((it & 31) == 31 && *abort_flag) return false;
     }
     *abort_flag = 1;
@@ -336,6 +350,7 @@ struct Conv1Args {
     long long M;          // positions n P^2
     int L;
     int* err;
+    uint32_t spin_limit;   // polls before a pipeline wait gives up
 };
 
 constexpr int kC1KP = 32;                       // K of the first layer: 9 taps x 2 channels, padded
@@ -421,7 +436,7 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
             uint32_t q = 0;
             for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++q) {
                 const uint32_t stage = q % S, use = q / S;
-                if (use > 0 && !mbar_wait(&sfree[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                if (use > 0 && !mbar_wait(&sfree[stage], (use - 1) & 1, &abort_flag, a.err, a.spin_limit)) break;
                 mbar_expect_tx(&full[stage], bytes);
                 tma_load_2d(sStrip + stage * kC1StripStage, &a.in_map, 0, (int)floor_div4(tile * 128 - P1),
                             &full[stage]);
@@ -435,8 +450,8 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
             for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
                 const uint32_t b = it % NACC, u = it / NACC;
                 const uint32_t stage = it % S, use = it / S;
-                if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
-                if (!mbar_wait(&afull[stage], use & 1, &abort_flag, a.err)) break;
+                if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err, a.spin_limit)) break;
+                if (!mbar_wait(&afull[stage], use & 1, &abort_flag, a.err, a.spin_limit)) break;
                 tc_fence_after();
 #pragma unroll
                 for (int ks = 0; ks < kC1KP / 16; ++ks) {
@@ -460,7 +475,7 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
         uint32_t q = 0;
         for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++q) {
             const uint32_t stage = q % S, use = q / S;
-            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) break;
+            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err, a.spin_limit)) break;
             const long long s0 = tile * 128 - P1;
             const int base = r + P1 + (int)(s0 - 4 * floor_div4(s0));   // strip index of position tile*128 + r
             const uint32_t* strip = reinterpret_cast<const uint32_t*>(sStrip + stage * kC1StripStage);
@@ -471,7 +486,7 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
             for (int t = 0; t < 9; ++t) w[t] = keep ? strip[base + sh[t]] : 0u;
             const uint32_t one2 = keep ? 0x3F803F80u : 0u;   // bf16 1.0 at k = 18, 19 (and k = 20)
             mbar_arrive(&sfree[stage]);
-            if (use > 0 && !mbar_wait(&aempty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+            if (use > 0 && !mbar_wait(&aempty[stage], (use - 1) & 1, &abort_flag, a.err, a.spin_limit)) break;
             uint8_t* st = sA + stage * kC1Stage;
             *reinterpret_cast<uint4*>(st + core_off(r, 0, KGS)) = make_uint4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<uint4*>(st + core_off(r, 1, KGS)) = make_uint4(w[4], w[5], w[6], w[7]);
@@ -492,7 +507,7 @@ __global__ void __launch_bounds__(kC1Threads, 1) conv1_kernel(const __grid_const
             const uint32_t b = it % NACC, u = it / NACC;
             uint8_t* out = sOut + (2 * grp + (k & 1)) * kOutTile;
             if (elected) bulk_wait_read<1>();   // the group's store of two tiles back has left this buffer
-            const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err);
+            const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err, a.spin_limit);
             if (!epi_all(ok, bar_id)) break;
             tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + b * NP;
@@ -539,6 +554,7 @@ struct ConvTmaArgs {
     int L;
     int halo_rows;       // rows of one halo tile, halo_tile_rows(L)
     int* err;
+    uint32_t spin_limit;   // polls before a pipeline wait gives up
 };
 
 // Rows of the halo tile of 128 output positions: the taps shift by up to
@@ -629,7 +645,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             uint32_t q = 0;
             for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++q) {
                 const uint32_t stage = q % S, use = q / S;
-                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err, a.spin_limit)) break;
                 mbar_expect_tx(&full[stage], bytes);
                 tma_load_2d(sA + stage * kTmaStage, &a.map, 0, (int)(tile * 128 - P1), &full[stage]);
             }
@@ -654,8 +670,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
                  tile += 2LL * gridDim.x, it += 2) {
                 const uint32_t b = it % NACC, u = it / NACC;
                 const uint32_t stage = it % S, use = it / S;
-                if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err)) break;
-                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) break;
+                if (u > 0 && !mbar_wait(&acce[b], (u - 1) & 1, &abort_flag, a.err, a.spin_limit)) break;
+                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err, a.spin_limit)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + b * NP;
                 const uint32_t a_st = a_lo0 + stage * (kTmaStage / 16);
@@ -697,7 +713,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             const uint32_t b = it % NACC, u = it / NACC, ob = it % NOB;
             uint8_t* out = sOut + ob * kOutTile;
             if (EPI == kEpiRelu && elected) bulk_wait_read<1>();   // the store of two tiles back has left this buffer
-            const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err);
+            const bool ok = mbar_wait(&accf[b], u & 1, &abort_flag, a.err, a.spin_limit);
             if (!epi_all(ok)) break;
             tc_fence_after();
             const long long m = tile * 128 + row;
@@ -710,7 +726,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             mbar_arrive(&acce[b]);
             uint8_t* orow = out + row * 128;
             const int sw = row & 7;
-            if (EPI == kEpiMask && mbar_wait(&maskf[ob], (it / NOB) & 1, &abort_flag, a.err) && elected) ++gated;
+            if (EPI == kEpiMask && mbar_wait(&maskf[ob], (it / NOB) & 1, &abort_flag, a.err, a.spin_limit) && elected) ++gated;
 #pragma unroll
             for (int j = 0; j < NP / 8; ++j) {
                 uint4* chunk = reinterpret_cast<uint4*>(orow + ((j ^ sw) << 4));
@@ -783,6 +799,7 @@ struct WgradArgs {
     int L;
     int halo_rows;
     int* err;
+    uint32_t spin_limit;   // polls before a pipeline wait gives up
 };
 
 constexpr int kWgS = 4;                          // pipeline depth
@@ -842,7 +859,7 @@ __global__ void __launch_bounds__(kWgTmaThreads, 1) wgrad_kernel(const __grid_co
             uint32_t q = 0;
             for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
                 const uint32_t stage = q % kWgS, use = q / kWgS;
-                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err, a.spin_limit)) break;
                 uint8_t* st = smem + stage * kWgStage;
                 mbar_expect_tx(&full[stage], bytes);
                 tma_load_2d(st, &a.xmap, 0, (int)(ch * 64 - P1), &full[stage]);
@@ -868,13 +885,9 @@ __global__ void __launch_bounds__(kWgTmaThreads, 1) wgrad_kernel(const __grid_co
             }
             a_off[4] = (uint32_t)((P1 + tap_shift(8, L)) * 8);
             uint32_t q = 0;
-            bool ok = true;
             for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
                 const uint32_t stage = q % kWgS, use = q / kWgS;
-                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err, a.spin_limit)) break;
                 tc_fence_after();
                 const uint32_t st = lo0 + stage * (kWgStage / 16);
                 // pair 4: the ones atom lies ones - window bytes after tap 8's window
@@ -891,16 +904,18 @@ __global__ void __launch_bounds__(kWgTmaThreads, 1) wgrad_kernel(const __grid_co
                 }
                 mma_commit(&empty[stage]);
             }
-            // completes after every MMA of the block (also on the abort path)
+            // completes after every MMA of the block (also on the abort path);
+            // waited out here, so that no MMA outlives the tensor memory even
+            // when the accumulator warps gave up first
             mma_commit(&accf);
-            if (!ok || c_end == c_begin) mbar_drain(&accf, 0, a.err);
+            mbar_drain(&accf, 0, a.err);
         }
     } else {
         const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
         float* out = a.partial + ((long long)blockIdx.x * kWgRows + row) * 64;
         bool ok = c_end > c_begin;
-        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err));
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err, a.spin_limit));
         if (ok) tc_fence_after();
 #pragma unroll 1
         for (int j = 0; j < kWgPairs; ++j) {
@@ -950,6 +965,7 @@ struct Wgrad0Args {
     long long M;
     int L;
     int* err;
+    uint32_t spin_limit;   // polls before a pipeline wait gives up
 };
 
 constexpr int kW0S = 4;                              // pipeline depth
@@ -1001,7 +1017,7 @@ __global__ void __launch_bounds__(kW0Threads, 1) wgrad0_kernel(const __grid_cons
             uint32_t q = 0;
             for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
                 const uint32_t stage = q % kW0S, use = q / kW0S;
-                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err)) break;
+                if (use > 0 && !mbar_wait(&empty[stage], (use - 1) & 1, &abort_flag, a.err, a.spin_limit)) break;
                 mbar_expect_tx(&full[stage], bytes);
                 tma_load_2d(sStrip + stage * kC1StripStage, &a.in_map, 0, (int)floor_div4(ch * 128 - P1),
                             &full[stage]);
@@ -1020,13 +1036,9 @@ __global__ void __launch_bounds__(kW0Threads, 1) wgrad0_kernel(const __grid_cons
             const uint32_t lo0 = (uint32_t)d0 & 0xFFFFu;
             const uint32_t lbo = (uint32_t)(kW0Tile >> 4) << 16;
             uint32_t q = 0;
-            bool ok = true;
             for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
                 const uint32_t stage = q % kW0S, use = q / kW0S;
-                if (!mbar_wait(&afull[stage], use & 1, &abort_flag, a.err)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(&afull[stage], use & 1, &abort_flag, a.err, a.spin_limit)) break;
                 tc_fence_after();
                 const uint32_t a_lo = (lo0 + stage * (kW0Stage / 16)) | lbo;
                 const uint32_t b_lo = (lo0 + stage * (kW0Stage / 16) + kW0Tile / 16) | lbo;
@@ -1036,9 +1048,11 @@ __global__ void __launch_bounds__(kW0Threads, 1) wgrad0_kernel(const __grid_cons
                                 (ch > c_begin || ks > 0) ? 1u : 0u);
                 mma_commit(&empty[stage]);
             }
-            // completes after every MMA of the block (also on the abort path)
+            // completes after every MMA of the block (also on the abort path);
+            // waited out here, so that no MMA outlives the tensor memory even
+            // when the accumulator warps gave up first
             mma_commit(&accf);
-            if (!ok || c_end == c_begin) mbar_drain(&accf, 0, a.err);
+            mbar_drain(&accf, 0, a.err);
         }
     } else {
         // operand rows: thread r writes row r (position ch * 128 + r) of every chunk
@@ -1049,7 +1063,7 @@ __global__ void __launch_bounds__(kW0Threads, 1) wgrad0_kernel(const __grid_cons
         uint32_t q = 0;
         for (long long ch = c_begin; ch < c_end; ++ch, ++q) {
             const uint32_t stage = q % kW0S, use = q / kW0S;
-            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err)) break;
+            if (!mbar_wait(&full[stage], use & 1, &abort_flag, a.err, a.spin_limit)) break;
             const long long s0 = ch * 128 - P1;
             const int base = r + P1 + (int)(s0 - 4 * floor_div4(s0));   // strip index of position ch*128 + r
             const uint32_t* strip = reinterpret_cast<const uint32_t*>(sStrip + stage * kC1StripStage);
@@ -1066,7 +1080,7 @@ __global__ void __launch_bounds__(kW0Threads, 1) wgrad0_kernel(const __grid_cons
         if (warp == 4) {
             // tensor-memory lanes 0..31 (this warp's quarter): rows R = 0..18
             bool ok = c_end > c_begin;
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err));
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&accf, 0, &abort_flag, a.err, a.spin_limit));
             float v[64];
             if (ok) {
                 tc_fence_after();
@@ -1500,6 +1514,7 @@ struct CnnNet {
     float *logprob = nullptr, *dz5 = nullptr, *loss_item = nullptr, *loss = nullptr, *S5 = nullptr, *Sb5 = nullptr;
     float* partial = nullptr;
     int* err = nullptr;
+    uint32_t spin_limit = kSpinLimit;   // polls of a pipeline wait (smaller only to test the time-out path)
     // TMA map of the first layer's input x0 (16-byte rows of 4 positions)
     CUtensorMap map_x0;
     // TMA maps of the 64-channel tensors that convs read: act[0..3], dz[0..1]
@@ -1603,6 +1618,7 @@ cudaError_t launch_wgrad0(const CnnNet* net, int dzi, long long M, cudaStream_t 
     a.M = M;
     a.L = net->L;
     a.err = net->err;
+    a.spin_limit = net->spin_limit;
     wgrad0_kernel<<<slices, kW0Threads, kW0Smem, s>>>(a);
     if ((e = cudaGetLastError())) return e;
     wgrad_reduce_kernel<<<(kWg0Rows * 64 + 31) / 32, 256, 0, s>>>(net->partial, (int)slices, kWg0Rows, 2,
@@ -1631,6 +1647,7 @@ cudaError_t launch_wgrad(const CnnNet* net, int xi, int dzi, long long M, int la
     a.L = net->L;
     a.halo_rows = wg_halo_rows(net->L);
     a.err = net->err;
+    a.spin_limit = net->spin_limit;
     wgrad_kernel<<<slices, kWgTmaThreads, kWgSmem, s>>>(a);
     if ((e = cudaGetLastError())) return e;
     wgrad_reduce_kernel<<<(577 * 64 + 31) / 32, 256, 0, s>>>(net->partial, slices, kWgRows, 64,
@@ -1676,6 +1693,7 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
     c1.M = M;
     c1.L = L;
     c1.err = net->err;
+    c1.spin_limit = net->spin_limit;
     if ((e = launch_conv1(net, c1, s))) return e;
     ConvTmaArgs a;
     memset(&a, 0, sizeof a);
@@ -1683,6 +1701,7 @@ cudaError_t cnn_forward_dev(CnnNet* net, const uint8_t* syn, long long n, const 
     a.L = L;
     a.halo_rows = halo_tile_rows(L);
     a.err = net->err;
+    a.spin_limit = net->spin_limit;
     for (int l = 1; l < 4; ++l) {
         a.map = net->map_act[l - 1];
         a.out_map = net->tile_act[l];
@@ -1722,6 +1741,7 @@ cudaError_t cnn_backward_dev(CnnNet* net, const uint8_t* syn, long long n, const
     a.L = L;
     a.halo_rows = halo_tile_rows(L);
     a.err = net->err;
+    a.spin_limit = net->spin_limit;
     int cur = 0;
     for (int l = 3; l >= 1; --l) {
         if ((e = launch_wgrad(net, l - 1, cur, M, l, s))) return e;
@@ -1774,7 +1794,8 @@ int check_err(surfmcmc_cnn* net, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(net, e, "network kernels");
     if (h) {
         cudaMemsetAsync(net->err, 0, sizeof(int), s);
-        return cfail(net, SURFMCMC_ECUDA, "network kernel: a pipeline wait timed out");
+        return cfail(net, SURFMCMC_ECUDA, h == kWaitTimeout ? "network kernel: a pipeline wait timed out (device flag 1)"
+                                                          : "network kernel: unknown device error flag");
     }
     return SURFMCMC_OK;
 }
@@ -1995,6 +2016,12 @@ int surfmcmc_cnn_soft_targets(const double* log_ratio, int64_t n, float* targets
     if (!device_ptr(log_ratio) || !device_ptr(targets)) return SURFMCMC_EINVAL;
     soft_targets_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(log_ratio, n, targets);
     return cudaGetLastError() == cudaSuccess ? SURFMCMC_OK : SURFMCMC_ECUDA;
+}
+
+int surfmcmc_cnn_set_wait_limit(surfmcmc_cnn* net, uint32_t polls) {
+    if (!net) return SURFMCMC_EINVAL;
+    net->spin_limit = polls ? polls : kSpinLimit;
+    return SURFMCMC_OK;
 }
 
 int surfmcmc_cnn_status(surfmcmc_cnn* net, void* stream) {

@@ -137,10 +137,13 @@ __host__ __device__ __forceinline__ int geo_nstab(int code, int L) { return code
 __host__ __device__ __forceinline__ int geo_words(int code, int L) { return (geo_nq(code, L) + 31) / 32; }
 __host__ __device__ __forceinline__ int geo_nc(int code, int L) { return code ? L * L / 2 : L * (L - 1) / 2; }
 
-// Shared-memory words of one bundle: X[0..nq+1] then Z[0..nq+1] (two dummy
-// slots each).  The stride is odd so that the bundles of a warp fall on banks
-// of opposite parity: same-colour generators in a row are two qubits apart.
-__host__ __device__ __forceinline__ int bundle_stride(int nq) { return 2 * (nq + 2) + 1; }
+// Shared-memory words of one bundle split over `lam` lanes: X then Z, each
+// of the qubits padded with zero words to a multiple of 8 lam (so that the
+// lanes' occupancy counts need no bounds test) and followed by two dummy
+// slots.  The stride is odd so that the bundles of a warp fall on banks of
+// opposite parity: same-colour generators in a row are two qubits apart.
+__host__ __device__ __forceinline__ int padded_nq(int nq, int lam) { return (nq + 8 * lam - 1) / (8 * lam) * (8 * lam); }
+__host__ __device__ __forceinline__ int bundle_stride(int nq, int lam) { return 2 * (padded_nq(nq, lam) + 2) + 1; }
 
 // Blocks per SM the sweep kernel is compiled for (its register bound): 6
 // with plane widths of 16 or 32 chains, 3 with narrower planes.

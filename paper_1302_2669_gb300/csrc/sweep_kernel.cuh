@@ -38,33 +38,34 @@ __device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32
 // Eight occupancy words of the qubits base + i LAM: for depolarizing noise
 // (IND false) a qubit counts once if it carries any error (X | Z); for
 // independent flips (IND true) its bit flip and its phase flip count
-// separately, four qubits per batch.
+// separately, four qubits per batch.  The planes are zero-padded to a
+// multiple of 8 LAM words, so every index is in range.
 template <int LAM, bool IND>
-__device__ __forceinline__ void occupancy8(const uint32_t* X, const uint32_t* Z, int nq, int base, uint32_t x[8]) {
+__device__ __forceinline__ void occupancy8(const uint32_t* X, const uint32_t* Z, int base, uint32_t x[8]) {
 #pragma unroll
     for (int i = 0; i < (IND ? 4 : 8); ++i) {
         const int q = base + i * LAM;
         if (IND) {
-            x[2 * i] = q < nq ? X[q] : 0u;
-            x[2 * i + 1] = q < nq ? Z[q] : 0u;
+            x[2 * i] = X[q];
+            x[2 * i + 1] = Z[q];
         } else {
-            x[i] = q < nq ? (X[q] | Z[q]) : 0u;
+            x[i] = X[q] | Z[q];
         }
     }
 }
 
 // n of the 32 chains of a bundle as kCountBits bit planes, identical in all
-// LAM lanes of the bundle.
+// LAM lanes of the bundle (nqp: the padded plane length).
 template <int LAM, bool IND>
-__device__ __forceinline__ void recount(const uint32_t* X, const uint32_t* Z, int nq, int sub,
+__device__ __forceinline__ void recount(const uint32_t* X, const uint32_t* Z, int nqp, int sub,
                                         uint32_t cnt[kCountBits]) {
     uint32_t ones = 0, twos = 0, fours = 0;
     uint32_t hi[kCountBits - 3];
 #pragma unroll
     for (int k = 0; k < kCountBits - 3; ++k) hi[k] = 0;
-    for (int base = sub; base < nq; base += (IND ? 4 : 8) * LAM) {
+    for (int base = sub; base < nqp; base += (IND ? 4 : 8) * LAM) {
         uint32_t x[8];
-        occupancy8<LAM, IND>(X, Z, nq, base, x);
+        occupancy8<LAM, IND>(X, Z, base, x);
         uint32_t ta, tb, fa, fb, e;
         csa(ta, ones, ones, x[0], x[1]);
         csa(tb, ones, ones, x[2], x[3]);
@@ -124,10 +125,10 @@ struct OccAcc {
 };
 
 template <int LAM, bool IND>
-__device__ __forceinline__ void accumulate_phase(OccAcc& a, const uint32_t* X, const uint32_t* Z, int nq, int sub) {
-    for (int base = sub; base < nq; base += (IND ? 4 : 8) * LAM) {
+__device__ __forceinline__ void accumulate_phase(OccAcc& a, const uint32_t* X, const uint32_t* Z, int nqp, int sub) {
+    for (int base = sub; base < nqp; base += (IND ? 4 : 8) * LAM) {
         uint32_t x[8];
-        occupancy8<LAM, IND>(X, Z, nq, base, x);
+        occupancy8<LAM, IND>(X, Z, base, x);
         uint32_t ta, tb, fa, fb, e;
         csa(ta, a.ones, a.ones, x[0], x[1]);
         csa(tb, a.ones, a.ones, x[2], x[3]);
@@ -353,7 +354,7 @@ constexpr int kAcptWordsPerWarp = (kAcptPlanes + 1) * 32;
 __device__ __forceinline__ uint32_t* acpt_words(uint32_t* smem, const SweepParams& p, int lam) {
     const int B = 32 / lam;
     const int warps = blockDim.x >> 5;
-    uint32_t* base = smem + 8 * p.grp_nc_max + warps * (B * bundle_stride(p.grp_nq_max) + warp_aux_words(B));
+    uint32_t* base = smem + 8 * p.grp_nc_max + warps * (B * bundle_stride(p.grp_nq_max, lam) + warp_aux_words(B));
     return base + (threadIdx.x >> 5) * kAcptWordsPerWarp + (threadIdx.x & 31);
 }
 
@@ -397,7 +398,8 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
     constexpr int NJ = 32 / LAM;                      // chains owned per lane
     constexpr int SLOTS = PlaneBatch<G>::SLOTS;
     const int nc = gd.nc, nq = gd.nq, L = gd.L;
-    const int stride = bundle_stride(nq);
+    const int nqp = padded_nq(nq, LAM);    // padded plane length; the dummies follow
+    const int stride = bundle_stride(nq, LAM);
     uint32_t* frames = smem + 8 * p.grp_nc_max;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -405,8 +407,8 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
     const long long bid = (unit * (blockDim.x >> 5) + warp) * B + slot;   // bundle within the group
     const bool active = bid < gd.n_bundles;
     uint32_t* X = frames + (warp * B + slot) * stride;
-    uint32_t* Z = X + nq + 2;
-    uint32_t* q_cnt = frames + (blockDim.x >> 5) * B * bundle_stride(p.grp_nq_max) + warp * warp_aux_words(B);
+    uint32_t* Z = X + nqp + 2;
+    uint32_t* q_cnt = frames + (blockDim.x >> 5) * B * bundle_stride(p.grp_nq_max, LAM) + warp * warp_aux_words(B);
     uint32_t* q_items = q_cnt + 1;
     uint32_t* binfo = q_items + kQueueCap * kQueueItem;  // per slot: w, sid[SLOTS]
 
@@ -466,9 +468,11 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                                         : nullptr;
     uint32_t* cfg = p.chain_frames ? p.chain_frames + gd.frames_off - (size_t)gd.item_base * p.C * 2 * W : nullptr;
     const uint32_t* st_in = p.state_in ? p.state_in + gd.state_off + (size_t)(active ? bid : 0) * 2 * nq : nullptr;
-    for (int q = sub; q < nq; q += LAM) {
+    for (int q = sub; q < nqp; q += LAM) {
         uint32_t xw = 0, zw = 0;
-        if (st_in) {
+        if (q >= nq) {
+            // zero padding
+        } else if (st_in) {
             if (active) {
                 xw = st_in[q];
                 zw = st_in[nq + q];
@@ -504,8 +508,8 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
         Z[q] = zw;
     }
     if (sub == 0) {
-        X[nq] = 0u; Z[nq] = 0xFFFFFFFFu;          // dummy of sigma_x generators
-        X[nq + 1] = 0xFFFFFFFFu; Z[nq + 1] = 0u;  // dummy of sigma_z generators
+        X[nqp] = 0u; Z[nqp] = 0xFFFFFFFFu;          // dummy of sigma_x generators
+        X[nqp + 1] = 0xFFFFFFFFu; Z[nqp + 1] = 0u;  // dummy of sigma_z generators
     }
     // Owned chains' sums live in the output array; flushes add to them.
     auto ci_of = [&](int b) -> size_t { return (size_t)syn_of(b) * p.C + chain_of(b); };
@@ -660,7 +664,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                     if constexpr (ACPT) it[4] = acc;
                     if (acc) {
                         uint32_t* qx = frames + (warp * B + qs) * stride;
-                        uint32_t* qown = col < 2 ? qx : qx + nq + 2;
+                        uint32_t* qown = col < 2 ? qx : qx + nqp + 2;
                         const ushort4 sp = tc[qm];
                         qown[sp.x] ^= acc;
                         qown[sp.y] ^= acc;
@@ -681,7 +685,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                 }
             }
             if (t >= gd.burn_in) {
-                accumulate_phase<LAM, IND>(occ, X, Z, nq, sub);
+                accumulate_phase<LAM, IND>(occ, X, Z, nqp, sub);
                 if (++since_flush == flush_every) {
                     flush_acc<LAM>(occ, sub, valid, p.chain_sum, ci_of);
                     since_flush = 0;
@@ -703,7 +707,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
         }
     }
     uint32_t cnt[kCountBits] = {};
-    if constexpr (!SCAN) recount<LAM, IND>(X, Z, nq, sub, cnt);
+    if constexpr (!SCAN) recount<LAM, IND>(X, Z, nqp, sub, cnt);
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
         const int b = sub + j * LAM;
@@ -761,6 +765,11 @@ __global__ void __launch_bounds__(128, sweep_blocks_per_sm(G)) sweep_kernel(cons
                     if (p.code) toric_colour_support(gd.L, col, m, q);
                     else colour_support(gd.L, col, m, q);
                 }
+                // dummy slots (nq, nq + 1) sit after the zero-padded planes
+                const int nq = gd.nq, shift = padded_nq(nq, LAM) - nq;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (q[k] >= nq) q[k] += shift;
                 tab[idx] = make_ushort4((unsigned short)q[0], (unsigned short)q[1], (unsigned short)q[2],
                                         (unsigned short)q[3]);
             }

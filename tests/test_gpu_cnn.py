@@ -159,6 +159,30 @@ def test_gradient_parity(pkg, ctx, L, n, seed):
     net.close()
 
 
+def test_wait_time_out_reports_and_recovers(pkg, ctx):
+    """The bounded pipeline waits of the network kernels give up cleanly.
+    With a bound of one poll (the first poll never suspends) the forward of
+    an L = 5 batch finds an mbarrier phase still pending, the block drains
+    its copies and MMAs and exits, and the call returns ECUDA with the
+    device flag's time-out message; with the default bound the same network
+    then gives exactly its earlier result."""
+    L, n = 5, 4096
+    syn, _ = O.gen_syndromes(4300, 0, n, L, 0.12)
+    dsyn = torch.from_numpy(syn).cuda()
+    net = pkg.Network(ctx, L, max_batch=n)
+    net.set_params(_params(5).astype(np.float32))
+    ref = net.forward(dsyn).cpu().numpy()
+    net.set_wait_limit(1)
+    with pytest.raises(pkg.SurfmcmcError) as e:
+        net.forward(dsyn)
+    assert e.value.code == pkg.ECUDA and "timed out" in str(e.value)
+    net.set_wait_limit(0)
+    again = net.forward(dsyn).cpu().numpy()
+    assert (again == ref).all()
+    net.status()                      # the flag was cleared by the failing call
+    net.close()
+
+
 def test_training_reduces_loss(pkg, ctx):
     """Adam on one fixed batch (one-hot targets of the true classes): the
     loss falls well below its start."""
