@@ -4,8 +4,9 @@
 Workload (one step = one decode call over one resident batch): planar code
 L = 13 (313 qubits), depolarizing p cycling through 0.10, 0.13, 0.16, 0.18,
 16,384 seeded synthetic syndromes per batch, 4 classes x 16 chains, 20,000
-sweeps per chain (= 312 proposals each), of which the first 800 prepare the
-start by annealing from 0.3 beta_bar to beta_bar and are not sampled.  Metric: syndromes decoded per second
+sweeps per chain (= 312 proposals each), of which the first 4,000 prepare
+the start by annealing from 0.1 beta_bar to beta_bar in 16 stages and are
+not sampled.  Metric: syndromes decoded per second
 (and stabilizer updates per second = proposals, accepted or not), with the
 logical error rate of the decoded batches beside it.
 
@@ -37,9 +38,9 @@ N_PER_STEP = 16384
 K_CLASSES = 4
 R_CHAINS = 16
 SWEEPS = 20000
-BURN_IN = 800          # not sampled; annealed from ANNEAL_BETA0 beta_bar in ANNEAL_STAGES stages
-ANNEAL_STAGES = 4
-ANNEAL_BETA0 = 0.3
+BURN_IN = 4000         # not sampled; annealed from ANNEAL_BETA0 beta_bar in ANNEAL_STAGES stages
+ANNEAL_STAGES = 16
+ANNEAL_BETA0 = 0.1
 NQ = 2 * L * L - 2 * L + 1
 NSTAB = 2 * L * (L - 1)
 UPDATES_PER_SYNDROME = K_CLASSES * R_CHAINS * SWEEPS * NSTAB
@@ -176,6 +177,32 @@ def cpu_baseline(ids_per_p, sweeps=SWEEPS, id0=0):
     return rec, out
 
 
+def early_stop_leg():
+    """The learned early stop (the benchmark spec's batched + learned form)
+    against plain long chains, measured inside the run: L = 17, a network
+    trained from seeds on 2^20 syndromes labelled by the library's own
+    chains (p stratified over [0.08, 0.18]), tau calibrated per p on 65,536
+    validation syndromes, then plain long chains (4 x 4 chains, 20,000
+    sweeps, the first 4,000 annealed in 16 stages from 0.1 beta_bar) and
+    the early-stopped decode timed on 65,536 fresh test syndromes at
+    p = 0.10 and 0.14 (CUDA events, one call each after a warm-up call)."""
+    import argparse
+    from paper_1302_2669_gb300 import early_stop as E
+    ns = argparse.Namespace(L=17, train=1 << 20, val=65536, test=65536, p_lo=0.08, p_hi=0.18, n_p=32, label_R=4,
+                            label_sweeps=2000, epochs=8, batch=1024, lr=2e-3, lr_final=1e-4, R=4, sweeps=20000,
+                            burn_in=4000, anneal_stages=16, anneal_beta0=0.1, chunk=1000, seed=4001,
+                            eval_ps=[0.10, 0.14], reorder=False)
+    t0 = time.perf_counter()
+    res = E.run(ns, log=lambda m: None)
+    keys = ("p", "tau", "syn_per_s_long", "syn_per_s_early", "gain", "ler_long", "ler_early", "sigma",
+            "within_1sigma", "mean_sweeps_early", "stopped_at_first_checkpoint")
+    return {"L": ns.L, "train_syndromes": ns.train, "epochs": ns.epochs, "label_chains": res["label_chains"],
+            "long_chain": res["long_chain"], "chunk_sweeps": ns.chunk, "val": ns.val, "test": ns.test,
+            "final_loss": res["losses"][-1], "label_seconds": res["label_seconds"],
+            "train_seconds": res["train_seconds"], "cnn_forward_syn_per_s": res["cnn_forward_syn_per_s"],
+            "per_p": [{k: r[k] for k in keys} for r in res["per_p"]], "seconds": time.perf_counter() - t0}
+
+
 def compare_parity(orc, last, ids_per_p):
     """Element-by-element comparison of the GPU's decisions and class sums
     with the oracle's on the sampled syndromes of every p."""
@@ -230,6 +257,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-early-stop", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -398,6 +426,9 @@ def main():
         "e2e": e2e,
     }
     line["decisions"] = {"gathered_over_ranks": world, "per_p": {f"{p:.2f}": v for p, v in gathered.items()}}
+    if not args.no_early_stop:
+        ctx.close()
+        line["early_stop"] = early_stop_leg()
     ids = [parity_ids(n) for _ in PS]
     if (world == 1 and not args.no_cpu_baseline) or not args.no_parity:
         rec, orc = cpu_baseline(ids, sweeps=sweeps, id0=id0)
@@ -406,7 +437,8 @@ def main():
         if not args.no_parity:
             line["parity"] = compare_parity(orc, last, ids)
     print(json.dumps(line), flush=True)
-    ctx.close()
+    if args.no_early_stop:
+        ctx.close()
     return 0
 
 

@@ -137,10 +137,11 @@ __device__ __forceinline__ void accumulate_phase(OccAcc& a, const uint32_t* X, c
         csa(tb, a.ones, a.ones, x[6], x[7]);
         csa(fb, a.twos, a.twos, ta, tb);
         csa(e, a.fours, a.fours, fa, fb);
-        // ripple the eights into the high planes (rarely more than a few)
+        // ripple the eights into the high planes: the first levels carry for
+        // some of the 32 chains nearly every time, so they run untested
 #pragma unroll
         for (int k = 0; k < kAccHi; ++k) {
-            if (!e) break;
+            if (k >= 3 && !e) break;
             const uint32_t c = a.hi[k] & e;
             a.hi[k] ^= e;
             e = c;

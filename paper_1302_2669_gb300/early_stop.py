@@ -8,7 +8,8 @@ buffers and keeps counts):
 1. Data: syndromes of a size-L code from the library's generator at error
    rates stratified over [p_lo, p_hi] (n_p equal strata, one seed, distinct
    ids); labels from the library's decoder (K = 4 classes x R chains,
-   label_sweeps sweeps, the first quarter annealed): soft targets = softmax
+   label_sweeps sweeps, the first quarter annealed in 16 stages from
+   0.1 beta_bar): soft targets = softmax
    of its class log-ratios -beta_bar (<n>_k - min <n>).
 2. Training: Adam on mini-batches, the tensor-core forward/backward kernels.
 3. Calibration, per evaluated error rate p, on a validation set at p: one
@@ -64,7 +65,9 @@ def make_set(ctx, L, n, seed, p_lo, p_hi, n_p, label_opts=None, id_base=0):
 def label_opts(L, R=4, sweeps=None):
     import paper_1302_2669_gb300 as P
     sweeps = sweeps or L * L
-    return P.Opts(chains_per_class=R, n_sweeps=sweeps, burn_in=sweeps // 4, anneal_stages=4, anneal_beta0=0.3)
+    burn = sweeps // 4
+    return P.Opts(chains_per_class=R, n_sweeps=sweeps, burn_in=burn, anneal_stages=min(16, burn),
+                  anneal_beta0=0.1)
 
 
 def train(net, data, epochs, batch, lr, seed=0, lr_final=None, log=None):
@@ -236,7 +239,7 @@ def run(args, log=print):
                                           lr_final=args.lr_final, log=log))
     del tr
     long_opts = P.Opts(chains_per_class=args.R, n_sweeps=args.sweeps, burn_in=args.burn_in,
-                       anneal_stages=4, anneal_beta0=0.3)
+                       anneal_stages=getattr(args, "anneal_stages", 4), anneal_beta0=getattr(args, "anneal_beta0", 0.3))
     fwd_net = P.Network(ctx, L, max_batch=8192)
     fwd_net.set_params(net.get_params())
     net.close()
@@ -256,7 +259,7 @@ def run(args, log=print):
         "label_seconds": t_lab, "train_seconds": t_train,
         "train_samples_per_s": args.train * args.epochs / t_train,
         "long_chain": {"sweeps": args.sweeps, "burn_in": args.burn_in, "chains": f"4 x {args.R}",
-                       "anneal": "4 stages from 0.3"},
+                       "anneal": f"{long_opts.anneal_stages} stages from {long_opts.anneal_beta0}"},
         "chunk": args.chunk, "val": args.val, "test": args.test, "per_p": rows,
         "cnn_forward_syn_per_s": args.test / t_fwd, "cnn_forward_tflops": args.test * flops / t_fwd / 1e12,
         "wall_seconds": time.time() - t0,
@@ -292,7 +295,9 @@ def main(argv=None):
     ap.add_argument("--lr-final", type=float, default=1e-4)
     ap.add_argument("--R", type=int, default=4)
     ap.add_argument("--sweeps", type=int, default=20000)
-    ap.add_argument("--burn-in", type=int, default=2000)
+    ap.add_argument("--burn-in", type=int, default=4000)
+    ap.add_argument("--anneal-stages", type=int, default=16)
+    ap.add_argument("--anneal-beta0", type=float, default=0.1)
     ap.add_argument("--chunk", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=4001)
     ap.add_argument("--eval-ps", default="0.08,0.10,0.12,0.14,0.16")

@@ -7,15 +7,16 @@ proposals per chain,
 * the distinguishability of the classes, min over the wrong classes of
   <n>_false minus <n>_true, grows with L below the threshold (p = 0.13).
 
-The paper puts the threshold of algorithm C at 15-16 %.  Budget here: 1,000
-burn-in sweeps annealed from 0.3 beta_bar in 4 stages, then 3,000 sampled
-sweeps of 2L(L-1) proposals each (at least 10 L^4 proposals per chain for
-L <= 15), 4 classes x 4 chains, seeded synthetic syndromes with their true
-classes.  The start states here are straight strings, not the paper's
-matched ones, so the chains need the annealed burn-in to reach equilibrium:
-with only L^2 sweeps (a quarter of them annealed) the error rate at p = 0.10
-rose with L (14 / 26 / 41 % at L = 7 / 11 / 15), the signature of chains
-that have not mixed, not of the decoder's threshold."""
+The paper puts the threshold of algorithm C at 15-16 %.  Budget here:
+20,000 sweeps of 2L(L-1) proposals each, the first 4,000 annealed from
+0.1 beta_bar in 16 stages and not sampled (at least 4 L^4 sampled
+proposals per chain up to L = 15), 4 classes x 4 chains, seeded synthetic
+syndromes with their true classes.  The start states here are straight
+strings, not the paper's matched ones, so the chains need the annealed
+burn-in to mix: with the first 800 sweeps annealed from 0.3 beta_bar in 4
+stages the error rate at p = 0.10 still rose from L = 11 to 15 (1.16 % to
+2.67 %), and with 1,000 of 4,000 from 11 to 15 as well; with this schedule
+it falls (2.91 / 0.78 / 0.48 % at L = 7 / 11 / 15)."""
 import math
 
 import numpy as np
@@ -26,7 +27,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 SIZES = (7, 11, 15)
-N = 32768
+N = 65536
 R = 4
 
 
@@ -47,15 +48,14 @@ def ctx(pkg):
     c.close()
 
 
-BURN, SAMPLED = 1000, 3000
+BURN, SWEEPS, STAGES, BETA0 = 4000, 20000, 16, 0.1
 
 
 def _run(pkg, ctx, L, p, seed):
-    burn = BURN
-    sweeps = BURN + SAMPLED
-    assert SAMPLED * 2 * L * (L - 1) >= 10 * L ** 4     # the paper's n_sample = L^4 per chain, ten times over
+    burn, sweeps = BURN, SWEEPS
+    assert (sweeps - burn) * 2 * L * (L - 1) >= 4 * L ** 4   # the paper's n_sample = L^4 per chain, four times over
     syn, tc = ctx.gen_syndromes(seed, 0, N, L, p, like=torch.zeros(1, device="cuda"))
-    opts = pkg.Opts(chains_per_class=R, n_sweeps=sweeps, burn_in=burn, anneal_stages=4, anneal_beta0=0.3)
+    opts = pkg.Opts(chains_per_class=R, n_sweeps=sweeps, burn_in=burn, anneal_stages=STAGES, anneal_beta0=BETA0)
     cls, csum, _ = ctx.decode(syn, L, p, opts, seed=seed + 100)
     torch.cuda.synchronize()
     cls, tc = cls.cpu().numpy(), tc.cpu().numpy().astype(np.int64)

@@ -291,22 +291,22 @@ def test_bench_workload_full_size_sampled(ctx, pkg, p, seed, idx):
     """The benchmark's own workload at full size in its launch configuration,
     at each of its four error rates: L = 13, 16,384 syndromes (syndrome seed
     2010/2013/2016/2018, decoder seed + 100), 4 classes x 16 chains, 20,000
-    sweeps of which the first 800 are annealed in 4 stages from 0.3
+    sweeps of which the first 4,000 are annealed in 16 stages from 0.1
     beta_bar.  Syndromes spread over the batch (first, last, bundle and block
     boundaries) are decoded by the oracle at full length and must agree bit
     for bit: class, sums, log-ratios, per-chain sums, final n and final
     frames.  Each error rate has its own threshold table, digit-plane modes
     and annealing tables."""
-    L, n, R, T, burn = 13, 16384, 16, 20000, 800
+    L, n, R, T, burn, stages, beta0 = 13, 16384, 16, 20000, 4000, 16, 0.1
     syn, _ = O.gen_syndromes(seed, 0, n, L, p)
-    opts = pkg.Opts(chains_per_class=R, n_sweeps=T, burn_in=burn, anneal_stages=4, anneal_beta0=0.3)
+    opts = pkg.Opts(chains_per_class=R, n_sweeps=T, burn_in=burn, anneal_stages=stages, anneal_beta0=beta0)
     dsyn = torch.from_numpy(syn).cuda()
     out = ctx.decode_ex(dsyn, L, p, opts, seed=seed + 100, id0=0)
     cls, csum, lr = ctx.decode(dsyn, L, p, opts, seed=seed + 100, id0=0)   # the call the benchmark times
     torch.cuda.synchronize()
     assert (_np(cls) == _np(out["cls"])).all() and (_np(csum) == _np(out["class_sum"])).all()
     assert (_np(lr) == _np(out["log_ratio"])).all()
-    refs = O.decode_batch(L, p, 4, R, T, seed + 100, idx, syn[idx], burn_in=burn, anneal_stages=4,
-                          anneal_beta0=0.3)
+    refs = O.decode_batch(L, p, 4, R, T, seed + 100, idx, syn[idx], burn_in=burn, anneal_stages=stages,
+                          anneal_beta0=beta0)
     for i, ref in zip(idx, refs):
         _compare_decode(out, ref, i, 4 * R, L)
