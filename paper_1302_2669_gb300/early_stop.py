@@ -15,8 +15,8 @@ buffers and keeps counts):
 3. Calibration, per evaluated error rate p, on a validation set at p: one
    chunked run of the long-chain decoder gives its decision at every
    checkpoint; for each candidate tau the early-stop rule is replayed on those
-   decisions, and the smallest tau whose error rate stays within one binomial
-   sigma of the long-chain rate is kept.
+   decisions, and the smallest tau whose error rate does not exceed the
+   long-chain rate is kept (the test set then has to stay within one sigma).
 4. Test at p: the long-chain decoder and the early-stop decoder on a fresh
    test set (one call each), both timed on the device; error rates against
    the true classes.  With --reorder, also the early stop with budget
@@ -143,8 +143,11 @@ def replay(logprob, dec, marks, tau):
     return cls, np.asarray(marks)[stop]
 
 
-def calibrate(logprob, dec, marks, true_cls, taus):
-    """Smallest tau whose error rate is within one sigma of the long chains'."""
+def calibrate(logprob, dec, marks, true_cls, taus, margin_sigma=0.0):
+    """Smallest tau whose validation error rate exceeds the long chains' by
+    at most margin_sigma binomial sigmas.  The default, no excess at all,
+    leaves room for the noise of a fresh test set, on which the early stop
+    has to stay within one sigma of the long chains."""
     n = len(true_cls)
     ler_long = float((dec[:, -1] != true_cls).mean())
     sigma = math.sqrt(max(ler_long * (1 - ler_long), 1.0 / n) / n)
@@ -154,7 +157,7 @@ def calibrate(logprob, dec, marks, true_cls, taus):
         cls, sw = replay(logprob, dec, marks, tau)
         ler = float((cls != true_cls).mean())
         rows.append({"tau": tau, "ler": ler, "mean_sweeps": float(sw.mean())})
-        if best is None and ler <= ler_long + sigma:
+        if best is None and ler <= ler_long + margin_sigma * sigma:
             best = tau
     return best, ler_long, sigma, rows
 

@@ -59,7 +59,7 @@ def test_replay_stop_rule():
     assert sw[0] == 10
 
 
-def test_calibrate_picks_smallest_tau_within_one_sigma():
+def test_calibrate_picks_smallest_tau_not_above_the_long_chains():
     rng = np.random.default_rng(5)
     n, marks = 4000, [10, 20]
     true = rng.integers(0, 4, size=n).astype(np.int32)
@@ -87,3 +87,6 @@ def test_calibrate_picks_smallest_tau_within_one_sigma():
     sweeps = [r["mean_sweeps"] for r in sorted(rows, key=lambda r: r["tau"])]
     assert all(a <= b for a, b in zip(sweeps, sweeps[1:]))   # a larger tau never stops earlier
     assert lers[4.0] == ler_long                       # nothing stops: the long chains' rate
+    assert lers[1.0] <= ler_long                       # the default margin: no excess at all
+    # with a margin of one sigma tau = 0 is still out
+    assert ES.calibrate(lp, dec, marks, true, [0.0, 1.0, 2.0, 4.0], margin_sigma=1.0)[0] == 1.0

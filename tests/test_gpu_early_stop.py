@@ -132,18 +132,19 @@ def test_invalid(pkg, ctx):
 def test_trained_network_gain(pkg, ctx):
     """L = 7: a network trained on the library's own labels (p over
     [0.08, 0.18]) stops many syndromes early at p = 0.10; on a fresh test set
-    the early-stop error rate stays within two binomial sigmas of the long
-    chains' and the throughput rises."""
+    of 131,072 syndromes the early-stop error rate stays within one binomial
+    sigma of the long chains' (the benchmark spec's bar) and the throughput
+    rises."""
     import argparse
     from paper_1302_2669_gb300 import early_stop as E
-    ns = argparse.Namespace(L=7, train=1 << 16, val=32768, test=32768, p_lo=0.08, p_hi=0.18, n_p=8, label_R=4,
+    ns = argparse.Namespace(L=7, train=1 << 16, val=65536, test=131072, p_lo=0.08, p_hi=0.18, n_p=8, label_R=4,
                             label_sweeps=400, epochs=4, batch=512, lr=2e-3, lr_final=2e-4, R=4, sweeps=2000,
-                            burn_in=200, chunk=200, seed=4001, eval_ps=[0.10])
+                            burn_in=400, anneal_stages=16, anneal_beta0=0.1, chunk=200, seed=4001, eval_ps=[0.10])
     res = E.run(ns, log=lambda m: None)
     row = res["per_p"][0]
     row = {k: v for k, v in row.items() if k != "calibration"}
     assert row["tau"] is not None
-    assert row["ler_early"] <= row["ler_long"] + 2 * row["sigma"], row
+    assert row["ler_early"] <= row["ler_long"] + row["sigma"], row
     assert row["mean_sweeps_early"] < 0.75 * ns.sweeps, row
     assert row["gain"] > 1.2, row
 
