@@ -54,9 +54,9 @@ INT_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) of one sampled sweep launch per syndrome of the
 # L = 13, 4 x 16-chain workload, from one ncu capture at 8,192 syndromes
-# (41,100,032 B read + 57,856 B written: the bit-sliced chain state handed
-# over from the annealing launch, proportional to the syndromes).
-SWEEP_DRAM_BYTES_PER_SYNDROME = (41100032 + 57856) / 8192
+# (41,282,560 B read + 31,232 B written: the bit-sliced chain state handed
+# over from the last annealing launch, proportional to the syndromes).
+SWEEP_DRAM_BYTES_PER_SYNDROME = (41282560 + 31232) / 8192
 
 
 def ops_per_update() -> float:
@@ -155,8 +155,9 @@ def cpu_baseline(ids_per_p, sweeps=SWEEPS, id0=0):
             syn, _ = O.gen_syndromes(s, id0 + j, 1, L, p)
             jobs.append((p, s, id0 + j, syn[0]))
             where.append((i, j))
-    burn = min(BURN_IN, sweeps)
+    burn = BURN_IN * sweeps // SWEEPS
     stages = ANNEAL_STAGES if burn >= ANNEAL_STAGES else 0
+    burn = burn if stages else 0
     work = [(L, p, K_CLASSES, R_CHAINS, sweeps, s + 100, ident, syn, burn, 1.0, stages, ANNEAL_BETA0, 0, 0, None)
             for p, s, ident, syn in jobs]
     procs = min(cores, len(work))
@@ -296,7 +297,9 @@ def main():
     b.build()
     ctx = pkg.Context(local)
     n, sweeps = args.n, args.sweeps
-    burn = min(BURN_IN, sweeps)
+    burn = BURN_IN * sweeps // SWEEPS       # the same share of a reduced run
+    if burn < ANNEAL_STAGES:
+        burn = 0
     opts = pkg.Opts(n_classes=K_CLASSES, chains_per_class=R_CHAINS, n_sweeps=sweeps, burn_in=burn,
                     anneal_stages=ANNEAL_STAGES if burn >= ANNEAL_STAGES else 0, anneal_beta0=ANNEAL_BETA0)
     id0 = shard.weak_id0(rank, n)

@@ -288,15 +288,21 @@ void surfmcmc_plan_destroy(surfmcmc_plan* plan);
 
 /* Autotuning of the launch shape (the paper has no counterpart): times the
  * sweep kernel on n_probe synthetic size-L syndromes for `sweeps` sweeps at
- * rate p with every supported lanes_per_bundle (2, 4, 8, 16, 32: threads per
- * 32-chain bundle, hence 32/lanes bundles and 32 x 32/lanes chains per warp)
- * and records the fastest in ctx for later calls with lanes_per_bundle = 0
- * and the same (L, chains_per_class); ragged calls use the entry of their
- * heaviest size.  Results never depend on the choice.  *best receives it and
- * ms[5] the timings in milliseconds (NaN where the shape does not fit); both
- * may be NULL.  EINVAL for bad arguments. */
+ * rate p for every supported lanes_per_bundle (2, 4, 8, 16, 32: threads per
+ * 32-chain bundle, hence 32/lanes bundles and 32 x 32/lanes chains per warp,
+ * and ceil(generators per colour / lanes) proposals per lane and colour)
+ * combined with every cap of 6, 5, 4, 3 resident blocks per multiprocessor
+ * (the persistent grid; a cap above what fits counts as no cap), and records
+ * the fastest pair in ctx for later calls with lanes_per_bundle = 0 and the
+ * same (L, chains_per_class); ragged calls use the entry of their heaviest
+ * size.  Results never depend on the choice.  *best_lanes and
+ * *best_blocks_per_sm receive it, ms[SURFMCMC_TUNE_LANES][SURFMCMC_TUNE_BLOCKS]
+ * the timings in milliseconds (NaN where the shape does not fit); any of the
+ * three may be NULL.  EINVAL for bad arguments. */
+#define SURFMCMC_TUNE_LANES 5
+#define SURFMCMC_TUNE_BLOCKS 4
 int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, double p, int64_t n_probe,
-                      uint32_t sweeps, int32_t* best, double* ms);
+                      uint32_t sweeps, int32_t* best_lanes, int32_t* best_blocks_per_sm, double* ms);
 
 /* Thermodynamic integration (Eq. 6: log Z_E(beta) = -int_0^beta <n>_{b,E} db
  * + n_stab log 2; Sec. IV: the integral by Simpson's rule; Sec. IV.A: 21

@@ -77,6 +77,9 @@ EXPORTS = ("surfmcmc_default_opts", "surfmcmc_create", "surfmcmc_destroy", "surf
            "surfmcmc_cnn_train_step", "surfmcmc_cnn_status", "surfmcmc_cnn_set_wait_limit", "surfmcmc_cnn_soft_targets",
            "surfmcmc_decode_early")
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
+TUNE_LANES = (2, 4, 8, 16, 32)              # candidates of surfmcmc_autotune
+TUNE_LANES_N = len(TUNE_LANES)
+TUNE_BLOCKS = (6, 5, 4, 3)
 
 
 def lib():
@@ -121,7 +124,7 @@ def lib():
         L.surfmcmc_server_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
         L.surfmcmc_server_destroy.argtypes = [vp]
         L.surfmcmc_server_destroy.restype = None
-        L.surfmcmc_autotune.argtypes = [vp, i32, i32, dbl, i64, u32, C.POINTER(i32), C.POINTER(dbl)]
+        L.surfmcmc_autotune.argtypes = [vp, i32, i32, dbl, i64, u32, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]
         L.surfmcmc_plan_destroy.argtypes = [vp]
         L.surfmcmc_plan_destroy.restype = None
         L.surfmcmc_cnn_n_params.argtypes = []
@@ -349,11 +352,14 @@ class Context:
         return cls, csum, sw
 
     def autotune(self, L, chains_per_class, p, n_probe=4096, sweeps=20):
-        """surfmcmc_autotune: returns (best lanes per bundle, {lanes: ms})."""
-        best = C.c_int32()
-        ms = (C.c_double * 5)()
-        self._check(lib().surfmcmc_autotune(self._h, L, chains_per_class, p, n_probe, sweeps, C.byref(best), ms))
-        return best.value, {lam: ms[i] for i, lam in enumerate((2, 4, 8, 16, 32))}
+        """surfmcmc_autotune: returns (best lanes per bundle, best cap of resident
+        blocks per multiprocessor, {(lanes, blocks): ms})."""
+        best, best_b = C.c_int32(), C.c_int32()
+        ms = (C.c_double * (TUNE_LANES_N * len(TUNE_BLOCKS)))()
+        self._check(lib().surfmcmc_autotune(self._h, L, chains_per_class, p, n_probe, sweeps, C.byref(best),
+                                            C.byref(best_b), ms))
+        return best.value, best_b.value, {(lam, bb): ms[i * len(TUNE_BLOCKS) + j]
+                                          for i, lam in enumerate(TUNE_LANES) for j, bb in enumerate(TUNE_BLOCKS)}
 
     def set_timing(self, enable: bool):
         """surfmcmc_set_timing: record CUDA events around every sweep kernel."""

@@ -20,6 +20,7 @@ using namespace surfmcmc;
 // Launch shape of the sweep kernel chosen by surfmcmc_autotune.
 struct Tuned {
     int lam = 0;             // lanes per bundle
+    int blocks_per_sm = 0;   // persistent blocks per multiprocessor (0: as many as fit)
 };
 
 struct surfmcmc_ctx {
@@ -161,6 +162,14 @@ int pick_lanes(int L, int requested, int* lam_out, const surfmcmc_ctx* ctx = nul
     }
     *lam_out = heuristic_lanes(L, code);
     return SURFMCMC_OK;
+}
+
+// Resident blocks per multiprocessor of a run: the autotuned value for (L,
+// chains per class) unless the caller fixed the lanes, else all that fit.
+int tuned_blocks(const surfmcmc_ctx* ctx, int L, int R, int requested_lanes) {
+    if (requested_lanes || !ctx) return 0;
+    auto it = ctx->tuned.find({L, R});
+    return it == ctx->tuned.end() ? 0 : it->second.blocks_per_sm;
 }
 
 // Widens the lanes of a small batch (widen_lanes_for) unless the caller
@@ -378,6 +387,7 @@ int ragged_layout(surfmcmc_ctx* ctx, const int32_t* Ls, const uint32_t* sweeps, 
     while (sweep_smem_bytes(n_qubits(lmax), lmax * (lmax - 1) / 2, lay.lam) > 200 * 1024 && lay.lam < 32) lay.lam *= 2;
     const int Cn = 4 * o.chains_per_class;
     init_chains(lay.sp, Cn, o.chains_per_class, 0);
+    if (!lay.groups.empty()) lay.sp.max_blocks_per_sm = tuned_blocks(ctx, lay.groups[0].L, o.chains_per_class, o.lanes_per_bundle);
     lay.sp.scan = o.scan;
     lay.sp.noise = o.noise;
     energy_table(o, lay.sp.energy);
@@ -775,6 +785,7 @@ int surfmcmc_decode_ex(surfmcmc_ctx* ctx, const uint8_t* syndromes, int64_t n, i
     sp.code = toric;
     sp.scan = o.scan;
     sp.noise = o.noise;
+    sp.max_blocks_per_sm = tuned_blocks(ctx, L, R, o.lanes_per_bundle);
     energy_table(o, sp.energy);
     lam = widen_lanes(ctx, L, o.lanes_per_bundle, lam, bundles_of(sp, n), sp.G, toric);
     add_group(sp, L, n, 0, 0, 0, 0, lam);
@@ -1100,7 +1111,7 @@ void surfmcmc_plan_destroy(surfmcmc_plan* plan) {
 
 
 int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, double p, int64_t n_probe,
-                      uint32_t sweeps, int32_t* best_out, double* ms_out) {
+                      uint32_t sweeps, int32_t* best_lanes, int32_t* best_blocks_per_sm, double* ms_out) {
     int rc = check_common(ctx, n_probe, L, 0);
     if (rc) return rc;
     if (n_probe < 1 || sweeps < 1 || chains_per_class < 1 || 4 * chains_per_class > 1024 || !(p > 0.0 && p <= 0.75))
@@ -1108,7 +1119,8 @@ int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, do
     ctx->last_error.clear();
     DeviceGuard g(ctx->device);
     const int R = chains_per_class, Cn = 4 * R, nq = n_qubits(L), W = n_words(L);
-    const int cand[5] = {2, 4, 8, 16, 32};
+    const int cand[SURFMCMC_TUNE_LANES] = {2, 4, 8, 16, 32};
+    const int bcand[SURFMCMC_TUNE_BLOCKS] = {6, 5, 4, 3};
     SweepParams base;
     init_chains(base, Cn, R, 0);
     Carver cv;
@@ -1127,42 +1139,48 @@ int surfmcmc_autotune(surfmcmc_ctx* ctx, int32_t L, int32_t chains_per_class, do
     CK(cudaEventCreate(&e_b));
     CK(launch_gen_syndromes(0x7475ull, 0, n_probe, L, p, syn, nullptr, s));
     CK(launch_start_frames(syn, n_probe, L, e0, code, s));
-    int best = 0;
+    int best = 0, best_b = 0;
     float best_ms = 0.f;
-    for (int i = 0; i < 5; ++i) {
-        if (ms_out) ms_out[i] = NAN;
-        const int lam = cand[i];
-        if (sweep_smem_bytes(nq, L * (L - 1) / 2, lam) > 200 * 1024) continue;
-        SweepParams sp = base;
-        add_group(sp, L, n_probe, 0, 0, 0, 0, lam);
-        set_temperature(sp, p, 1.0);
-        make_round_keys(0x7475u, 0u, &sp.rk);
-        sp.grp[0].t_begin = 0;
-        sp.grp[0].t_end = sweeps;
-        sp.grp[0].burn_in = 0;
-        sp.e0 = e0;
-        sp.e0code = code;
-        sp.chain_sum = (uint64_t*)(b + o_cs);
-        sp.unit_counter = (unsigned int*)(b + o_ctr);
-        CK(launch_sweep(sp, lam, s));  // warm-up
-        CK(cudaEventRecord(e_a, s));
-        CK(launch_sweep(sp, lam, s));
-        CK(cudaEventRecord(e_b, s));
-        CK(cudaEventSynchronize(e_b));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e_a, e_b));
-        if (ms_out) ms_out[i] = ms;
-        if (!best || ms < best_ms) {
-            best = lam;
-            best_ms = ms;
+    for (int i = 0; i < SURFMCMC_TUNE_LANES; ++i) {
+        for (int j = 0; j < SURFMCMC_TUNE_BLOCKS; ++j) {
+            double* slot = ms_out ? ms_out + i * SURFMCMC_TUNE_BLOCKS + j : nullptr;
+            if (slot) *slot = NAN;
+            const int lam = cand[i];
+            if (sweep_smem_bytes(nq, L * (L - 1) / 2, lam) > kSweepSmemLimit) continue;
+            SweepParams sp = base;
+            sp.max_blocks_per_sm = bcand[j];
+            add_group(sp, L, n_probe, 0, 0, 0, 0, lam);
+            set_temperature(sp, p, 1.0);
+            make_round_keys(0x7475u, 0u, &sp.rk);
+            sp.grp[0].t_begin = 0;
+            sp.grp[0].t_end = sweeps;
+            sp.grp[0].burn_in = 0;
+            sp.e0 = e0;
+            sp.e0code = code;
+            sp.chain_sum = (uint64_t*)(b + o_cs);
+            sp.unit_counter = (unsigned int*)(b + o_ctr);
+            CK(launch_sweep(sp, lam, s));  // warm-up
+            CK(cudaEventRecord(e_a, s));
+            CK(launch_sweep(sp, lam, s));
+            CK(cudaEventRecord(e_b, s));
+            CK(cudaEventSynchronize(e_b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e_a, e_b));
+            if (slot) *slot = ms;
+            if (!best || ms < best_ms) {
+                best = lam;
+                best_b = bcand[j];
+                best_ms = ms;
+            }
         }
     }
     cudaEventDestroy(e_a);
     cudaEventDestroy(e_b);
     cudaStreamDestroy(s);
     if (!best) return fail(ctx, SURFMCMC_EINVAL, "no lanes_per_bundle fits L=%d", L);
-    ctx->tuned[{L, R}].lam = best;
-    if (best_out) *best_out = best;
+    ctx->tuned[{L, R}] = Tuned{best, best_b};
+    if (best_lanes) *best_lanes = best;
+    if (best_blocks_per_sm) *best_blocks_per_sm = best_b;
     return SURFMCMC_OK;
 }
 
@@ -1203,6 +1221,7 @@ int surfmcmc_decode_early(surfmcmc_ctx* ctx, surfmcmc_cnn* net, const uint8_t* s
 
     SweepParams sp0;
     init_chains(sp0, Cn, R, id0);
+    sp0.max_blocks_per_sm = tuned_blocks(ctx, L, R, o.lanes_per_bundle);
     add_group(sp0, L, n, 0, 0, 0, 0, lam);
     const long long nb_max = sp0.grp[0].n_bundles;
 

@@ -202,6 +202,7 @@ struct SweepParams {
     int grp_nq_max, grp_nc_max;   // largest group (shared-memory layout)
     long long total_units;
     unsigned int* unit_counter;   // work queue of the persistent blocks (reset by the launcher)
+    int max_blocks_per_sm;        // persistent blocks per multiprocessor, at most (0: as many as fit)
     GroupDesc grp[kMaxGroups];
 };
 

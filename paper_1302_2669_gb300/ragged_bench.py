@@ -13,8 +13,13 @@ the launching stream after a warm-up, all buffers on the device:
           and replayed
   per_L   five surfmcmc_decode calls, one per size, on that size's items
 
-Prints one JSON line: syndromes/s and stabilizer updates/s of each, and
-whether the plan's classes and sums equal the ragged call's.
+With --autotune (the default) the launch shape of every size is tuned
+first (surfmcmc_autotune: lanes per bundle x resident blocks per
+multiprocessor, timed on that size's own items) and the three timings use
+the tuned shapes; the ragged call is also timed on a fresh context with the
+fixed rule-based shape for comparison.  Prints one JSON line: syndromes/s
+and stabilizer updates/s of each, the tuned shapes, and whether the plan's
+and the fixed-shape call's classes and sums equal the ragged call's.
 """
 from __future__ import annotations
 
@@ -31,6 +36,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=65536)
     ap.add_argument("--p", type=float, default=0.14)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args(argv)
 
     import torch
@@ -69,7 +75,21 @@ def main(argv=None):
         return a.elapsed_time(e) / 1000.0 / args.reps
 
     out = {}
+    tuned = {}
+    if not args.no_autotune:
+        for L in LS:
+            lam, bps, grid = ctx.autotune(int(L), R, p, n_probe=max(1, int((Ls == L).sum())),
+                                          sweeps=min(int(L) * int(L), 64))
+            tuned[int(L)] = {"lanes_per_bundle": lam, "blocks_per_sm": bps,
+                             "ms": {f"{a}x{b}": v for (a, b), v in grid.items() if v == v}}
+        fixed_ctx = P.Context(0)
+        t_fixed = timed(lambda: out.__setitem__("f", fixed_ctx.decode_ragged(cat, dLs, p, opts, n_sweeps=sw,
+                                                                               seed=3101)))
     t_ragged = timed(lambda: out.__setitem__("r", ctx.decode_ragged(cat, dLs, p, opts, n_sweeps=sw, seed=3101)))
+    if not args.no_autotune:
+        same_fixed = bool((out["f"][0].cpu() == out["r"][0].cpu()).all()) and \
+            bool((out["f"][1].cpu() == out["r"][1].cpu()).all())
+        fixed_ctx.close()
     cls = torch.empty(n, dtype=torch.int32, device="cuda")
     csum = torch.empty((n, 4), dtype=torch.uint64, device="cuda")
     plan = P.RaggedPlan(ctx, dLs, p, cat, cls, csum, opts=opts, n_sweeps=sw, seed=3101)
@@ -89,6 +109,10 @@ def main(argv=None):
             "plan": {"ms": t_plan * 1e3, "syndromes_per_s": n / t_plan, "updates_per_s": updates / t_plan,
                      "equals_ragged": same},
             "per_L": {"ms": t_perl * 1e3, "syndromes_per_s": n / t_perl, "updates_per_s": updates / t_perl}}
+    if tuned:
+        line["tuned"] = tuned
+        line["ragged_fixed_shape"] = {"ms": t_fixed * 1e3, "syndromes_per_s": n / t_fixed,
+                                      "updates_per_s": updates / t_fixed, "equals_tuned": same_fixed}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0

@@ -267,12 +267,14 @@ def test_decode_ti(ctx, pkg, L, R, nb, anneal):
 
 
 def test_autotune_choice_keeps_results(ctx, pkg):
-    """The autotuner picks the fastest lanes-per-bundle for (L, R); decodes
-    with the tuned shape give the same results as any explicit shape."""
+    """The autotuner picks the fastest (lanes per bundle, resident blocks per
+    multiprocessor) for (L, R); decodes with the tuned shape give the same
+    results as any explicit shape."""
     L, p, R, n = 9, 0.13, 16, 7
-    best, ms = ctx.autotune(L, R, p, n_probe=2048, sweeps=10)
-    assert best in (2, 4, 8, 16, 32)
-    assert ms[best] == min(v for v in ms.values() if v == v)
+    best, best_b, ms = ctx.autotune(L, R, p, n_probe=2048, sweeps=10)
+    assert best in pkg.TUNE_LANES and best_b in pkg.TUNE_BLOCKS
+    assert ms[(best, best_b)] == min(v for v in ms.values() if v == v)
+    assert len(ms) == len(pkg.TUNE_LANES) * len(pkg.TUNE_BLOCKS)
     syn, _ = _oracle_syndromes(2222, n, L, p)
     d = torch.from_numpy(syn).cuda()
     tuned = ctx.decode_ex(d, L, p, pkg.Opts(chains_per_class=R, n_sweeps=15), seed=3)
