@@ -824,7 +824,9 @@ static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM, SCAN, IND, ACPT>, 32 * kWarps,
                                                               smem);
         if (e != cudaSuccess) return e;
-        const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        int bps = per_sm > 0 ? per_sm : 1;
+        if (p.max_blocks_per_sm > 0 && p.max_blocks_per_sm < bps) bps = p.max_blocks_per_sm;
+        const long long resident = (long long)sms * bps;
         if (blocks > resident) blocks = resident;
         e = cudaMemsetAsync(p.unit_counter, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return e;
