@@ -179,8 +179,8 @@ def cpu_baseline(ids_per_p, sweeps=SWEEPS, id0=0):
 
 
 def early_stop_leg():
-    """The learned early stop (the benchmark spec's batched + learned form)
-    against plain long chains, measured inside the run: L = 17, a network
+    """The learned early stop (batched decoding with the network) against
+    plain long chains, measured inside the run: L = 17, a network
     trained from seeds on 2^20 syndromes labelled by the library's own
     chains (p stratified over [0.08, 0.18]), tau calibrated per p on 65,536
     validation syndromes, then plain long chains (4 x 4 chains, 20,000

@@ -133,7 +133,7 @@ def test_trained_network_gain(pkg, ctx):
     """L = 7: a network trained on the library's own labels (p over
     [0.08, 0.18]) stops many syndromes early at p = 0.10; on a fresh test set
     of 131,072 syndromes the early-stop error rate stays within one binomial
-    sigma of the long chains' (the benchmark spec's bar) and the throughput
+    sigma of the long chains' (the bar for a matched error rate) and the throughput
     rises."""
     import argparse
     from paper_1302_2669_gb300 import early_stop as E
