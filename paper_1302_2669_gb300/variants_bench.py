@@ -15,9 +15,11 @@ classes of the sampled errors:
   toric       toric code, 16 classes
 
 All at L = 9 (toric: L = 8), 4 chains per class, 400 sweeps of which the
-first 100 are annealed in 4 stages from 0.3 beta_bar.  Prints one JSON line
-per variant: syndromes/s, stabilizer updates/s (proposals; x 21 for TI) and
-the logical error rate with its binomial sigma.
+first 100 are annealed in 4 stages from 0.3 beta_bar; and the small parity
+configuration itself (small: L = 5, p = 0.15, 200 syndromes of seed 1001,
+decoder seed 1101, 4 x 4 chains, 2,000 sweeps, no burn-in).  Prints one JSON
+line per variant: syndromes/s, stabilizer updates/s (proposals; x 21 for
+TI) and the logical error rate with its binomial sigma.
 """
 from __future__ import annotations
 
@@ -56,7 +58,7 @@ def main(argv=None):
     base = dict(chains_per_class=R, n_sweeps=T, burn_in=burn, anneal_stages=4, anneal_beta0=0.3)
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def run(name, L, p, n, syn, tc, fn, K, n_stab, factor=1):
+    def run(name, L, p, n, syn, tc, fn, K, n_stab, factor=1, T=T, R=R):
         out = fn()
         torch.cuda.synchronize()
         a.record()
@@ -93,6 +95,11 @@ def main(argv=None):
     syn, tc = ctx.gen_syndromes_pauli(9003, 0, 4096, L, px, py, pz, like=like)
     o = P.Opts(**base, noise=2, scan=1, pauli_energy=eg)
     run("general", L, p, 4096, syn, tc, lambda: ctx.decode(syn, L, p, o, seed=9103), 4, ns)
+
+    Ls, ps, Ts = 5, 0.15, 2000
+    syn, tc = ctx.gen_syndromes(1001, 0, 200, Ls, ps, like=like)
+    o = P.Opts(chains_per_class=4, n_sweeps=Ts)
+    run("small", Ls, ps, 200, syn, tc, lambda: ctx.decode(syn, Ls, ps, o, seed=1101), 4, 2 * Ls * (Ls - 1), T=Ts)
 
     Lt, pt = 8, 0.08
     syn, tc = ctx.gen_syndromes_toric(9004, 0, 16384, Lt, pt, like=like)
