@@ -223,6 +223,9 @@ struct DecideParams {
 // Launchers (return cudaGetLastError() after the launch).
 cudaError_t launch_sweep(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
 cudaError_t launch_sweep_flips(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
+// The launch on a kernel with its digit-plane modes compiled in;
+// cudaErrorNotSupported (nothing launched) where there is none.
+cudaError_t launch_sweep_modes(const SweepParams& p, int lanes_per_bundle, cudaStream_t s);
 cudaError_t prepare_sweep_flips(const SweepParams& p, int lanes_per_bundle);
 cudaError_t prepare_sweep(const SweepParams& p, int lanes_per_bundle);
 size_t sweep_smem_bytes(int nq, int nc, int lanes_per_bundle);  // dynamic shared memory of a block

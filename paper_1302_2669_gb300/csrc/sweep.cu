@@ -19,6 +19,9 @@ cudaError_t prepare_sweep(const SweepParams& p, int lam) {
 }
 
 cudaError_t launch_sweep(const SweepParams& p, int lam, cudaStream_t s) {
+    // kernels with the launch's digit-plane modes compiled in, where they exist
+    const cudaError_t e = launch_sweep_modes(p, lam, s);
+    if (e != cudaErrorNotSupported) return e;
     // the general channel (noise 2) runs only in random scan, which reads the
     // energy table and not the template's noise model
     return p.noise == 1 ? launch_sweep_flips(p, lam, s) : launch_noise<false>(p, lam, s);

@@ -242,12 +242,36 @@ struct PlaneBatch {
     }
 };
 
+// Digit-plane modes of a launch (per quad of planes: 0 every threshold digit
+// is 0, 1 only T[1] has nonzero digits, 2 general).  At every temperature the
+// decoder meets, the quads after the first two are general, and the first
+// two are (0, 1), (1, 2) or (2, 2); those three patterns have kernels of
+// their own (HM = 1, 2, 3) with the modes known at compile time, which saves
+// the per-quad dispatch in every proposal.  HM = 0 reads the modes from the
+// launch parameters.
+// Modes of quads 0 and 1 as in SweepParams::qmodes (quad q in bits 2q, 2q+1).
+__host__ __device__ constexpr uint32_t kHeadPatterns[4] = {0u, 0x4u /* 0, 1 */, 0x9u /* 1, 2 */, 0xAu /* 2, 2 */};
+
+template <int HM>
+__device__ __forceinline__ uint32_t quad_mode(const SweepParams& p, int q) {
+    if constexpr (HM == 0) return (p.qmodes >> (2 * q)) & 3u;
+    else return q >= 2 ? 2u : (kHeadPatterns[HM] >> (2 * q)) & 3u;
+}
+
+// The specialised head pattern of a launch's modes (0: none).
+__host__ __device__ inline int head_pattern(uint32_t qmodes) {
+    if ((qmodes >> 4) != 0xAAAu) return 0;   // quads 2 .. 7 general (mode 2 each)
+    for (int hm = 1; hm <= 3; ++hm)
+        if ((qmodes & 0xFu) == (kHeadPatterns[hm] & 0xFu)) return hm;
+    return 0;
+}
+
 // Accept mask of the undecided uphill chains U (all have Delta n = d > 0,
 // d - 1 = E0 + 2 E1 bitwise): chains whose u < T[d], deciding with the digit
 // planes of batches BT0 .. BT1-1.  U keeps the chains still undecided.  The
 // head batches (BT0 = 0) always run in full: some lane of the warp nearly
 // always needs them, so an early exit would only add divergence.
-template <int G, int BT0, int BT1>
+template <int G, int BT0, int BT1, int HM = 0>
 __device__ __forceinline__ uint32_t bernoulli_range(const SweepParams& p, uint32_t& U, uint32_t E0, uint32_t E1,
                                                     const uint32_t* sid, uint32_t w, uint32_t t, uint32_t colm) {
     using PB = PlaneBatch<G>;
@@ -262,7 +286,7 @@ __device__ __forceinline__ uint32_t bernoulli_range(const SweepParams& p, uint32
 #pragma unroll
         for (int qd = 0; qd < PPB / 4; ++qd) {
             const int k0 = bt * PPB + 4 * qd;
-            const uint32_t mode = (p.qmodes >> (2 * (k0 / 4))) & 3u;
+            const uint32_t mode = quad_mode<HM>(p, k0 / 4);
             if (mode == 0) {
                 // every threshold digit is 0 here: a 1 digit rejects
 #pragma unroll
@@ -392,7 +416,7 @@ __device__ __forceinline__ void acpt_add(uint32_t* a, uint32_t acc, uint32_t val
     if (++a[32 * kAcptPlanes] == kAcptCapacity) acpt_flush(a, valid, accepts, ci_of);
 }
 
-template <int G, int LAM, bool SCAN, bool IND, bool ACPT>
+template <int G, int LAM, bool SCAN, bool IND, bool ACPT, int HM>
 __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& gd, long long unit,
                                          uint32_t* smem, const ushort4* tab) {
     constexpr int B = 32 / LAM;                       // bundles per warp
@@ -614,15 +638,16 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                     const uint32_t Wge1 = w0 | w1 | w2, Wge3 = w2 | (w1 & w0);
                     const uint32_t P = (Z0 & Wge1) | (D1 & Wge3);
                     uint32_t acc = ~P & valid;
-                    if (p.accept_all) {
+                    // (a launch with a head pattern has 0 < T[1] < 2^32: neither flag)
+                    if (HM == 0 && p.accept_all) {
                         acc = valid;
                     } else {
                         uint32_t U = P & valid;
-                        if (U && !p.reject_all) {
+                        if (U && (HM != 0 || !p.reject_all)) {
                             // Delta n - 1 = E0 + 2 E1 on the uphill chains
                             const uint32_t E0 = ~w0, E1 = Z0 & Wge3;
                             const uint32_t cm = colm | (uint32_t)m;
-                            acc |= bernoulli_range<G, 0, HEAD>(p, U, E0, E1, sid, w, t, cm);
+                            acc |= bernoulli_range<G, 0, HEAD, HM>(p, U, E0, E1, sid, w, t, cm);
                             if constexpr (HEAD < NBATCH) {
                                 if (U) {
                                     const uint32_t qi = atomicAdd(q_cnt, 1u);
@@ -635,7 +660,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                                         it[4] = acc;
                                         continue;  // flipped after the queue is resolved
                                     }
-                                    acc |= bernoulli_range<G, HEAD, NBATCH>(p, U, E0, E1, sid, w, t, cm);
+                                    acc |= bernoulli_range<G, HEAD, NBATCH, HM>(p, U, E0, E1, sid, w, t, cm);
                                 }
                             }
                         }
@@ -660,7 +685,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                     uint32_t qsid[SLOTS];
 #pragma unroll
                     for (int s = 0; s < SLOTS; ++s) qsid[s] = info[1 + s];
-                    acc |= bernoulli_range<G, HEAD, NBATCH>(p, U, it[2], it[3], qsid, info[0], t,
+                    acc |= bernoulli_range<G, HEAD, NBATCH, HM>(p, U, it[2], it[3], qsid, info[0], t,
                                                             colm | (uint32_t)qm);
                     if constexpr (ACPT) it[4] = acc;
                     if (acc) {
@@ -737,7 +762,7 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
 // fill its warps) first by its index, then from a queue counter, in the order
 // the host arranged (largest work first), and rebuilds the support table in
 // shared memory when the group's code size changes.
-template <int G, int LAM, bool SCAN, bool IND, bool ACPT>
+template <int G, int LAM, bool SCAN, bool IND, bool ACPT, int HM = 0>
 __global__ void __launch_bounds__(128, sweep_blocks_per_sm(G)) sweep_kernel(const __grid_constant__ SweepParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ long long s_unit;
@@ -777,7 +802,7 @@ __global__ void __launch_bounds__(128, sweep_blocks_per_sm(G)) sweep_kernel(cons
             cur = g;
             __syncthreads();
         }
-        run_unit<G, LAM, SCAN, IND, ACPT>(p, gd, u - gd.unit_base, smem, tab);
+        run_unit<G, LAM, SCAN, IND, ACPT, HM>(p, gd, u - gd.unit_base, smem, tab);
         __syncthreads();
         if (!p.unit_counter) break;
     }
@@ -805,14 +830,14 @@ struct SmemLimit {
     }
 };
 
-template <int G, int LAM, bool SCAN, bool IND, bool ACPT = false>
+template <int G, int LAM, bool SCAN, bool IND, bool ACPT = false, int HM = 0>
 static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
     const size_t smem = sweep_smem_bytes(p.grp_nq_max, p.grp_nc_max, LAM) +
                         (ACPT ? (size_t)kWarps * kAcptWordsPerWarp * 4 : 0);
     static SmemLimit limit;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = limit.ensure(sweep_kernel<G, LAM, SCAN, IND, ACPT>, dev, smem);
+    if (e == cudaSuccess) e = limit.ensure(sweep_kernel<G, LAM, SCAN, IND, ACPT, HM>, dev, smem);
     if (e != cudaSuccess) return e;
     if (p.total_units == 0) return cudaSuccess;
     long long blocks = p.total_units;
@@ -821,7 +846,7 @@ static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
         int sms = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM, SCAN, IND, ACPT>, 32 * kWarps,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<G, LAM, SCAN, IND, ACPT, HM>, 32 * kWarps,
                                                               smem);
         if (e != cudaSuccess) return e;
         int bps = per_sm > 0 ? per_sm : 1;
@@ -831,7 +856,7 @@ static cudaError_t launch_t(const SweepParams& p, cudaStream_t s) {
         e = cudaMemsetAsync(p.unit_counter, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return e;
     }
-    sweep_kernel<G, LAM, SCAN, IND, ACPT><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
+    sweep_kernel<G, LAM, SCAN, IND, ACPT, HM><<<(unsigned)blocks, 32 * kWarps, smem, s>>>(p);
     return cudaGetLastError();
 }
 
