@@ -26,14 +26,51 @@ struct RoundKeys {
     uint32_t k[20];  // k[2i], k[2i+1]: key words used in round i
 };
 
-__device__ __forceinline__ uint4 philox10(uint4 c, const RoundKeys& rk) {
+constexpr uint32_t kPhiloxMa = 0xD2511F53u, kPhiloxMb = 0xCD9E8D57u;
+
+// Rounds FIRST .. 9 of Philox4x32-10 on the state c after round FIRST - 1.
+template <int FIRST = 0>
+__device__ __forceinline__ uint4 philox_rounds(uint4 c, const RoundKeys& rk) {
 #pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        const uint32_t h0 = __umulhi(0xD2511F53u, c.x), l0 = 0xD2511F53u * c.x;
-        const uint32_t h1 = __umulhi(0xCD9E8D57u, c.z), l1 = 0xCD9E8D57u * c.z;
+    for (int i = FIRST; i < 10; ++i) {
+        const uint32_t h0 = __umulhi(kPhiloxMa, c.x), l0 = kPhiloxMa * c.x;
+        const uint32_t h1 = __umulhi(kPhiloxMb, c.z), l1 = kPhiloxMb * c.z;
         c = make_uint4(h1 ^ c.y ^ rk.k[2 * i], l1, h0 ^ c.w ^ rk.k[2 * i + 1], l0);
     }
     return c;
+}
+
+__device__ __forceinline__ uint4 philox10(uint4 c, const RoundKeys& rk) { return philox_rounds<0>(c, rk); }
+
+// The same generator split for counters (x0, y0, z0, w0) whose words x0 and
+// w0 stay fixed over many blocks.  Round 0 gives z1 = hi(Ma x0) ^ w0 ^ k[1]
+// and w1 = lo(Ma x0) from x0 and w0 alone, so round 1's products of z1 and
+// w1 ^ k[3] are fixed as well: PhiloxFixed holds M = hi(Mb z1) ^ k[2],
+// N = lo(Mb z1) and A = w1 ^ k[3].  The varying words give x1 = hi(Mb z0) ^
+// y0 ^ k[0], y1 = lo(Mb z0), and the state after round 1 is
+// (M ^ y1, N, hi(Ma x1) ^ A, lo(Ma x1)); rounds 2 .. 9 follow as usual.
+struct PhiloxFixed {
+    uint32_t M, N, A;
+};
+
+__device__ __forceinline__ PhiloxFixed philox_fixed(uint32_t x0, uint32_t w0, const RoundKeys& rk) {
+    const uint32_t z1 = __umulhi(kPhiloxMa, x0) ^ w0 ^ rk.k[1];
+    return {__umulhi(kPhiloxMb, z1) ^ rk.k[2], kPhiloxMb * z1, (kPhiloxMa * x0) ^ rk.k[3]};
+}
+
+// Round 0 and the products of round 1 that depend on the varying words only.
+struct PhiloxVarying {
+    uint32_t y1, hx1, lx1;
+};
+
+__device__ __forceinline__ PhiloxVarying philox_varying(uint32_t y0, uint32_t z0, const RoundKeys& rk) {
+    const uint32_t x1 = __umulhi(kPhiloxMb, z0) ^ y0 ^ rk.k[0];
+    return {kPhiloxMb * z0, __umulhi(kPhiloxMa, x1), kPhiloxMa * x1};
+}
+
+__device__ __forceinline__ uint4 philox10_split(uint32_t M, uint32_t N, uint32_t A, const PhiloxVarying& v,
+                                                const RoundKeys& rk) {
+    return philox_rounds<2>(make_uint4(M ^ v.y1, N, v.hx1 ^ A, v.lx1), rk);
 }
 
 inline void make_round_keys(uint32_t k0, uint32_t k1, RoundKeys* rk) {

@@ -7,7 +7,8 @@ namespace surfmcmc {
 
 size_t sweep_smem_bytes(int nq, int nc, int lam) {
     const int B = 32 / lam;
-    return (size_t)8 * nc * 4 + (size_t)kWarps * ((size_t)B * bundle_stride(nq, lam) + warp_aux_words(B)) * 4;
+    return (size_t)8 * nc * 4 +
+           (size_t)kWarps * ((size_t)B * (kHeadFixedWords + bundle_stride(nq, lam)) + warp_aux_words(B)) * 4;
 }
 
 long long sweep_units(long long n_bundles, int lam) { return (n_bundles + (long long)kWarps * (32 / lam) - 1) /
