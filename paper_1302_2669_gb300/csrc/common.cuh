@@ -176,11 +176,11 @@ __host__ __device__ __forceinline__ int geo_words(int code, int L) { return (geo
 __host__ __device__ __forceinline__ int geo_nc(int code, int L) { return code ? L * L / 2 : L * (L - 1) / 2; }
 
 // Shared-memory words of one bundle split over `lam` lanes: X then Z, each
-// of the qubits padded with zero words to a multiple of 8 lam (so that the
-// lanes' occupancy counts need no bounds test) and followed by two dummy
-// slots.  The stride is odd so that the bundles of a warp fall on banks of
+// of the qubits padded with zero words to a multiple of 4 lam (so that the
+// lanes' occupancy counts, in batches of 8 or 4 words per lane, need no
+// bounds test) and followed by two dummy slots.  The stride is odd so that the bundles of a warp fall on banks of
 // opposite parity: same-colour generators in a row are two qubits apart.
-__host__ __device__ __forceinline__ int padded_nq(int nq, int lam) { return (nq + 8 * lam - 1) / (8 * lam) * (8 * lam); }
+__host__ __device__ __forceinline__ int padded_nq(int nq, int lam) { return (nq + 4 * lam - 1) / (4 * lam) * (4 * lam); }
 __host__ __device__ __forceinline__ int bundle_stride(int nq, int lam) { return 2 * (padded_nq(nq, lam) + 2) + 1; }
 
 // Blocks per SM the sweep kernel is compiled for (its register bound): 6

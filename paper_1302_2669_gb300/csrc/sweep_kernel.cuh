@@ -35,15 +35,17 @@ __device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32
     l = u ^ c;
 }
 
-// Eight occupancy words of the qubits base + i LAM: for depolarizing noise
-// (IND false) a qubit counts once if it carries any error (X | Z); for
-// independent flips (IND true) its bit flip and its phase flip count
-// separately, four qubits per batch.  The planes are zero-padded to a
-// multiple of 8 LAM words, so every index is in range.
-template <int LAM, bool IND>
-__device__ __forceinline__ void occupancy8(const uint32_t* X, const uint32_t* Z, int base, uint32_t x[8]) {
+// Occupancy words of the qubits base + i LAM, i < 8 (N = 8) or i < 4 (N =
+// 4): for depolarizing noise (IND false) a qubit counts once if it carries
+// any error (X | Z); for independent flips (IND true) its bit flip and its
+// phase flip count separately, four qubits per batch of 8 words.  The planes
+// are zero-padded to a multiple of 4 LAM words, so a depolarizing pass takes
+// batches of 8 and at most one batch of 4, every index in range.
+template <int LAM, bool IND, int N = 8>
+__device__ __forceinline__ void occupancy(const uint32_t* X, const uint32_t* Z, int base, uint32_t x[N]) {
+    static_assert(N == 8 || (N == 4 && !IND), "independent flips count in batches of 8 words");
 #pragma unroll
-    for (int i = 0; i < (IND ? 4 : 8); ++i) {
+    for (int i = 0; i < (IND ? 4 : N); ++i) {
         const int q = base + i * LAM;
         if (IND) {
             x[2 * i] = X[q];
@@ -52,6 +54,31 @@ __device__ __forceinline__ void occupancy8(const uint32_t* X, const uint32_t* Z,
             x[i] = X[q] | Z[q];
         }
     }
+}
+
+// Adds a batch of occupancy words to a carry-save count (ones, twos, fours)
+// and returns the carry of weight 8.
+template <int N>
+__device__ __forceinline__ uint32_t add_batch(uint32_t& ones, uint32_t& twos, uint32_t& fours, const uint32_t x[N]) {
+    uint32_t ta, tb, e;
+    if constexpr (N == 8) {
+        uint32_t fa, fb;
+        csa(ta, ones, ones, x[0], x[1]);
+        csa(tb, ones, ones, x[2], x[3]);
+        csa(fa, twos, twos, ta, tb);
+        csa(ta, ones, ones, x[4], x[5]);
+        csa(tb, ones, ones, x[6], x[7]);
+        csa(fb, twos, twos, ta, tb);
+        csa(e, fours, fours, fa, fb);
+    } else {
+        uint32_t f;
+        csa(ta, ones, ones, x[0], x[1]);
+        csa(tb, ones, ones, x[2], x[3]);
+        csa(f, twos, twos, ta, tb);
+        e = fours & f;
+        fours ^= f;
+    }
+    return e;
 }
 
 // n of the 32 chains of a bundle as kCountBits bit planes, identical in all
@@ -63,22 +90,27 @@ __device__ __forceinline__ void recount(const uint32_t* X, const uint32_t* Z, in
     uint32_t hi[kCountBits - 3];
 #pragma unroll
     for (int k = 0; k < kCountBits - 3; ++k) hi[k] = 0;
-    for (int base = sub; base < nqp; base += (IND ? 4 : 8) * LAM) {
-        uint32_t x[8];
-        occupancy8<LAM, IND>(X, Z, base, x);
-        uint32_t ta, tb, fa, fb, e;
-        csa(ta, ones, ones, x[0], x[1]);
-        csa(tb, ones, ones, x[2], x[3]);
-        csa(fa, twos, twos, ta, tb);
-        csa(ta, ones, ones, x[4], x[5]);
-        csa(tb, ones, ones, x[6], x[7]);
-        csa(fb, twos, twos, ta, tb);
-        csa(e, fours, fours, fa, fb);
+    auto ripple = [&](uint32_t e) {
 #pragma unroll
         for (int k = 0; k < kCountBits - 3; ++k) {
             const uint32_t c = hi[k] & e;
             hi[k] ^= e;
             e = c;
+        }
+    };
+    constexpr int STEP = (IND ? 4 : 8) * LAM;
+    const int end8 = nqp - nqp % STEP;
+    int base = sub;
+    for (; base < end8; base += STEP) {
+        uint32_t x[8];
+        occupancy<LAM, IND>(X, Z, base, x);
+        ripple(add_batch<8>(ones, twos, fours, x));
+    }
+    if constexpr (!IND) {
+        if (end8 < nqp) {   // the last 4 LAM qubits
+            uint32_t x[4];
+            occupancy<LAM, IND, 4>(X, Z, base, x);
+            ripple(add_batch<4>(ones, twos, fours, x));
         }
     }
     cnt[0] = ones;
@@ -126,25 +158,30 @@ struct OccAcc {
 
 template <int LAM, bool IND>
 __device__ __forceinline__ void accumulate_phase(OccAcc& a, const uint32_t* X, const uint32_t* Z, int nqp, int sub) {
-    for (int base = sub; base < nqp; base += (IND ? 4 : 8) * LAM) {
-        uint32_t x[8];
-        occupancy8<LAM, IND>(X, Z, base, x);
-        uint32_t ta, tb, fa, fb, e;
-        csa(ta, a.ones, a.ones, x[0], x[1]);
-        csa(tb, a.ones, a.ones, x[2], x[3]);
-        csa(fa, a.twos, a.twos, ta, tb);
-        csa(ta, a.ones, a.ones, x[4], x[5]);
-        csa(tb, a.ones, a.ones, x[6], x[7]);
-        csa(fb, a.twos, a.twos, ta, tb);
-        csa(e, a.fours, a.fours, fa, fb);
-        // ripple the eights into the high planes: the first levels carry for
-        // some of the 32 chains nearly every time, so they run untested
+    // ripple the eights into the high planes: the first levels carry for
+    // some of the 32 chains nearly every time, so they run untested
+    auto ripple = [&](uint32_t e) {
 #pragma unroll
         for (int k = 0; k < kAccHi; ++k) {
             if (k >= 3 && !e) break;
             const uint32_t c = a.hi[k] & e;
             a.hi[k] ^= e;
             e = c;
+        }
+    };
+    constexpr int STEP = (IND ? 4 : 8) * LAM;
+    const int end8 = nqp - nqp % STEP;
+    int base = sub;
+    for (; base < end8; base += STEP) {
+        uint32_t x[8];
+        occupancy<LAM, IND>(X, Z, base, x);
+        ripple(add_batch<8>(a.ones, a.twos, a.fours, x));
+    }
+    if constexpr (!IND) {
+        if (end8 < nqp) {   // the last 4 LAM qubits
+            uint32_t x[4];
+            occupancy<LAM, IND, 4>(X, Z, base, x);
+            ripple(add_batch<4>(a.ones, a.twos, a.fours, x));
         }
     }
 }
