@@ -183,9 +183,11 @@ __host__ __device__ __forceinline__ int geo_nc(int code, int L) { return code ? 
 __host__ __device__ __forceinline__ int padded_nq(int nq, int lam) { return (nq + 4 * lam - 1) / (4 * lam) * (4 * lam); }
 __host__ __device__ __forceinline__ int bundle_stride(int nq, int lam) { return 2 * (padded_nq(nq, lam) + 2) + 1; }
 
-// Blocks per SM the sweep kernel is compiled for (its register bound): 6
-// with plane widths of 16 or 32 chains, 3 with narrower planes.
-__host__ __device__ constexpr int sweep_blocks_per_sm(int G) { return G >= 16 ? 6 : 3; }
+// Blocks per SM the sweep kernel is compiled for (its register bound): 5
+// with plane widths of 32 chains (96 registers, no spills: 0.8 % faster at
+// L = 13 than 6 blocks at 80 registers), 6 with 16 (6 blocks measured 3.7 %
+// faster than 5 there), 3 with narrower planes.
+__host__ __device__ constexpr int sweep_blocks_per_sm(int G) { return G == 32 ? 5 : G == 16 ? 6 : 3; }
 
 // ---------------------------------------------------------------------------
 // Sweep kernel parameters.  One launch runs the chains of up to kMaxGroups
