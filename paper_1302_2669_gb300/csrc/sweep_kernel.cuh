@@ -747,12 +747,15 @@ __device__ __forceinline__ void run_unit(const SweepParams& p, const GroupDesc& 
                     // Delta n = W - 2D > 0  iff  (D = 0, W >= 1) or (D = 1, W >= 3)
                     const uint32_t Wge1 = w0 | w1 | w2, Wge3 = w2 | (w1 & w0);
                     const uint32_t P = (Z0 & Wge1) | (D1 & Wge3);
-                    uint32_t acc = ~P & valid;
+                    // the kernels with a head pattern on 32-chain planes run only
+                    // whole bundles (their launches have a multiple of 32 chains)
+                    const uint32_t vmask = (HM != 0 && G == 32) ? 0xFFFFFFFFu : valid;
+                    uint32_t acc = ~P & vmask;
                     // (a launch with a head pattern has 0 < T[1] < 2^32: neither flag)
                     if (HM == 0 && p.accept_all) {
                         acc = valid;
                     } else {
-                        uint32_t U = P & valid;
+                        uint32_t U = P & vmask;
                         if (U && (HM != 0 || !p.reject_all)) {
                             // Delta n - 1 = E0 + 2 E1 on the uphill chains
                             const uint32_t E0 = ~w0, E1 = Z0 & Wge3;

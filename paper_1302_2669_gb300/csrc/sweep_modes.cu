@@ -35,7 +35,8 @@ cudaError_t launch_sweep_modes(const SweepParams& p, int lam, cudaStream_t s) {
     if (hm == 0) return cudaErrorNotSupported;
     switch (p.G) {
         case 16: return launch_g_hm<16>(p, lam, hm, s);
-        case 32: return launch_g_hm<32>(p, lam, hm, s);
+        // whole bundles only: the kernels take every chain of a bundle as valid
+        case 32: return p.C % 32 == 0 ? launch_g_hm<32>(p, lam, hm, s) : cudaErrorNotSupported;
         default: return cudaErrorNotSupported;
     }
 }
