@@ -54,9 +54,9 @@ INT_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) of one sampled sweep launch per syndrome of the
 # L = 13, 4 x 16-chain workload, from one ncu capture at 8,192 syndromes
-# (41,099,008 B read + 2,560 B written: the bit-sliced chain state handed
+# (41,110,784 B read + 3,584 B written: the bit-sliced chain state handed
 # over from the last annealing launch, proportional to the syndromes).
-SWEEP_DRAM_BYTES_PER_SYNDROME = (41099008 + 2560) / 8192
+SWEEP_DRAM_BYTES_PER_SYNDROME = (41110784 + 3584) / 8192
 
 
 def ops_per_update() -> float:

@@ -6,11 +6,12 @@ library's continuous-batching server.
 Requests: L uniform over {9, 13, 17, 25}, depolarizing p = 0.12, sweeps = L^2
 (the first quarter annealed from 0.3 beta_bar in 4 stages, not sampled),
 4 classes x 4 chains.  Syndromes are seeded synthetic inputs made by the
-library's generator before the run.  The same arrivals are served twice:
-without a memory budget and with --memory-budget bytes (default 2 MiB,
-about two batches' scratch at this rate), so that admission has to wait
-for memory.  Prints one JSON line with, per run, the offered and achieved
-rates, p50/p99/max latency, batches and memory stalls.
+library's generator before the run.  The same arrivals are served without a
+memory budget and then under each of --memory-budgets (bytes of device
+scratch; default 2 MiB, 512 KiB and 256 KiB), so that admission has to
+shrink batches and, under the tighter budgets, wait for memory.  Prints one
+JSON line with, per run, the offered and achieved rates, p50/p99/max
+latency, batches and memory stalls.
 """
 from __future__ import annotations
 
@@ -31,8 +32,8 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--max-batch", type=int, default=1024)
     ap.add_argument("--max-wait-us", type=float, default=500.0)
-    ap.add_argument("--memory-budget", type=int, default=2 * 1024 * 1024,
-                    help="budget of the second run (0: run only without a budget)")
+    ap.add_argument("--memory-budgets", default="2097152,524288,262144",
+                    help="comma-separated budgets of the runs after the unbudgeted one (empty: none)")
     ap.add_argument("--seed", type=int, default=5001)
     args = ap.parse_args(argv)
 
@@ -93,7 +94,8 @@ def main(argv=None):
                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                 "max_ms": float(lat_ms.max()), "batches": st["batches"], "memory_stalls": st["memory_stalls"]}
 
-    runs = [serve(0)] + ([serve(args.memory_budget)] if args.memory_budget > 0 else [])
+    budgets = [int(x) for x in args.memory_budgets.split(",") if x.strip()]
+    runs = [serve(0)] + [serve(b) for b in budgets if b > 0]
     line = {"metric": "serving latency and throughput", "offered_rps": args.rate, "requests": n_req,
             **{k: v for k, v in runs[0].items() if k != "memory_budget"},
             "runs": runs,
