@@ -185,13 +185,14 @@ def early_stop_leg():
     chains (p stratified over [0.08, 0.18]), tau calibrated per p on 65,536
     validation syndromes, then plain long chains (4 x 4 chains, 20,000
     sweeps, the first 4,000 annealed in 16 stages from 0.1 beta_bar) and
-    the early-stopped decode timed on 65,536 fresh test syndromes at
-    p = 0.10 and 0.14 (CUDA events, one call each after a warm-up call)."""
+    the early-stopped decode (checkpoints every 500 sweeps after the
+    burn-in) timed on 65,536 fresh test syndromes at p = 0.10 and 0.14
+    (CUDA events, one call each after a warm-up call)."""
     import argparse
     from paper_1302_2669_gb300 import early_stop as E
     ns = argparse.Namespace(L=17, train=1 << 20, val=65536, test=65536, p_lo=0.08, p_hi=0.18, n_p=32, label_R=4,
                             label_sweeps=2000, epochs=8, batch=1024, lr=2e-3, lr_final=1e-4, R=4, sweeps=20000,
-                            burn_in=4000, anneal_stages=16, anneal_beta0=0.1, chunk=1000, seed=4001,
+                            burn_in=4000, anneal_stages=16, anneal_beta0=0.1, chunk=500, seed=4001,
                             eval_ps=[0.10, 0.14], reorder=False)
     t0 = time.perf_counter()
     res = E.run(ns, log=lambda m: None)

@@ -364,7 +364,9 @@ int surfmcmc_server_poll(surfmcmc_server* server, int64_t max_results, uint32_t*
                          uint64_t* class_sums, double* latency_us, int64_t* n_out, int32_t wait_us);
 
 /* Counters since creation: requests admitted to batches, batches launched,
- * admissions deferred by the memory budget, requests waiting now. */
+ * times admission had to wait for memory (a free slot and waiting requests,
+ * but not even one request's scratch fits the budget next to the batches in
+ * flight; counted once per wait), requests waiting now. */
 int surfmcmc_server_stats(surfmcmc_server* server, int64_t* admitted, int64_t* batches, int64_t* memory_stalls,
                           int64_t* pending);
 

@@ -79,21 +79,21 @@ struct surfmcmc_server {
     bool stop = false;
     std::thread worker;
     int64_t admitted = 0, batches = 0, memory_stalls = 0;
+    bool waiting_for_memory = false;     // admission is waiting for memory now
     size_t in_flight_bytes = 0;
     std::string error;
 };
 
 namespace {
 
-// Device scratch a ragged batch of these sizes needs (upper bound, as the
-// library carves it): rows, tables, pure errors, sums, bundle state.
-size_t batch_bytes(const std::vector<Request>& b, int R) {
-    size_t bytes = 64 * 1024;
-    for (const Request& r : b) {
-        const size_t nq = (size_t)n_qubits(r.L), W = (size_t)n_words(r.L);
-        bytes += (size_t)n_stabs(r.L) + 64 + 2 * W * 4 + (size_t)4 * R * 8 + 2 * nq * 4 + 256;
-    }
-    return bytes;
+// Device scratch of a ragged batch (upper bound, as the library carves it):
+// a fixed part plus, per request, its row, table entries, pure error, sums
+// and bundle state.
+constexpr size_t kBatchBaseBytes = 64 * 1024;
+
+size_t request_bytes(int L, int R) {
+    const size_t nq = (size_t)n_qubits(L), W = (size_t)n_words(L);
+    return (size_t)n_stabs(L) + 64 + 2 * W * 4 + (size_t)4 * R * 8 + 2 * nq * 4 + 256;
 }
 
 void finish_slot(surfmcmc_server* s, Slot& sl) {
@@ -141,28 +141,33 @@ void worker_main(surfmcmc_server* s) {
                                           Clock::now() - s->pending.front().t_submit).count();
                 const bool full = (int64_t)s->pending.size() >= s->sopts.max_batch;
                 if (full || waited >= s->sopts.max_wait_us || s->stop) {
-                    while (!s->pending.empty() && (int64_t)batch.size() < s->sopts.max_batch) {
-                        batch.push_back(std::move(s->pending.front()));
-                        s->pending.pop_front();
+                    // the batch: the longest prefix of the queue of at most
+                    // max_batch requests whose scratch fits the memory budget
+                    // next to the batches in flight (at least one request)
+                    const size_t budget = (size_t)s->sopts.memory_budget;
+                    size_t need = kBatchBaseBytes;
+                    int64_t k = 0;
+                    for (auto it = s->pending.begin(); it != s->pending.end() && k < s->sopts.max_batch; ++it) {
+                        const size_t b = request_bytes(it->L, R);
+                        if (budget > 0 && k > 0 && s->in_flight_bytes + need + b > budget) break;
+                        need += b;
+                        ++k;
                     }
-                    size_t need = batch_bytes(batch, R);
-                    // admission by memory: shrink the batch until it fits next to the batches in flight
-                    while (s->sopts.memory_budget > 0 && batch.size() > 1 &&
-                           s->in_flight_bytes + need > (size_t)s->sopts.memory_budget) {
-                        s->pending.push_front(std::move(batch.back()));
-                        batch.pop_back();
-                        need = batch_bytes(batch, R);
-                    }
-                    if (s->sopts.memory_budget > 0 && s->in_flight_bytes > 0 &&
-                        s->in_flight_bytes + need > (size_t)s->sopts.memory_budget) {
-                        for (auto it = batch.rbegin(); it != batch.rend(); ++it)
-                            s->pending.push_front(std::move(*it));
-                        batch.clear();
-                        ++s->memory_stalls;
+                    if (budget > 0 && s->in_flight_bytes > 0 && s->in_flight_bytes + need > budget) {
+                        // not even one request fits: wait for a batch in flight
+                        // to finish (counted once per wait)
+                        if (!s->waiting_for_memory) ++s->memory_stalls;
+                        s->waiting_for_memory = true;
                     } else {
+                        s->waiting_for_memory = false;
+                        batch.reserve((size_t)k);
+                        for (int64_t i = 0; i < k; ++i) {
+                            batch.push_back(std::move(s->pending.front()));
+                            s->pending.pop_front();
+                        }
                         free_slot->scratch = need;
                         s->in_flight_bytes += need;
-                        s->admitted += (int64_t)batch.size();
+                        s->admitted += k;
                         ++s->batches;
                     }
                 }

@@ -292,7 +292,7 @@ def main(argv=None):
     ap.add_argument("--n-p", type=int, default=32)
     ap.add_argument("--label-R", type=int, default=4)
     ap.add_argument("--label-sweeps", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--lr-final", type=float, default=1e-4)
@@ -301,7 +301,9 @@ def main(argv=None):
     ap.add_argument("--burn-in", type=int, default=4000)
     ap.add_argument("--anneal-stages", type=int, default=16)
     ap.add_argument("--anneal-beta0", type=float, default=0.1)
-    ap.add_argument("--chunk", type=int, default=1000)
+    ap.add_argument("--chunk", type=int, default=500,
+                    help="sweeps between checkpoints after the burn-in (500 measured 5-9 %% faster than 1000 "
+                         "at p = 0.08-0.14, and 250 no better)")
     ap.add_argument("--seed", type=int, default=4001)
     ap.add_argument("--eval-ps", default="0.08,0.10,0.12,0.14,0.16")
     ap.add_argument("--out", default=None)
