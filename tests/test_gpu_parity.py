@@ -106,9 +106,12 @@ def test_config1_all_200(ctx, pkg):
         _compare_decode(out, ref, i, 4 * R, L)
 
 
+# (R = 6 and 12: 24 and 48 chains, 32-chain planes with a partly filled
+# bundle, which the kernels specialised for whole bundles must not take)
 @pytest.mark.parametrize("L,p,R,sweeps", [(2, 0.2, 4, 50), (3, 0.1, 16, 30), (4, 0.12, 8, 30),
                                           (7, 0.13, 16, 20), (13, 0.16, 16, 6), (17, 0.18, 4, 3),
-                                          (25, 0.1, 8, 2), (31, 0.14, 4, 2)])
+                                          (25, 0.1, 8, 2), (31, 0.14, 4, 2), (9, 0.13, 12, 10),
+                                          (5, 0.16, 6, 20)])
 def test_decode_sizes(ctx, pkg, L, p, R, sweeps):
     n = 9
     syn, _ = _oracle_syndromes(2000 + L, n, L, p)
