@@ -191,7 +191,7 @@ def early_stop_leg():
     import argparse
     from paper_1302_2669_gb300 import early_stop as E
     ns = argparse.Namespace(L=17, train=1 << 20, val=65536, test=65536, p_lo=0.08, p_hi=0.18, n_p=32, label_R=4,
-                            label_sweeps=2000, epochs=8, batch=1024, lr=2e-3, lr_final=1e-4, R=4, sweeps=20000,
+                            label_sweeps=4000, epochs=16, batch=1024, lr=2e-3, lr_final=1e-4, R=4, sweeps=20000,
                             burn_in=4000, anneal_stages=16, anneal_beta0=0.1, chunk=500, seed=4001,
                             eval_ps=[0.10, 0.14], reorder=False)
     t0 = time.perf_counter()

@@ -1,8 +1,10 @@
 // Sweep kernels with the digit-plane modes known at compile time (the three
 // head patterns of depolarizing noise, see head_pattern), for plane widths
 // of 16 and 32 chains and 8, 16 or 32 lanes per bundle: the shapes that
-// decodes with 9 or more chains per syndrome take.  Other launches use the
-// kernels of sweep.cu, which read the modes from their parameters.
+// decodes with 9 or more chains per syndrome take.  The 32-chain kernels
+// take every chain of a bundle as valid, so they serve launches whose chain
+// count per syndrome is a multiple of 32.  Other launches use the kernels
+// of sweep.cu, which read the modes from their parameters.
 #include "sweep_kernel.cuh"
 
 namespace surfmcmc {

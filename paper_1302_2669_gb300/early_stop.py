@@ -291,8 +291,8 @@ def main(argv=None):
     ap.add_argument("--p-hi", type=float, default=0.18)
     ap.add_argument("--n-p", type=int, default=32)
     ap.add_argument("--label-R", type=int, default=4)
-    ap.add_argument("--label-sweeps", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--label-sweeps", type=int, default=4000)
+    ap.add_argument("--epochs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--lr-final", type=float, default=1e-4)
