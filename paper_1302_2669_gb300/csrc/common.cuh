@@ -178,17 +178,10 @@ __host__ __device__ __forceinline__ int geo_nc(int code, int L) { return code ? 
 // Shared-memory words of one bundle split over `lam` lanes: X then Z, each
 // of the qubits padded with zero words to a multiple of 4 lam (so that the
 // lanes' occupancy counts, in batches of 8 or 4 words per lane, need no
-// bounds test) and followed by two dummy slots.  The stride (rounded up to
-// lam + 1 mod 32) is odd, so that the bundles of a warp fall on banks of
-// opposite parity (same-colour generators in a row are two qubits apart), and
-// puts the k-th bundle of a warp k lam banks further, so that the bundles'
-// windows of lam consecutive words in the occupancy counts barely overlap
-// (at 16 lanes: one bank of 16 instead of 11 with the plain odd stride).
+// bounds test) and followed by two dummy slots.  The stride is odd so that the bundles of a warp fall on banks of
+// opposite parity: same-colour generators in a row are two qubits apart.
 __host__ __device__ __forceinline__ int padded_nq(int nq, int lam) { return (nq + 4 * lam - 1) / (4 * lam) * (4 * lam); }
-__host__ __device__ __forceinline__ int bundle_stride(int nq, int lam) {
-    const int s = 2 * (padded_nq(nq, lam) + 2) + 1;
-    return s + ((lam + 1 - s) & 31);
-}
+__host__ __device__ __forceinline__ int bundle_stride(int nq, int lam) { return 2 * (padded_nq(nq, lam) + 2) + 1; }
 
 // Blocks per SM the sweep kernel is compiled for (its register bound): 5
 // with plane widths of 32 chains (96 registers, no spills: 0.8 % faster at
