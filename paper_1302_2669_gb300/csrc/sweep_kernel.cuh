@@ -237,14 +237,7 @@ struct PlaneBatch {
             const uint4 b = philox10(make_uint4(sid[0], t, colm, (w << 8) | bt), p.rk);
             pl[0] = b.x; pl[1] = b.y; pl[2] = b.z; pl[3] = b.w;
         } else if constexpr (G == 16) {
-            const uint4 a = philox10(make_uint4(sid[0], t, colm, bt), p.rk);
-            const uint4 c = philox10(make_uint4(sid[1], t, colm, bt), p.rk);
-            const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, cw[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                pl[2 * i] = __byte_perm(aw[i], cw[i], 0x5410);
-                pl[2 * i + 1] = __byte_perm(aw[i], cw[i], 0x7632);
-            }
+            merge16(philox10(make_uint4(sid[0], t, colm, bt), p.rk), philox10(make_uint4(sid[1], t, colm, bt), p.rk));
         } else if constexpr (G == 8) {
             uint32_t bw[4][4];
 #pragma unroll
@@ -289,14 +282,19 @@ struct PlaneBatch {
                                     : philox10_split(mn.z, mn.w, a2.x, v, p.rk);
             pl[0] = b.x; pl[1] = b.y; pl[2] = b.z; pl[3] = b.w;
         } else {
-            const uint4 a = philox10_split(mn.x, mn.y, a2.x, v, p.rk);
-            const uint4 c = philox10_split(mn.z, mn.w, a2.y, v, p.rk);
-            const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, cw[4] = {c.x, c.y, c.z, c.w};
+            merge16(philox10_split(mn.x, mn.y, a2.x, v, p.rk), philox10_split(mn.z, mn.w, a2.y, v, p.rk));
+        }
+    }
+
+    // G = 16: the blocks a and c of the bundle's two syndromes; plane 2i
+    // takes the low halves of word i of each (a's in bits 0-15), plane 2i + 1
+    // the high halves.
+    __device__ __forceinline__ void merge16(const uint4& a, const uint4& c) {
+        const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, cw[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                pl[2 * i] = __byte_perm(aw[i], cw[i], 0x5410);
-                pl[2 * i + 1] = __byte_perm(aw[i], cw[i], 0x7632);
-            }
+        for (int i = 0; i < 4; ++i) {
+            pl[2 * i] = __byte_perm(aw[i], cw[i], 0x5410);
+            pl[2 * i + 1] = __byte_perm(aw[i], cw[i], 0x7632);
         }
     }
 };
